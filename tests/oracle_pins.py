@@ -1,0 +1,255 @@
+"""Pins that tie the CPU oracle to facts other than itself.
+
+Each pin takes an oracle library handle (``oracle.load()`` or a deliberately
+broken copy built by the mutation tests) and raises AssertionError when the
+oracle disagrees with:
+
+* brute force in numpy complex128 on tiny inputs (an independent evaluation
+  of Eq. (outer) of Sec. 2.1 and of the lower-triangle packing);
+* invariants the definition fixes: real non-negative autocorrelations equal
+  to sum |x|^2, Hermitian symmetry of the diagonal baselines' cross-pol
+  products, identical signals giving identical visibilities, the closed form
+  of a scaled common signal, quadratic scaling, the cross-term expansion of
+  a sum of signals;
+* the statistical expectation for injected point sources (this fixes the
+  conjugation convention: the phase of V_ab is phi_a - phi_b);
+* the int32 range argument of the 8-bit path (Sec. 5 input, int64 oracle);
+* central finite differences of the FP64 forward for the adjoint.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_1107_4264_gb300 import synth
+
+
+def _cx(x: np.ndarray) -> np.ndarray:
+    """[..., 2] real pairs -> complex128."""
+    x = np.asarray(x, dtype=np.float64)
+    return x[..., 0] + 1j * x[..., 1]
+
+
+def brute_force(x: np.ndarray, gains=None) -> np.ndarray:
+    """Independent evaluation with numpy: V_f = Y_f^T conj(Y_f) over time,
+    then the lower triangle of station pairs in row-major order."""
+    T, F, N, P, _ = x.shape
+    X = _cx(x).reshape(T, F, N * P)
+    if gains is not None:
+        X = X * _cx(gains).reshape(1, 1, N * P)
+    V = np.einsum("tfa,tfb->fab", X, X.conj())
+    rows, cols = np.tril_indices(N)
+    out = np.zeros((F, len(rows), P * P, 2))
+    for p1 in range(P):
+        for p2 in range(P):
+            v = V[:, rows * P + p1, cols * P + p2]
+            out[:, :, p1 * P + p2, 0] = v.real
+            out[:, :, p1 * P + p2, 1] = v.imag
+    return out
+
+
+def pin_brute_force_int(lib):
+    rng = np.random.default_rng(11)
+    for (T, F, N, P) in [(37, 3, 5, 2), (1, 1, 1, 1), (8, 2, 7, 1), (0, 2, 3, 2)]:
+        x = rng.integers(-128, 128, (T, F, N, P, 2)).astype(np.int8)
+        got = oracle.correlate_i8(x, lib=lib)
+        want = brute_force(x)
+        assert got.dtype == np.int64
+        np.testing.assert_array_equal(got, np.rint(want).astype(np.int64))
+    # channel subset selects channels
+    x = rng.integers(-128, 128, (9, 4, 3, 2, 2)).astype(np.int8)
+    np.testing.assert_array_equal(oracle.correlate_i8(x, chans=[3, 1], lib=lib),
+                                  oracle.correlate_i8(x, lib=lib)[[3, 1]])
+
+
+def pin_brute_force_float(lib):
+    rng = np.random.default_rng(12)
+    for (T, F, N, P) in [(23, 2, 4, 2), (5, 3, 3, 1)]:
+        x = rng.standard_normal((T, F, N, P, 2))
+        g = rng.standard_normal((N, P, 2))
+        np.testing.assert_allclose(oracle.correlate_f64(x, lib=lib), brute_force(x),
+                                   rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(oracle.correlate_f64(x, gains=g, lib=lib),
+                                   brute_force(x, gains=g), rtol=1e-12, atol=1e-12)
+
+
+def _diag_k(N):
+    return [s * (s + 1) // 2 + s for s in range(N)]
+
+
+def pin_autocorrelations(lib):
+    x = synth.tiny_input(synth.TINY).numpy()
+    T, F, N, P, _ = x.shape
+    out = oracle.correlate_i8(x, lib=lib)
+    xs = x.astype(np.int64)
+    power = (xs[..., 0] ** 2 + xs[..., 1] ** 2).sum(axis=0)  # [F][N][P]
+    for s, k in enumerate(_diag_k(N)):
+        for p in range(P):
+            v = out[:, k, p * P + p]
+            assert (v[:, 1] == 0).all(), "autocorrelation must be real"
+            assert (v[:, 0] >= 0).all()
+            np.testing.assert_array_equal(v[:, 0], power[:, s, p])
+
+
+def pin_hermitian_diagonal(lib):
+    x = synth.tiny_input(synth.TINY).numpy()
+    N, P = x.shape[2], x.shape[3]
+    out = oracle.correlate_i8(x, lib=lib)
+    for k in _diag_k(N):
+        xy, yx = out[:, k, 0 * P + 1], out[:, k, 1 * P + 0]
+        np.testing.assert_array_equal(xy[:, 0], yx[:, 0])
+        np.testing.assert_array_equal(xy[:, 1], -yx[:, 1])
+
+
+def pin_identical_signals(lib):
+    rng = np.random.default_rng(13)
+    T, F, N, P = 50, 2, 6, 2
+    s = rng.integers(-100, 101, (T, F, 1, 1, 2)).astype(np.int8)
+    x = np.broadcast_to(s, (T, F, N, P, 2)).copy()
+    out = oracle.correlate_i8(x, lib=lib)
+    pw = (s.astype(np.int64) ** 2).sum(axis=(0, 2, 3, 4))  # [F]
+    for f in range(F):
+        assert (out[f, :, :, 0] == pw[f]).all()
+        assert (out[f, :, :, 1] == 0).all()
+
+
+def pin_closed_form(lib):
+    """x_a(t) = c_a s(t) with integer complex c_a: V_ab = c_a conj(c_b) sum|s|^2."""
+    rng = np.random.default_rng(14)
+    T, F, N, P = 40, 3, 5, 2
+    s = rng.integers(-5, 6, (T, F, 2))
+    c = rng.integers(-4, 5, (N, P, 2))
+    x = np.zeros((T, F, N, P, 2), dtype=np.int64)
+    x[..., 0] = s[:, :, None, None, 0] * c[None, None, :, :, 0] - s[:, :, None, None, 1] * c[None, None, :, :, 1]
+    x[..., 1] = s[:, :, None, None, 0] * c[None, None, :, :, 1] + s[:, :, None, None, 1] * c[None, None, :, :, 0]
+    out = oracle.correlate_i8(x.astype(np.int8), lib=lib)
+    S = (s ** 2).sum(axis=(0, 2))  # [F]
+    for s1 in range(N):
+        for s2 in range(s1 + 1):
+            k = s1 * (s1 + 1) // 2 + s2
+            for p1 in range(P):
+                for p2 in range(P):
+                    ar, ai = c[s1, p1]
+                    br, bi = c[s2, p2]
+                    re = ar * br + ai * bi  # c_a conj(c_b)
+                    im = ai * br - ar * bi
+                    np.testing.assert_array_equal(out[:, k, p1 * P + p2, 0], re * S)
+                    np.testing.assert_array_equal(out[:, k, p1 * P + p2, 1], im * S)
+
+
+def pin_scaling_and_cross_terms(lib):
+    rng = np.random.default_rng(15)
+    T, F, N, P = 30, 2, 4, 2
+    x = rng.integers(-20, 21, (T, F, N, P, 2))
+    y = rng.integers(-20, 21, (T, F, N, P, 2))
+    Vx = oracle.correlate_i8(x.astype(np.int8), lib=lib)
+    # V(alpha x) = |alpha|^2 V(x), alpha = 2 - 3i
+    ax = np.empty_like(x)
+    ax[..., 0] = 2 * x[..., 0] + 3 * x[..., 1]
+    ax[..., 1] = 2 * x[..., 1] - 3 * x[..., 0]
+    np.testing.assert_array_equal(oracle.correlate_i8(ax.astype(np.int8), lib=lib), 13 * Vx)
+    # V(x + y) = V(x) + V(y) + [x y^H + y x^H] (cross terms by numpy)
+    Vy = oracle.correlate_i8(y.astype(np.int8), lib=lib)
+    Vxy = oracle.correlate_i8((x + y).astype(np.int8), lib=lib)
+    X, Y = _cx(x).reshape(T, F, N * P), _cx(y).reshape(T, F, N * P)
+    C = np.einsum("tfa,tfb->fab", X, Y.conj()) + np.einsum("tfa,tfb->fab", Y, X.conj())
+    rows, cols = np.tril_indices(N)
+    for p1 in range(P):
+        for p2 in range(P):
+            cv = C[:, rows * P + p1, cols * P + p2]
+            d = Vxy[:, :, p1 * P + p2] - Vx[:, :, p1 * P + p2] - Vy[:, :, p1 * P + p2]
+            np.testing.assert_array_equal(d[..., 0], np.rint(cv.real).astype(np.int64))
+            np.testing.assert_array_equal(d[..., 1], np.rint(cv.imag).astype(np.int64))
+
+
+def pin_point_source_statistics(lib):
+    """E[V_ab^{pq}]/T = delta_pq [sigma_c^2 delta_ab + sum_k A^2 e^{i(phi_ka - phi_kb)}]."""
+    T, F, N, P, K, A, sig = 20000, 2, 4, 2, 2, 1.0, 0.5
+    seed = 4242
+    x = synth.sky_voltages(T, F, N, P, noise_sigma=sig, nsrc=K, src_amp=A, seed=seed,
+                           dtype=torch_float64()).numpy()
+    out = oracle.correlate_f64(x, lib=lib) / T
+    phi = synth.steering_phases(N, F, K, seed)  # [K][F][N]
+    noise_pow = 2 * sig ** 2
+    for f in range(F):
+        for s1 in range(N):
+            for s2 in range(s1 + 1):
+                k = s1 * (s1 + 1) // 2 + s2
+                for p1 in range(P):
+                    for p2 in range(P):
+                        e = 0j
+                        if p1 == p2:
+                            e = (noise_pow if s1 == s2 else 0.0) + A ** 2 * np.exp(
+                                1j * (phi[:, f, s1] - phi[:, f, s2])).sum()
+                        got = complex(*out[f, k, p1 * P + p2])
+                        # per-sample power <= noise + K A^2; std of the mean ~ power/sqrt(T)
+                        tol = 6.0 * (noise_pow + K * A ** 2) / np.sqrt(T)
+                        assert abs(got - e) < tol, (f, s1, s2, p1, p2, got, e)
+
+
+def torch_float64():
+    import torch
+    return torch.float64
+
+
+INT32_MAX = 2 ** 31 - 1
+T_MAX_FULL_RANGE = 66572  # largest T with T * 2 * 127^2 < 2^31
+
+
+def pin_int32_bound(lib):
+    for T, fits in [(T_MAX_FULL_RANGE, True), (T_MAX_FULL_RANGE + 1, False)]:
+        x = np.full((T, 1, 1, 1, 2), 127, dtype=np.int8)
+        out = oracle.correlate_i8(x, lib=lib)
+        assert out[0, 0, 0, 0] == T * 2 * 127 * 127
+        assert (out[0, 0, 0, 0] <= INT32_MAX) == fits
+
+
+def _loss_and_grad_out(V, M, W):
+    d = V - M
+    L = float((W[..., None] * d * d).sum())
+    return L, 2.0 * W[..., None] * d
+
+
+def pin_adjoint_finite_differences(lib):
+    rng = np.random.default_rng(16)
+    T, F, N, P = 5, 2, 3, 2
+    x = rng.standard_normal((T, F, N, P, 2))
+    g = rng.standard_normal((N, P, 2))
+    M = rng.standard_normal((F, N * (N + 1) // 2, P * P, 2))
+    W = rng.uniform(0, 1, (F, N * (N + 1) // 2, P * P))
+
+    def loss(xx, gg):
+        V = oracle.correlate_f64(xx, gains=gg, lib=lib)
+        return _loss_and_grad_out(V, M, W)[0]
+
+    V = oracle.correlate_f64(x, gains=g, lib=lib)
+    _, go = _loss_and_grad_out(V, M, W)
+    gx, gg = oracle.backward_f64(x, go, gains=g, lib=lib)
+    h = 1e-5
+    idx = [tuple(rng.integers(0, s) for s in x.shape) for _ in range(24)]
+    for i in idx:
+        xp, xm = x.copy(), x.copy()
+        xp[i] += h
+        xm[i] -= h
+        fd = (loss(xp, g) - loss(xm, g)) / (2 * h)
+        assert abs(fd - gx[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, gx[i])
+    for i in np.ndindex(g.shape):
+        gp, gm = g.copy(), g.copy()
+        gp[i] += h
+        gm[i] -= h
+        fd = (loss(x, gp) - loss(x, gm)) / (2 * h)
+        assert abs(fd - gg[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, gg[i])
+
+
+ALL_PINS = [
+    pin_brute_force_int,
+    pin_brute_force_float,
+    pin_autocorrelations,
+    pin_hermitian_diagonal,
+    pin_identical_signals,
+    pin_closed_form,
+    pin_scaling_and_cross_terms,
+    pin_point_source_statistics,
+    pin_int32_bound,
+    pin_adjoint_finite_differences,
+]
