@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""X-engine benchmark: Large-N 8-bit workload on GB300.
+
+Workload (one step): 10 integrations of N=256 dual-polarisation stations,
+F=1024 channels, T=1000 samples per integration, complex int8 input
+[T][F][N][P][2] (noise sigma 3 plus 3 point sources, rounded and clipped),
+int32 visibilities of the N(N+1)/2 baselines x 4 polarisation products.
+
+Metric: X-engine TOPS at 8 real ops per complex multiply-accumulate, one CMAC
+per stored (baseline, polarisation product) per sample (the Eq. flops
+convention of Sec. 2.1 applied to the stored products), with the tensor-core
+fraction of peak and the speedup over the plain FP32 CUDA-core form of the
+same X-engine on the same GPU.
+
+  value   device-resident inputs (HBM), timed with CUDA events over K steps.
+  e2e     the same work through xc_correlate_stream: inputs in pinned host
+          memory, H2D copies overlapped with compute (Algorithm 1 of Sec. 5)
+          and every visibility copied back to pinned host memory.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xc|reference]
+Under torchrun (N > 1) every rank correlates its own 10 integrations (weak
+scaling, no data-path collective; barrier and max-over-ranks timing only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "X-engine TOPS (8 ops/CMAC) & % tensor peak vs plain FP32 CUDA-core X-engine"
+UNIT = "TOPS"
+N_INTEGRATIONS = 10
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+TRAFFIC_FILE = os.path.join(PROFILE_DIR, "traffic.json")
+MAIN_KERNEL_SOURCES = ["paper_1107_4264_gb300/csrc/xc_tc.cu", "paper_1107_4264_gb300/csrc/xc_ptx.cuh"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["xc", "reference"], default="xc")
+    ap.add_argument("--comparator-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-channels", type=int, default=0,
+                    help="channels in the CPU-baseline sample (default: 8 per host core)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    describes the current kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != source_sha(MAIN_KERNEL_SOURCES):
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9], float(parts[3])))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[3] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return "0"
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_oracle_sample(x_cpu_chans, w, channels):
+    """Time the CPU oracle, as it stands, on `channels` channels of one
+    integration.  Returns (seconds, ops, threads)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_num_threads(threads)
+    t0 = time.perf_counter()
+    oracle.correlate_i8(x_cpu_chans)
+    dt = time.perf_counter() - t0
+    ops = w.useful_ops // w.nfreq * channels
+    return dt, ops, oracle.num_threads()
+
+
+# --------------------------------------------------------------- reference
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on the host cores, same workload, metric
+    and unit; each step is a bounded sample of channels of one integration."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_1107_4264_gb300 import synth
+
+    oracle.build()
+    w = synth.LARGE_N
+    cores = os.cpu_count() or 1
+    nchan = args.cpu_channels or cores
+    x = synth.large_n_input(w, 0, device="cpu")
+    chans = list(range(nchan))
+    xs = x[:, chans].contiguous().numpy()
+    for _ in range(args.warmup):
+        cpu_oracle_sample(xs, w, nchan)
+    t_tot, ops_tot, thr = 0.0, 0, 1
+    for _ in range(args.steps):
+        dt, ops, thr = cpu_oracle_sample(xs, w, nchan)
+        t_tot += dt
+        ops_tot += ops
+    value = ops_tot / t_tot / 1e12
+    sample = "%d of %d channels of one integration per step (N=256 x 2 pols, T=1000)" % (nchan, w.nfreq)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nstation": w.nstation, "npol": w.npol, "nfreq": w.nfreq,
+                   "ntime": w.ntime, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": sample, "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- ours
+
+
+def run_xc(args):
+    import torch
+
+    from paper_1107_4264_gb300 import build as engine_build
+    from paper_1107_4264_gb300 import synth, xc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        engine_build.build()
+    if dist:
+        dist.barrier()
+    xc.load()
+
+    w = synth.LARGE_N
+    nint = N_INTEGRATIONS
+    peaks, peaks_kind = load_peaks()
+
+    # Inputs resident in HBM: this rank's 10 integrations (1.05 GB each).
+    xs = torch.empty((nint,) + w.shape, dtype=torch.int8, device=dev)
+    for i in range(nint):
+        synth.large_n_input(w, integration=rank * nint + i, device=dev, out=xs[i])
+    outs = torch.empty((nint,) + w.out_shape, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "int8", engine=xc.XC_ENGINE_TENSOR)
+    eng.set_option(xc.XC_OPT_PROFILE, 1)
+
+    def step():
+        for i in range(nint):
+            eng.correlate(xs[i], out=outs[i], stream=stream)
+
+    def timed(fn, k):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    eng.synchronize(stream)
+    eng.kernel_times(reset=True)
+
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    sampler.start()
+    ms = timed(step, args.steps)
+    clocks = sampler.stop()
+    eng.synchronize(stream)
+    (form_ms, main_ms), (n_form, n_main) = eng.kernel_times(reset=True)
+
+    ops_int = w.useful_ops  # per integration
+    total_units = world * args.steps * nint
+    value = total_units * ops_int / (ms * 1e-3) / 1e12
+    ms_step = ms / args.steps
+
+    # Roofline of the dominant kernel (the tensor-core X-engine), live events.
+    main_s = main_ms * 1e-3 / max(n_main, 1)
+    form_s = form_ms * 1e-3 / max(n_form, 1)
+    achieved = ops_int / main_s / 1e12
+    long_region = ms * 1e-3 > 1.0
+    peak = peaks["bf16_tflops_sustained"] if long_region else peaks["bf16_tflops"]
+    peak_note = ("%s bf16 dense %s (fp16 dense has the same nominal rate, ratio 1.0)"
+                 % (peaks_kind, "sustained" if long_region else "burst"))
+    n_rows = 2 * w.npol * w.nstation
+    nb = (n_rows + 127) // 128
+    executed_ops = 2 * (nb * (nb + 1) // 2) * 128 * 128 * ((w.ntime + 63) // 64 * 64) * w.nfreq
+    roofline = {
+        "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "frac": achieved / peak, "traffic": traffic_for("tc_xengine_kernel"),
+        "kernel": "tc_xengine_kernel<int> (tcgen05 kind::f16, 128x128 lower blocks)",
+        "peak_source": peak_note,
+        "kernel_ms": main_s * 1e3, "launches": n_main,
+        "executed_tflops": executed_ops / main_s / 1e12,
+        "form_kernel_ms": form_s * 1e3,
+        "form_kernel_gbs": (w.ntime * w.nfreq * n_rows + 2 * w.nfreq * n_rows * ((w.ntime + 63) // 64 * 64)) / form_s / 1e9,
+        "algorithmic_ops_per_launch": ops_int,
+    }
+    gpu_launches = n_form + n_main
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+        "data": "synthetic",
+        "config": {
+            "workload": w.name, "nstation": w.nstation, "npol": w.npol, "nfreq": w.nfreq,
+            "ntime": w.ntime, "integrations_per_step": nint, "input": "complex int8 [T][F][N][P][2]",
+            "output": "int32 [F][N(N+1)/2][4][2], bit-exact",
+            "arithmetic": "int8 exact in fp16, tcgen05 fp32 accumulation, int32 drain every 1024 samples",
+            "l2": "inputs larger than L2 (1.05 GB per integration, 10.5 GB per step)",
+            "ops_convention": "8 ops per CMAC, one CMAC per stored (baseline, pol product) per sample",
+            "eq_flops_tops": value * (2 * w.nstation + 1) / (2 * (w.nstation + 1)),
+            "parallelism": "replicas (each rank its own integrations)" if world > 1 else "1 GPU",
+        },
+        "roofline": roofline,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+
+    # Same-GPU comparator: plain FP32 CUDA-core X-engine on the same inputs.
+    if not args.no_comparator:
+        eng.set_option(xc.XC_OPT_ENGINE, xc.XC_ENGINE_FP32)
+        step()
+        eng.synchronize(stream)
+        eng.kernel_times(reset=True)
+        cms = timed(step, args.comparator_steps)
+        eng.synchronize(stream)
+        (_, fp32_ms), (_, n_fp32) = eng.kernel_times(reset=True)
+        eng.set_option(xc.XC_OPT_ENGINE, xc.XC_ENGINE_TENSOR)
+        cvalue = world * args.comparator_steps * nint * ops_int / (cms * 1e-3) / 1e12
+        props = torch.cuda.get_device_properties(dev)
+        sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+        fp32_peak_max = props.multi_processor_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        result["comparator_fp32"] = {
+            "value": cvalue, "unit": UNIT, "kernel_ms": fp32_ms / max(n_fp32, 1),
+            "fp32_peak_tflops_at_median_clock": fp32_peak, "fp32_peak_tflops_at_max_clock": fp32_peak_max,
+            "frac_of_fp32_peak": cvalue / fp32_peak,
+            "tensor_speedup": value / cvalue,
+        }
+        result["gpu_launches_comparator"] = n_fp32
+
+    # End to end through the public streamed call: pinned host in and out.
+    if not args.no_e2e:
+        host_in = torch.empty((nint,) + w.shape, dtype=torch.int8, pin_memory=True)
+        host_in.copy_(xs)
+        host_out = torch.empty((nint,) + w.out_shape, dtype=torch.int32, pin_memory=True)
+        torch.cuda.synchronize(dev)
+
+        def e2e_step():
+            eng.correlate_stream(host_in, nint, outs, host_out=host_out, stream=stream)
+
+        e2e_step()
+        eng.synchronize(stream)
+        ems = timed(e2e_step, args.e2e_steps)
+        eng.synchronize(stream)
+        eng.kernel_times(reset=True)
+        result["e2e"] = {
+            "value": world * args.e2e_steps * nint * ops_int / (ems * 1e-3) / 1e12, "unit": UNIT,
+            "h2d_bytes_per_step": host_in.numel(), "d2h_bytes_per_step": host_out.numel() * 4,
+            "ms_per_step": ems / args.e2e_steps,
+            "h2d_gbs": host_in.numel() * args.e2e_steps / (ems * 1e-3) / 1e9,
+        }
+        del host_in, host_out
+
+    # CPU baseline: the oracle as it stands, bounded sample, rank 0 at N=1.
+    if not args.no_cpu_baseline and world == 1 and rank == 0:
+        cores = os.cpu_count() or 1
+        nchan = args.cpu_channels or 8 * cores
+        nchan = min(nchan, w.nfreq)
+        xs_cpu = xs[0][:, :nchan].contiguous().cpu().numpy()
+        dt, ops, thr = cpu_oracle_sample(xs_cpu, w, nchan)
+        result["cpu_baseline"] = {
+            "value": ops / dt / 1e12, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": "%d of %d channels of integration 0 (N=256 x 2 pols, T=1000), %.1f s"
+                      % (nchan, w.nfreq, dt),
+            "cpu": cpu_model(),
+        }
+
+    eng.close()
+    if rank == 0:
+        print(json.dumps(result))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_xc(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

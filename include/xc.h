@@ -1,0 +1,199 @@
+/*
+ * xc.h -- C ABI of the GB300 (sm_103a) X-engine.
+ *
+ * The X-engine is the cross-multiply stage of an FX correlator (Clark,
+ * La Plante & Greenhill, Sec. 2.1): for every frequency channel f it
+ * accumulates, over an integration of T samples, the self outer products of
+ * the station signal vector (Eq. outer),
+ *
+ *     V_f[a][b] = sum_{t<T} x_f(t)[a] * conj(x_f(t)[b]),
+ *
+ * where a = s*P + p runs over N stations times P polarisations (dual
+ * polarisation, Sec. 2.1).  V_f is Hermitian, so only the lower triangle of
+ * station pairs is produced: N(N+1)/2 baselines (autocorrelations included),
+ * each with all P*P polarisation products.
+ *
+ * LAYOUTS (all arrays dense, row-major, no padding)
+ *   input   in [T][F][N][P][2]  -- corner-turned order of Sec. 4.1: station
+ *           fastest, then channel, then time; {re, im} interleaved.
+ *           Element type from xc_dtype: int8 (XC_CI8, Sec. 5 8-bit input),
+ *           IEEE fp16 (XC_CF16) or fp32 (XC_CF32).
+ *   output  out[F][N(N+1)/2][P*P][2] -- baseline k(s1,s2) = s1(s1+1)/2 + s2
+ *           for 0 <= s2 <= s1 < N (the lower-triangle block order of
+ *           Sec. 4.2), polarisation product index p1*P + p2, {re, im}:
+ *             out[f][k(s1,s2)][p1*P+p2] = sum_t x[t][f][s1][p1] * conj(x[t][f][s2][p2]).
+ *           Element type: int32 for XC_CI8 input (exact integer sums),
+ *           fp32 for float input.  Diagonal baselines hold all P*P products
+ *           (the yx product is the conjugate of xy).
+ *
+ * MEMORY AND OWNERSHIP
+ *   Every data pointer passed to a call is owned by the caller.  Device
+ *   pointers must be device memory of the handle's device, 16-byte aligned.
+ *   The handle owns its workspace (allocated at xc_create), its streams and
+ *   events, and its device status word.
+ *
+ * STREAMS
+ *   `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are stream-ordered and asynchronous: they return once
+ *   the work is queued.  A handle may be used by one host thread at a time,
+ *   and one call's work must finish before another call on the same handle
+ *   starts on a different stream (the workspace is shared).
+ *
+ * ERRORS
+ *   Calls return an xc_status; nothing aborts the process.  The status of
+ *   the last call on this thread is kept in xc_last_error(), with a message
+ *   in xc_last_error_message().  Kernel-side failures (a bounded wait that
+ *   ran out) are recorded in the handle's device status word and reported
+ *   by xc_synchronize() as XC_ERR_TIMEOUT.
+ */
+#ifndef XC_H
+#define XC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xc_handle xc_handle; /* opaque, owned by the library */
+
+/* Input sample type; samples are complex, {re, im} interleaved. */
+typedef enum {
+  XC_CI8 = 0,  /* two's-complement 8-bit integers (Sec. 5) */
+  XC_CF16 = 1, /* IEEE half */
+  XC_CF32 = 2  /* IEEE single */
+} xc_dtype;
+
+typedef enum {
+  XC_OK = 0,
+  XC_ERR_INVALID_ARG = 1,   /* NULL pointer, a size <= 0, npol not 1 or 2, bad option */
+  XC_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  XC_ERR_OVERFLOW_RISK = 3, /* XC_CI8 with ntime > XC_CI8_MAX_NTIME */
+  XC_ERR_ALIGNMENT = 4,     /* a device pointer not 16-byte aligned */
+  XC_ERR_CUDA = 5,          /* a CUDA runtime/driver call failed */
+  XC_ERR_TIMEOUT = 6,       /* a kernel's bounded wait ran out */
+  XC_ERR_OOM = 7,           /* device or pinned allocation failed */
+  XC_ERR_NO_DEVICE = 8      /* no CUDA device, or not an sm_103 device */
+} xc_status;
+
+/*
+ * Largest ntime accepted for XC_CI8: every visibility component is a sum of
+ * 2T products of magnitude <= 128*128, and must fit int32
+ * (T * 2 * 127^2 < 2^31 for the symmetric range used by the paper's 8-bit
+ * samples).  Longer integrations are split by the caller into several calls
+ * (see XC_OPT_ACCUMULATE), with int32 range their responsibility.
+ */
+#define XC_CI8_MAX_NTIME 66572
+
+/*
+ * Create an engine for fixed sizes on the current CUDA device.
+ *   nstation N >= 1, npol P in {1, 2}, nfreq F >= 1, ntime T >= 1.
+ * Allocates the workspace (an fp16 copy of one integration's operands plus a
+ * status word).  Returns NULL on error; the reason is in xc_last_error().
+ */
+xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_dtype);
+
+/*
+ * One integration (Eq. outer over T samples for all F channels).
+ *   in  : device, layout and type above, T*F*N*P*2 elements.
+ *   out : device, F*N(N+1)/2*P*P*2 elements of int32 (XC_CI8) or fp32.
+ *         Overwritten, or added to when XC_OPT_ACCUMULATE is 1 (the
+ *         chunked integration of Sec. 5, Algorithm 1).
+ * Stream-ordered on `stream`.
+ */
+xc_status xc_correlate(xc_handle* h, const void* in, void* out, void* stream);
+
+/*
+ * Adjoint of xc_correlate for float input (the paper has no adjoint; this is
+ * the differentiable form of the engine).  With G the dense P*N x P*N matrix
+ * holding grad_out on the stored (lower-triangle) entries and zero elsewhere,
+ * H = G + G^H and y = g*x (gains, unit unless set):
+ *     grad_in[t][f] = conj(g) * (H_f y_f(t)).
+ *   grad_out: device fp32, layout of `out`; grad_in: device fp32, layout of
+ *   `in`.  Returns XC_ERR_UNSUPPORTED for XC_CI8 handles.
+ */
+xc_status xc_correlate_backward(xc_handle* h, const void* grad_out, const void* in, void* grad_in,
+                                void* stream);
+
+/* Free a handle (NULL-safe).  Synchronises the handle's own streams first. */
+void xc_destroy(xc_handle* h);
+
+/* ------------------------------------------------------------- extensions */
+
+/* Status of the last call made on this host thread. */
+xc_status xc_last_error(void);
+/* Human-readable message of the last error on this host thread. */
+const char* xc_last_error_message(void);
+/* Static name of a status code. */
+const char* xc_status_string(xc_status s);
+
+/* Option keys for xc_set_option. */
+enum {
+  XC_OPT_ENGINE = 1,     /* XC_ENGINE_TENSOR (default) or XC_ENGINE_FP32 */
+  XC_OPT_ACCUMULATE = 2, /* 0: out = V (default); 1: out += V */
+  XC_OPT_TIMEOUT_MS = 3, /* bound on any in-kernel wait, milliseconds (default 2000) */
+  XC_OPT_PROFILE = 4     /* 1: time every kernel with CUDA events (see xc_kernel_times) */
+};
+/* Engines: the tcgen05 tensor-core path, or the plain FP32 CUDA-core form
+ * of the same X-engine (register tile over a shared-memory double buffer,
+ * after the paper's kernel 11, Sec. 4.4), kept as the same-GPU comparator. */
+enum { XC_ENGINE_TENSOR = 0, XC_ENGINE_FP32 = 1 };
+
+xc_status xc_set_option(xc_handle* h, int key, long long value);
+
+/*
+ * Wait for `stream`, then read and clear the handle's device status word.
+ * Returns XC_ERR_TIMEOUT if a kernel gave up on a bounded wait since the
+ * last check, XC_ERR_CUDA on a CUDA error, else XC_OK.
+ */
+xc_status xc_synchronize(xc_handle* h, void* stream);
+
+/*
+ * Integrated pipeline (Sec. 5, Algorithm 1): n_integrations consecutive
+ * integrations stored back to back in pinned host memory are copied to the
+ * device through two staging buffers on a side copy stream, each copy
+ * overlapping the correlation of the previous integration on `stream`.
+ *   host_in : pinned host memory, n_integrations * (T*F*N*P*2) samples.
+ *   out     : device.  With XC_OPT_ACCUMULATE = 0 it holds n_integrations
+ *             outputs back to back (one per integration); with 1, a single
+ *             output that all integrations are added into (Algorithm 1).
+ *   host_out: optional pinned host memory of the same size as `out`; when
+ *             not NULL each integration's output is also copied back on a
+ *             second side stream once computed.
+ * Stream-ordered on `stream`: returns once all work is queued.
+ */
+xc_status xc_correlate_stream(xc_handle* h, const void* host_in, int n_integrations, void* out,
+                              void* host_out, void* stream);
+
+/*
+ * Kernel timing, for profiling runs (XC_OPT_PROFILE = 1).  While enabled,
+ * every launch is bracketed by CUDA events recorded on the launching stream.
+ * This call waits for those events and returns, per kernel class, the summed
+ * device time in milliseconds and the number of launches since the last
+ * reset:  index 0 = operand formation, 1 = X-engine kernel (tensor-core or
+ * FP32).  ms and launches each point to 2 elements (either may be NULL).
+ */
+xc_status xc_kernel_times(xc_handle* h, double* ms, long long* launches, int reset);
+
+/* Sizes (bytes) of one integration's input and output. */
+size_t xc_input_bytes(const xc_handle* h);
+size_t xc_output_bytes(const xc_handle* h);
+
+/*
+ * Lower-triangle block map of Sec. 4.2: block (bx, by), 0 <= bx <= by, has
+ * linear index g = by(by+1)/2 + bx.  xc_tri_coords inverts it with the
+ * paper's b_y = floor(-1/2 + sqrt(1/4 + 2g)), corrected to exact integers.
+ * Host-side helpers (no device work), exposed for tests and schedulers.
+ */
+int64_t xc_tri_index(int64_t bx, int64_t by);
+void xc_tri_coords(int64_t g, int64_t* bx, int64_t* by);
+
+/* Library version string. */
+const char* xc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XC_H */

@@ -1,0 +1,475 @@
+// xc_api.cpp -- the C ABI of include/xc.h: handle life cycle, argument
+// checks, the TMA descriptor of the operand workspace, kernel dispatch and
+// the integrated host->device pipeline of Sec. 5 (Algorithm 1).
+#include "xc.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "xc_internal.h"
+#include "xc_launch.h"
+
+namespace {
+
+thread_local xc_status t_status = XC_OK;
+thread_local char t_msg[512] = "";
+
+xc_status fail(xc_status s, const char* fmt, ...) {
+  t_status = s;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_msg, sizeof(t_msg), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+xc_status succeed() {
+  t_status = XC_OK;
+  t_msg[0] = '\0';
+  return XC_OK;
+}
+
+xc_status cuda_fail(cudaError_t e, const char* what) {
+  (void)cudaGetLastError();  // clear a sticky launch error for the next call
+  if (e == cudaErrorMemoryAllocation) return fail(XC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(XC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+constexpr int kKBlock = 64;  // operand K-block (samples) of the tensor-core engine
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t sample_bytes(xc_dtype d) { return d == XC_CI8 ? 1 : (d == XC_CF16 ? 2 : 4); }
+
+}  // namespace
+
+struct xc_handle {
+  int device = 0;
+  xc::Geometry g{};
+  xc_dtype dtype = XC_CI8;
+  size_t in_bytes = 0, out_bytes = 0;
+  int engine = XC_ENGINE_TENSOR;
+  int accumulate = 0;
+  unsigned long long timeout_ns = 2000ull * 1000000ull;
+  int num_sms = 0;
+  void* ws = nullptr;  // fp16 operands [F][R][Tp]
+  int* d_status = nullptr;
+  CUtensorMap tmap;
+  // Integrated pipeline (allocated on first use).
+  void* stage[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
+  cudaEvent_t ev_ready[2] = {nullptr, nullptr};
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr, ev_computed = nullptr, ev_d2h = nullptr;
+  // Kernel timing (XC_OPT_PROFILE): events bracketing each launch.
+  int profile = 0;
+  struct Timed {
+    cudaEvent_t ev[3];
+    int nkern;  // 1: main kernel only (FP32 engine); 2: formation + main
+  };
+  std::vector<Timed> timed;
+  size_t timed_used = 0;
+  double acc_ms[2] = {0.0, 0.0};
+  long long acc_launches[2] = {0, 0};
+};
+
+namespace {
+
+void release(xc_handle* h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  for (auto& t : h->timed)
+    for (int i = 0; i < 3; ++i)
+      if (t.ev[i]) {
+        cudaEventSynchronize(t.ev[i]);
+        cudaEventDestroy(t.ev[i]);
+      }
+  if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+  if (h->d2h_stream) cudaStreamSynchronize(h->d2h_stream);
+  for (int b = 0; b < 2; ++b) {
+    if (h->stage[b]) cudaFree(h->stage[b]);
+    if (h->ev_ready[b]) cudaEventDestroy(h->ev_ready[b]);
+    if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
+  }
+  if (h->ev_start) cudaEventDestroy(h->ev_start);
+  if (h->ev_computed) cudaEventDestroy(h->ev_computed);
+  if (h->ev_d2h) cudaEventDestroy(h->ev_d2h);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
+  if (h->ws || h->d_status) cudaDeviceSynchronize();
+  if (h->ws) cudaFree(h->ws);
+  if (h->d_status) cudaFree(h->d_status);
+  cudaSetDevice(cur);
+  delete h;
+}
+
+// Events for one timed launch (reused from the handle's pool).
+xc_handle::Timed* next_timed(xc_handle* h, int nkern) {
+  if (h->timed_used == h->timed.size()) {
+    xc_handle::Timed t{};
+    for (int i = 0; i < 3; ++i)
+      if (cudaEventCreate(&t.ev[i]) != cudaSuccess) return nullptr;
+    h->timed.push_back(t);
+  }
+  xc_handle::Timed* t = &h->timed[h->timed_used++];
+  t->nkern = nkern;
+  return t;
+}
+
+xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
+  cudaError_t e;
+  xc_handle::Timed* tm = nullptr;
+  if (h->profile) {
+    tm = next_timed(h, h->engine == XC_ENGINE_FP32 ? 1 : 2);
+    if (!tm) return fail(XC_ERR_CUDA, "profiling event creation failed");
+    cudaEventRecord(tm->ev[0], s);
+  }
+  if (h->engine == XC_ENGINE_FP32) {
+    e = xc::launch_fp32_xengine(in, static_cast<int>(h->dtype), out, h->g, h->accumulate, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fp32 X-engine launch");
+    if (tm) cudaEventRecord(tm->ev[1], s);
+    return succeed();
+  }
+  e = xc::launch_form_operands(in, static_cast<int>(h->dtype), h->ws, h->g, s);
+  if (e != cudaSuccess) return cuda_fail(e, "operand formation launch");
+  if (tm) cudaEventRecord(tm->ev[1], s);
+  xc::TcLaunch L;
+  L.g = h->g;
+  L.out = out;
+  L.is_int = h->dtype == XC_CI8 ? 1 : 0;
+  L.accumulate = h->accumulate;
+  L.grid = h->num_sms;
+  L.timeout_ns = h->timeout_ns;
+  L.status = h->d_status;
+  e = xc::launch_tc_xengine(&h->tmap, L, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core X-engine launch");
+  if (tm) cudaEventRecord(tm->ev[2], s);
+  return succeed();
+}
+
+}  // namespace
+
+extern "C" {
+
+xc_status xc_last_error(void) { return t_status; }
+
+const char* xc_last_error_message(void) { return t_msg; }
+
+const char* xc_status_string(xc_status s) {
+  switch (s) {
+    case XC_OK: return "XC_OK";
+    case XC_ERR_INVALID_ARG: return "XC_ERR_INVALID_ARG";
+    case XC_ERR_UNSUPPORTED: return "XC_ERR_UNSUPPORTED";
+    case XC_ERR_OVERFLOW_RISK: return "XC_ERR_OVERFLOW_RISK";
+    case XC_ERR_ALIGNMENT: return "XC_ERR_ALIGNMENT";
+    case XC_ERR_CUDA: return "XC_ERR_CUDA";
+    case XC_ERR_TIMEOUT: return "XC_ERR_TIMEOUT";
+    case XC_ERR_OOM: return "XC_ERR_OOM";
+    case XC_ERR_NO_DEVICE: return "XC_ERR_NO_DEVICE";
+  }
+  return "XC_ERR_UNKNOWN";
+}
+
+const char* xc_version(void) { return "xc 0.1 (sm_103a)"; }
+
+int64_t xc_tri_index(int64_t bx, int64_t by) { return xc::tri_index(bx, by); }
+
+void xc_tri_coords(int64_t g, int64_t* bx, int64_t* by) {
+  int64_t x = 0, y = 0;
+  xc::tri_coords(g, &x, &y);
+  if (bx) *bx = x;
+  if (by) *by = y;
+}
+
+size_t xc_input_bytes(const xc_handle* h) { return h ? h->in_bytes : 0; }
+size_t xc_output_bytes(const xc_handle* h) { return h ? h->out_bytes : 0; }
+
+xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_dtype) {
+  if (nstation <= 0 || nfreq <= 0 || ntime <= 0) {
+    fail(XC_ERR_INVALID_ARG, "sizes must be positive (nstation=%d nfreq=%d ntime=%d)", nstation,
+         nfreq, ntime);
+    return nullptr;
+  }
+  if (npol != 1 && npol != 2) {
+    fail(XC_ERR_INVALID_ARG, "npol must be 1 or 2 (got %d)", npol);
+    return nullptr;
+  }
+  if (in_dtype != XC_CI8 && in_dtype != XC_CF16 && in_dtype != XC_CF32) {
+    fail(XC_ERR_INVALID_ARG, "unknown input dtype %d", static_cast<int>(in_dtype));
+    return nullptr;
+  }
+  if (in_dtype == XC_CI8 && ntime > XC_CI8_MAX_NTIME) {
+    fail(XC_ERR_OVERFLOW_RISK, "8-bit input with ntime=%d > %d can overflow int32 visibilities",
+         ntime, XC_CI8_MAX_NTIME);
+    return nullptr;
+  }
+  if (nfreq > 65535) {
+    fail(XC_ERR_UNSUPPORTED, "nfreq=%d > 65535 (split the band across handles)", nfreq);
+    return nullptr;
+  }
+  const int64_t R = 2LL * npol * nstation;
+  const int64_t Tp = (static_cast<int64_t>(ntime) + kKBlock - 1) / kKBlock * kKBlock;
+  if (R > (1LL << 30) || Tp / kKBlock > 65535) {
+    fail(XC_ERR_UNSUPPORTED, "problem too large (rows=%lld, ntime=%d)", static_cast<long long>(R),
+         ntime);
+    return nullptr;
+  }
+
+  int dev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    (void)cudaGetLastError();
+    fail(XC_ERR_NO_DEVICE, "no CUDA device");
+    return nullptr;
+  }
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "cudaGetDeviceProperties");
+    return nullptr;
+  }
+  if (!(prop.major == 10 && prop.minor == 3)) {
+    fail(XC_ERR_NO_DEVICE, "device %d is sm_%d%d; this library is built for sm_103a only", dev,
+         prop.major, prop.minor);
+    return nullptr;
+  }
+
+  xc_handle* h = new (std::nothrow) xc_handle();
+  if (!h) {
+    fail(XC_ERR_OOM, "host allocation failed");
+    return nullptr;
+  }
+  h->device = dev;
+  h->dtype = in_dtype;
+  h->num_sms = prop.multiProcessorCount;
+  h->g.N = nstation;
+  h->g.P = npol;
+  h->g.F = nfreq;
+  h->g.T = ntime;
+  h->g.R = static_cast<int>(R);
+  h->g.Tp = static_cast<int>(Tp);
+  h->g.NB = static_cast<int64_t>(nstation) * (nstation + 1) / 2;
+  h->in_bytes = static_cast<size_t>(ntime) * nfreq * nstation * npol * 2 * sample_bytes(in_dtype);
+  h->out_bytes = static_cast<size_t>(nfreq) * h->g.NB * npol * npol * 2 * 4;
+
+  const size_t ws_bytes = static_cast<size_t>(nfreq) * R * Tp * 2;
+  e = cudaMalloc(&h->ws, ws_bytes);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "workspace allocation");
+    release(h);
+    return nullptr;
+  }
+  e = cudaMalloc(reinterpret_cast<void**>(&h->d_status), sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cuda_fail(e, "status word");
+    release(h);
+    return nullptr;
+  }
+
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) {
+    fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+    release(h);
+    return nullptr;
+  }
+  // Operand workspace as a 3-D tensor {t (Tp), row (R), channel (F)} of fp16,
+  // loaded in boxes of 64 samples x 128 rows x 1 channel with 128-byte swizzle.
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(Tp), static_cast<cuuint64_t>(R),
+                              static_cast<cuuint64_t>(nfreq)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(Tp) * 2,
+                                 static_cast<cuuint64_t>(R) * Tp * 2};
+  const cuuint32_t box[3] = {64, 128, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult cr = enc(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, h->ws, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(cr));
+    release(h);
+    return nullptr;
+  }
+  succeed();
+  return h;
+}
+
+void xc_destroy(xc_handle* h) {
+  release(h);
+  succeed();
+}
+
+xc_status xc_set_option(xc_handle* h, int key, long long value) {
+  if (!h) return fail(XC_ERR_INVALID_ARG, "NULL handle");
+  switch (key) {
+    case XC_OPT_ENGINE:
+      if (value != XC_ENGINE_TENSOR && value != XC_ENGINE_FP32)
+        return fail(XC_ERR_INVALID_ARG, "unknown engine %lld", value);
+      h->engine = static_cast<int>(value);
+      return succeed();
+    case XC_OPT_ACCUMULATE:
+      if (value != 0 && value != 1) return fail(XC_ERR_INVALID_ARG, "ACCUMULATE must be 0 or 1");
+      h->accumulate = static_cast<int>(value);
+      return succeed();
+    case XC_OPT_PROFILE:
+      if (value != 0 && value != 1) return fail(XC_ERR_INVALID_ARG, "PROFILE must be 0 or 1");
+      h->profile = static_cast<int>(value);
+      return succeed();
+    case XC_OPT_TIMEOUT_MS:
+      if (value <= 0 || value > 3600LL * 1000) return fail(XC_ERR_INVALID_ARG, "bad timeout");
+      h->timeout_ns = static_cast<unsigned long long>(value) * 1000000ull;
+      return succeed();
+    default:
+      return fail(XC_ERR_INVALID_ARG, "unknown option key %d", key);
+  }
+}
+
+xc_status xc_correlate(xc_handle* h, const void* in, void* out, void* stream) {
+  if (!h || !in || !out) return fail(XC_ERR_INVALID_ARG, "NULL handle or buffer");
+  if (!aligned16(in) || !aligned16(out))
+    return fail(XC_ERR_ALIGNMENT, "input and output must be 16-byte aligned");
+  return launch_one(h, in, out, static_cast<cudaStream_t>(stream));
+}
+
+xc_status xc_correlate_backward(xc_handle* h, const void* grad_out, const void* in, void* grad_in,
+                                void* stream) {
+  (void)stream;
+  if (!h || !grad_out || !in || !grad_in) return fail(XC_ERR_INVALID_ARG, "NULL handle or buffer");
+  if (h->dtype == XC_CI8) return fail(XC_ERR_UNSUPPORTED, "backward needs float input");
+  return fail(XC_ERR_UNSUPPORTED, "backward is not built in this version");
+}
+
+xc_status xc_kernel_times(xc_handle* h, double* ms, long long* launches, int reset) {
+  if (!h) return fail(XC_ERR_INVALID_ARG, "NULL handle");
+  for (size_t i = 0; i < h->timed_used; ++i) {
+    const xc_handle::Timed& t = h->timed[i];
+    cudaError_t e = cudaEventSynchronize(t.ev[t.nkern]);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel timing");
+    float a = 0.f, b = 0.f;
+    if (t.nkern == 1) {
+      cudaEventElapsedTime(&b, t.ev[0], t.ev[1]);
+    } else {
+      cudaEventElapsedTime(&a, t.ev[0], t.ev[1]);
+      cudaEventElapsedTime(&b, t.ev[1], t.ev[2]);
+      h->acc_ms[0] += a;
+      h->acc_launches[0] += 1;
+    }
+    h->acc_ms[1] += b;
+    h->acc_launches[1] += 1;
+  }
+  h->timed_used = 0;
+  for (int k = 0; k < 2; ++k) {
+    if (ms) ms[k] = h->acc_ms[k];
+    if (launches) launches[k] = h->acc_launches[k];
+    if (reset) {
+      h->acc_ms[k] = 0.0;
+      h->acc_launches[k] = 0;
+    }
+  }
+  return succeed();
+}
+
+xc_status xc_synchronize(xc_handle* h, void* stream) {
+  if (!h) return fail(XC_ERR_INVALID_ARG, "NULL handle");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  if (st != 0) {
+    e = cudaMemsetAsync(h->d_status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "status reset");
+    if (st & xc::kStatusTimeout)
+      return fail(XC_ERR_TIMEOUT, "a kernel gave up on a bounded wait (status 0x%x)", st);
+    return fail(XC_ERR_CUDA, "device status 0x%x", st);
+  }
+  return succeed();
+}
+
+xc_status xc_correlate_stream(xc_handle* h, const void* host_in, int n_integrations, void* out,
+                              void* host_out, void* stream) {
+  if (!h || !host_in || !out) return fail(XC_ERR_INVALID_ARG, "NULL handle or buffer");
+  if (n_integrations < 0) return fail(XC_ERR_INVALID_ARG, "n_integrations < 0");
+  if (!aligned16(out)) return fail(XC_ERR_ALIGNMENT, "output must be 16-byte aligned");
+  if (n_integrations == 0) return succeed();
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (!h->copy_stream) {
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaMalloc(&h->stage[b], h->in_bytes);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_ready[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_computed, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_d2h, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline set-up");
+  }
+  const char* src = static_cast<const char*>(host_in);
+  char* dst = static_cast<char*>(out);
+  char* hdst = static_cast<char*>(host_out);
+  // The staging buffers may still be read by work queued earlier on `stream`.
+  e = cudaEventRecord(h->ev_start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->ev_start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h_stream, h->ev_start, 0);
+  for (int i = 0; i < n_integrations && e == cudaSuccess; ++i) {
+    const int b = i & 1;
+    // H2D of integration i into buffer b once the correlation of i-2 has read it.
+    if (i >= 2) e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->stage[b], src + static_cast<size_t>(i) * h->in_bytes, h->in_bytes,
+                          cudaMemcpyHostToDevice, h->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_ready[b], h->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_ready[b], 0);
+    if (e != cudaSuccess) break;
+    char* o = h->accumulate ? dst : dst + static_cast<size_t>(i) * h->out_bytes;
+    xc_status st = launch_one(h, h->stage[b], o, s);
+    if (st != XC_OK) return st;
+    e = cudaEventRecord(h->ev_free[b], s);
+    if (e == cudaSuccess && hdst && (!h->accumulate || i == n_integrations - 1)) {
+      e = cudaEventRecord(h->ev_computed, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h_stream, h->ev_computed, 0);
+      char* ho = h->accumulate ? hdst : hdst + static_cast<size_t>(i) * h->out_bytes;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ho, o, h->out_bytes, cudaMemcpyDeviceToHost, h->d2h_stream);
+    }
+  }
+  // Later work on `stream` is ordered after the copies of this call.
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_d2h, h->d2h_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_d2h, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "integrated pipeline");
+  return succeed();
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+"""Python binding of the C ABI in ``include/xc.h`` (ctypes; marshalling only).
+
+The functions carry the C names (``xc_create``, ``xc_correlate``, ...) and
+take raw pointers; :class:`Correlator` adds torch-tensor conveniences
+(allocation of outputs, the current CUDA stream) on top.  Every step of the
+X-engine runs in the library's CUDA kernels: there is no Python or CPU
+fallback, and a missing library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libxc.so")
+
+XC_CI8, XC_CF16, XC_CF32 = 0, 1, 2
+XC_OK = 0
+XC_ERR_INVALID_ARG = 1
+XC_ERR_UNSUPPORTED = 2
+XC_ERR_OVERFLOW_RISK = 3
+XC_ERR_ALIGNMENT = 4
+XC_ERR_CUDA = 5
+XC_ERR_TIMEOUT = 6
+XC_ERR_OOM = 7
+XC_ERR_NO_DEVICE = 8
+XC_OPT_ENGINE, XC_OPT_ACCUMULATE, XC_OPT_TIMEOUT_MS, XC_OPT_PROFILE = 1, 2, 3, 4
+XC_ENGINE_TENSOR, XC_ENGINE_FP32 = 0, 1
+XC_CI8_MAX_NTIME = 66572
+
+# Symbols declared in include/xc.h (checked by the tests against the header).
+EXPORTS = [
+    "xc_create", "xc_correlate", "xc_correlate_backward", "xc_destroy", "xc_last_error",
+    "xc_last_error_message", "xc_status_string", "xc_set_option", "xc_synchronize",
+    "xc_correlate_stream", "xc_input_bytes", "xc_output_bytes", "xc_tri_index", "xc_tri_coords",
+    "xc_version", "xc_kernel_times",
+]
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+class XcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (status_string(status) if _lib else status, message))
+        self.status = status
+
+
+def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "xc_create": ([i32, i32, i32, i32, i32], vp),
+        "xc_correlate": ([vp, vp, vp, vp], i32),
+        "xc_correlate_backward": ([vp, vp, vp, vp, vp], i32),
+        "xc_destroy": ([vp], None),
+        "xc_last_error": ([], i32),
+        "xc_last_error_message": ([], ctypes.c_char_p),
+        "xc_status_string": ([i32], ctypes.c_char_p),
+        "xc_set_option": ([vp, i32, ctypes.c_longlong], i32),
+        "xc_synchronize": ([vp, vp], i32),
+        "xc_correlate_stream": ([vp, vp, i32, vp, vp, vp], i32),
+        "xc_input_bytes": ([vp], sz),
+        "xc_output_bytes": ([vp], sz),
+        "xc_tri_index": ([i64, i64], i64),
+        "xc_tri_coords": ([i64, ctypes.POINTER(i64), ctypes.POINTER(i64)], None),
+        "xc_version": ([], ctypes.c_char_p),
+        "xc_kernel_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                             i32], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libxc.so (built by ``__graft_entry__.build()``).  Raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libxc.so is not built (%s); run __graft_entry__.build()" % path)
+        _lib = _bind(ctypes.CDLL(path))
+    return _lib
+
+
+def _check(status: int) -> int:
+    if status != XC_OK:
+        raise XcError(status, xc_last_error_message())
+    return status
+
+
+# ------------------------------------------------------------ C-named calls
+
+def xc_create(nstation: int, npol: int, nfreq: int, ntime: int, in_dtype: int) -> int:
+    h = load().xc_create(nstation, npol, nfreq, ntime, in_dtype)
+    if not h:
+        raise XcError(xc_last_error(), xc_last_error_message())
+    return h
+
+
+def xc_correlate(h: int, in_ptr: int, out_ptr: int, stream: int = 0) -> int:
+    return load().xc_correlate(h, in_ptr, out_ptr, stream)
+
+
+def xc_correlate_backward(h: int, grad_out_ptr: int, in_ptr: int, grad_in_ptr: int,
+                          stream: int = 0) -> int:
+    return load().xc_correlate_backward(h, grad_out_ptr, in_ptr, grad_in_ptr, stream)
+
+
+def xc_destroy(h: int) -> None:
+    load().xc_destroy(h)
+
+
+def xc_last_error() -> int:
+    return load().xc_last_error()
+
+
+def xc_last_error_message() -> str:
+    return load().xc_last_error_message().decode()
+
+
+def status_string(s: int) -> str:
+    return load().xc_status_string(s).decode()
+
+
+xc_status_string = status_string
+
+
+def xc_set_option(h: int, key: int, value: int) -> int:
+    return load().xc_set_option(h, key, value)
+
+
+def xc_synchronize(h: int, stream: int = 0) -> int:
+    return load().xc_synchronize(h, stream)
+
+
+def xc_correlate_stream(h: int, host_in_ptr: int, n_integrations: int, out_ptr: int,
+                        host_out_ptr: int = 0, stream: int = 0) -> int:
+    return load().xc_correlate_stream(h, host_in_ptr, n_integrations, out_ptr, host_out_ptr,
+                                      stream)
+
+
+def xc_input_bytes(h: int) -> int:
+    return load().xc_input_bytes(h)
+
+
+def xc_output_bytes(h: int) -> int:
+    return load().xc_output_bytes(h)
+
+
+def xc_tri_index(bx: int, by: int) -> int:
+    return load().xc_tri_index(bx, by)
+
+
+def xc_tri_coords(g: int):
+    bx, by = ctypes.c_int64(), ctypes.c_int64()
+    load().xc_tri_coords(g, ctypes.byref(bx), ctypes.byref(by))
+    return bx.value, by.value
+
+
+def xc_kernel_times(h: int, reset: bool = True):
+    """((formation_ms, main_ms), (formation_launches, main_launches))."""
+    ms = (ctypes.c_double * 2)()
+    n = (ctypes.c_longlong * 2)()
+    _check(load().xc_kernel_times(h, ms, n, int(reset)))
+    return (ms[0], ms[1]), (n[0], n[1])
+
+
+def xc_version() -> str:
+    return load().xc_version().decode()
+
+
+# ------------------------------------------------------ torch convenience
+
+_DTYPES = {"int8": XC_CI8, "float16": XC_CF16, "float32": XC_CF32}
+
+
+class Correlator:
+    """One engine for fixed (nstation, npol, nfreq, ntime, dtype).
+
+    Tensors: input ``[T][F][N][P][2]`` (int8 / float16 / float32) on the
+    handle's CUDA device; output ``[F][N(N+1)/2][P*P][2]`` int32 (int8 input)
+    or float32.
+    """
+
+    def __init__(self, nstation: int, npol: int, nfreq: int, ntime: int, dtype: str = "int8",
+                 engine: int = XC_ENGINE_TENSOR, accumulate: bool = False,
+                 timeout_ms: Optional[int] = None):
+        import torch
+        self._torch = torch
+        self.nstation, self.npol, self.nfreq, self.ntime = nstation, npol, nfreq, ntime
+        self.dtype = dtype
+        self.h = xc_create(nstation, npol, nfreq, ntime, _DTYPES[dtype])
+        self.set_option(XC_OPT_ENGINE, engine)
+        self.set_option(XC_OPT_ACCUMULATE, int(accumulate))
+        if timeout_ms is not None:
+            self.set_option(XC_OPT_TIMEOUT_MS, timeout_ms)
+
+    @property
+    def in_shape(self):
+        return (self.ntime, self.nfreq, self.nstation, self.npol, 2)
+
+    @property
+    def out_shape(self):
+        nb = self.nstation * (self.nstation + 1) // 2
+        return (self.nfreq, nb, self.npol * self.npol, 2)
+
+    @property
+    def out_dtype(self):
+        return self._torch.int32 if self.dtype == "int8" else self._torch.float32
+
+    def set_option(self, key: int, value: int) -> None:
+        _check(xc_set_option(self.h, key, int(value)))
+
+    def new_output(self, n: int = 1, device=None):
+        shape = self.out_shape if n == 1 else (n,) + self.out_shape
+        return self._torch.zeros(shape, dtype=self.out_dtype,
+                                 device=device or self._torch.device("cuda"))
+
+    def _stream(self, stream) -> int:
+        s = stream if stream is not None else self._torch.cuda.current_stream()
+        return s.cuda_stream
+
+    def correlate(self, x, out=None, stream=None, sync: bool = False):
+        assert x.is_cuda and x.is_contiguous() and tuple(x.shape) == self.in_shape, x.shape
+        if out is None:
+            out = self.new_output(device=x.device)
+        assert out.is_cuda and out.is_contiguous() and out.dtype == self.out_dtype
+        _check(xc_correlate(self.h, x.data_ptr(), out.data_ptr(), self._stream(stream)))
+        if sync:
+            self.synchronize(stream)
+        return out
+
+    def correlate_stream(self, host_in, n_integrations: int, out, host_out=None, stream=None):
+        assert host_in.is_contiguous() and not host_in.is_cuda
+        _check(xc_correlate_stream(self.h, host_in.data_ptr(), n_integrations, out.data_ptr(),
+                                   0 if host_out is None else host_out.data_ptr(),
+                                   self._stream(stream)))
+        return out
+
+    def kernel_times(self, reset: bool = True):
+        return xc_kernel_times(self.h, reset)
+
+    def synchronize(self, stream=None) -> None:
+        _check(xc_synchronize(self.h, self._stream(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            xc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

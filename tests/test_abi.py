@@ -1,0 +1,91 @@
+"""The C-ABI library: builds, loads without a GPU, exports every symbol that
+include/xc.h declares, validates arguments on the host, and its triangular
+block map (Sec. 4.2) round-trips exactly."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1107_4264_gb300 import build as engine_build
+from paper_1107_4264_gb300 import xc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    engine_build.build()
+    return xc.load()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "xc.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(xc_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(xc.EXPORTS) == names
+
+
+def test_version_and_status_strings(lib):
+    assert "sm_103a" in xc.xc_version()
+    assert xc.status_string(xc.XC_OK) == "XC_OK"
+    assert xc.status_string(xc.XC_ERR_TIMEOUT) == "XC_ERR_TIMEOUT"
+
+
+@pytest.mark.parametrize("args,status", [
+    ((0, 2, 8, 256, xc.XC_CI8), xc.XC_ERR_INVALID_ARG),
+    ((16, 3, 8, 256, xc.XC_CI8), xc.XC_ERR_INVALID_ARG),
+    ((16, 2, 0, 256, xc.XC_CI8), xc.XC_ERR_INVALID_ARG),
+    ((16, 2, 8, 0, xc.XC_CI8), xc.XC_ERR_INVALID_ARG),
+    ((16, 2, 8, 256, 7), xc.XC_ERR_INVALID_ARG),
+    ((16, 2, 8, xc.XC_CI8_MAX_NTIME + 1, xc.XC_CI8), xc.XC_ERR_OVERFLOW_RISK),
+    ((16, 2, 70000, 256, xc.XC_CI8), xc.XC_ERR_UNSUPPORTED),
+])
+def test_create_rejects_bad_arguments(lib, args, status):
+    h = lib.xc_create(*args)
+    assert not h
+    assert lib.xc_last_error() == status
+    assert lib.xc_last_error_message()
+
+
+def test_null_handle_calls(lib):
+    assert lib.xc_correlate(None, None, None, None) == xc.XC_ERR_INVALID_ARG
+    assert lib.xc_correlate_stream(None, None, 1, None, None, None) == xc.XC_ERR_INVALID_ARG
+    assert lib.xc_set_option(None, xc.XC_OPT_ENGINE, 0) == xc.XC_ERR_INVALID_ARG
+    assert lib.xc_synchronize(None, None) == xc.XC_ERR_INVALID_ARG
+    assert lib.xc_correlate_backward(None, None, None, None, None) == xc.XC_ERR_INVALID_ARG
+    assert lib.xc_input_bytes(None) == 0
+    lib.xc_destroy(None)  # NULL-safe
+
+
+def test_tri_map_round_trip_exhaustive(lib):
+    # every block of the lower triangle up to 4000 block rows (8e6 blocks)
+    n = 4000
+    by = np.repeat(np.arange(n, dtype=np.int64), np.arange(1, n + 1))
+    bx = np.arange(len(by), dtype=np.int64) - by * (by + 1) // 2
+    g = np.arange(len(by), dtype=np.int64)
+    assert (bx >= 0).all() and (bx <= by).all()
+    # forward map through the library on a sample, inverse on a dense prefix
+    for i in list(range(0, 20000)) + list(range(len(g) - 2000, len(g))):
+        assert lib.xc_tri_index(int(bx[i]), int(by[i])) == g[i]
+        assert xc.xc_tri_coords(int(g[i])) == (int(bx[i]), int(by[i]))
+
+
+def test_tri_map_boundaries(lib):
+    # first and last block of every row near 2^31 blocks, where a float
+    # square root without the integer correction can pick the wrong row
+    for y in list(range(0, 200)) + [65535, 65536, 92681, 92682, 2 ** 20, 3_000_000]:
+        first = y * (y + 1) // 2
+        assert xc.xc_tri_coords(first) == (0, y)
+        assert xc.xc_tri_coords(first + y) == (y, y)
+        if y:
+            assert xc.xc_tri_coords(first - 1) == (y - 1, y - 1)
