@@ -57,7 +57,11 @@ def parse_args():
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-channels", type=int, default=0,
-                    help="channels in the CPU-baseline sample (default: 8 per host core)")
+                    help="channels in the CPU-baseline sample (default: all 1024 of one integration)")
+    ap.add_argument("--nfreq", type=int, default=0,
+                    help="channels per integration (default 1024; smaller only for profiling captures)")
+    ap.add_argument("--integrations", type=int, default=N_INTEGRATIONS,
+                    help="integrations per step (default 10)")
     return ap.parse_args()
 
 
@@ -248,7 +252,10 @@ def run_xc(args):
     xc.load()
 
     w = synth.LARGE_N
-    nint = N_INTEGRATIONS
+    if args.nfreq:
+        w = synth.Workload(w.name.replace("F=1024", "F=%d" % args.nfreq), w.nstation, w.npol,
+                           args.nfreq, w.ntime, w.seed)
+    nint = args.integrations
     peaks, peaks_kind = load_peaks()
 
     # Inputs resident in HBM: this rank's 10 integrations (1.05 GB each).
@@ -336,7 +343,9 @@ def run_xc(args):
             "ntime": w.ntime, "integrations_per_step": nint, "input": "complex int8 [T][F][N][P][2]",
             "output": "int32 [F][N(N+1)/2][4][2], bit-exact",
             "arithmetic": "int8 exact in fp16, tcgen05 fp32 accumulation, int32 drain every 1024 samples",
-            "l2": "inputs larger than L2 (1.05 GB per integration, 10.5 GB per step)",
+            "l2": "inputs larger than L2 (%.2f GB per integration, %.1f GB per step)"
+                  % (w.ntime * w.nfreq * w.nstation * w.npol * 2 / 1e9,
+                     nint * w.ntime * w.nfreq * w.nstation * w.npol * 2 / 1e9),
             "ops_convention": "8 ops per CMAC, one CMAC per stored (baseline, pol product) per sample",
             "eq_flops_tops": value * (2 * w.nstation + 1) / (2 * (w.nstation + 1)),
             "parallelism": "replicas (each rank its own integrations)" if world > 1 else "1 GPU",
@@ -395,8 +404,7 @@ def run_xc(args):
     # CPU baseline: the oracle as it stands, bounded sample, rank 0 at N=1.
     if not args.no_cpu_baseline and world == 1 and rank == 0:
         cores = os.cpu_count() or 1
-        nchan = args.cpu_channels or 8 * cores
-        nchan = min(nchan, w.nfreq)
+        nchan = min(args.cpu_channels or w.nfreq, w.nfreq)
         xs_cpu = xs[0][:, :nchan].contiguous().cpu().numpy()
         dt, ops, thr = cpu_oracle_sample(xs_cpu, w, nchan)
         result["cpu_baseline"] = {
