@@ -189,6 +189,43 @@ size_t xc_output_bytes(const xc_handle* h);
 int64_t xc_tri_index(int64_t bx, int64_t by);
 void xc_tri_coords(int64_t g, int64_t* bx, int64_t* by);
 
+/*
+ * No-allocation X-engine (the paper has no counterpart; this is a service
+ * for callers of this library).
+ *
+ * Some callers cannot call cudaMalloc: a real-time correlator loop that
+ * reserved all of its memory at start-up and may not allocate afterwards
+ * (an allocation can stall the device and break a budget sized in advance),
+ * an application whose device memory is entirely held by another allocator,
+ * or a plug-in whose host forbids allocation inside its processing callback.
+ * xc_create allocates the operand workspace, so those callers use this call
+ * instead: it computes exactly what xc_correlate computes (tensor-core
+ * engine, out overwritten) and allocates nothing, neither device nor pinned
+ * memory.
+ *
+ * Its scratch is a static device array of XC_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  The band is
+ * processed in groups of channels whose fp16 operands (2*P*N rows x T
+ * rounded up to 64 samples x 2 bytes per channel) fit that array; a size
+ * where one channel alone does not fit is rejected with
+ * XC_ERR_UNSUPPORTED (message in xc_last_error_message()).
+ *
+ *   sizes, in_dtype, in, out: as for xc_create / xc_correlate.
+ *   status: optional caller-owned device int; a kernel whose bounded wait
+ *           gives up ORs 1 into it (the caller zeroes it).  NULL: not reported.
+ *   stream: cudaStream_t as void*; the call is stream-ordered and returns
+ *           once the work is queued.
+ * The first call on each device does a one-time set-up (device query and the
+ * device address of the static scratch, with that device current); make that
+ * first call before any stream capture begins.  Every call on a device shares
+ * the one scratch array, so calls whose work overlaps on the GPU (different
+ * streams, or different host threads, without ordering between them) race
+ * and corrupt each other's results: order them.
+ */
+#define XC_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+xc_status xc_correlate_noalloc(int nstation, int npol, int nfreq, int ntime, xc_dtype in_dtype,
+                               const void* in, void* out, int* status, void* stream);
+
 /* Library version string. */
 const char* xc_version(void);
 

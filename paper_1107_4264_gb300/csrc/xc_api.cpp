@@ -178,6 +178,21 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
 
 }  // namespace
 
+namespace xc {
+xc_status record_error(xc_status s, const char* fmt, ...) {
+  t_status = s;
+  if (s == XC_OK) {
+    t_msg[0] = '\0';
+    return s;
+  }
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_msg, sizeof(t_msg), fmt, ap);
+  va_end(ap);
+  return s;
+}
+}  // namespace xc
+
 extern "C" {
 
 xc_status xc_last_error(void) { return t_status; }

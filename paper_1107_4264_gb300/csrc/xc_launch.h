@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "xc.h"
 #include "xc_internal.h"
 
 namespace xc {
@@ -29,5 +30,9 @@ int tc_smem_bytes();
 // FP32 CUDA-core X-engine (comparator) directly from the input.
 cudaError_t launch_fp32_xengine(const void* in, int in_dtype, void* out, const Geometry& g,
                                 int accumulate, cudaStream_t s);
+
+// Record `s` and a printf-style message as this thread's last error
+// (xc_last_error / xc_last_error_message); returns s.
+xc_status record_error(xc_status s, const char* fmt, ...);
 
 }  // namespace xc

@@ -34,7 +34,7 @@ EXPORTS = [
     "xc_create", "xc_correlate", "xc_correlate_backward", "xc_destroy", "xc_last_error",
     "xc_last_error_message", "xc_status_string", "xc_set_option", "xc_synchronize",
     "xc_correlate_stream", "xc_input_bytes", "xc_output_bytes", "xc_tri_index", "xc_tri_coords",
-    "xc_version", "xc_kernel_times",
+    "xc_version", "xc_kernel_times", "xc_correlate_noalloc",
 ]
 
 _lib: Optional[ctypes.CDLL] = None
@@ -66,6 +66,7 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "xc_version": ([], ctypes.c_char_p),
         "xc_kernel_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                              i32], i32),
+        "xc_correlate_noalloc": ([i32, i32, i32, i32, i32, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -165,6 +166,19 @@ def xc_kernel_times(h: int, reset: bool = True):
     n = (ctypes.c_longlong * 2)()
     _check(load().xc_kernel_times(h, ms, n, int(reset)))
     return (ms[0], ms[1]), (n[0], n[1])
+
+
+XC_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
+
+
+def xc_correlate_noalloc(nstation: int, npol: int, nfreq: int, ntime: int, in_dtype: int,
+                         in_ptr: int, out_ptr: int, status_ptr: int = 0, stream: int = 0) -> int:
+    """The X-engine without any allocation, for callers that may not allocate
+    device memory (they cannot create a handle, which allocates a workspace):
+    scratch is the library's static device array of XC_NOALLOC_SCRATCH_BYTES.
+    Same result as xc_correlate; calls that overlap on the GPU race."""
+    return load().xc_correlate_noalloc(nstation, npol, nfreq, ntime, in_dtype, in_ptr, out_ptr,
+                                       status_ptr or None, stream)
 
 
 def xc_version() -> str:
