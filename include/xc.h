@@ -89,8 +89,9 @@ typedef enum {
 /*
  * Create an engine for fixed sizes on the current CUDA device.
  *   nstation N >= 1, npol P in {1, 2}, nfreq F >= 1, ntime T >= 1.
- * Allocates the workspace (an fp16 copy of one integration's operands plus a
- * status word).  Returns NULL on error; the reason is in xc_last_error().
+ * Allocates the workspace (a ring of fp16 operand slots for a few channels,
+ * at most 16 and about 32 MiB, plus counters and a status word).  Returns
+ * NULL on error; the reason is in xc_last_error().
  */
 xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_dtype);
 
@@ -135,10 +136,29 @@ enum {
   XC_OPT_TIMEOUT_MS = 3, /* bound on any in-kernel wait, milliseconds (default 2000) */
   XC_OPT_PROFILE = 4     /* 1: time every kernel with CUDA events (see xc_kernel_times) */
 };
-/* Engines: the tcgen05 tensor-core path, or the plain FP32 CUDA-core form
- * of the same X-engine (register tile over a shared-memory double buffer,
- * after the paper's kernel 11, Sec. 4.4), kept as the same-GPU comparator. */
-enum { XC_ENGINE_TENSOR = 0, XC_ENGINE_FP32 = 1 };
+/* Engines:
+ *   XC_ENGINE_TENSOR (default): one fused persistent tcgen05 kernel in
+ *     planar complex form (real and imaginary fp16 operand planes, four MMAs
+ *     per 16-sample step into separate real and imaginary accumulators,
+ *     128 x 128 complex blocks); operands are formed once per channel into a
+ *     small ring that stays in L2.
+ *   XC_ENGINE_TENSOR_1CTA: fused kernel in interleaved real form
+ *     (G = Y Y^T over 128 x 128 real blocks, 2x2 combine in the epilogue).
+ *   XC_ENGINE_TENSOR_PAIR: the interleaved form on CTA pairs
+ *     (tcgen05 cta_group::2, 256 x 256 real blocks over two SMs).
+ *   XC_ENGINE_FP32: the plain FP32 CUDA-core form of the same X-engine
+ *     (register tile over a shared-memory double buffer, after the paper's
+ *     kernel 11, Sec. 4.4), kept as the same-GPU comparator.
+ *   XC_ENGINE_TENSOR_2PASS: the same tensor-core arithmetic with operand
+ *     formation as a separate pass through a full fp16 copy of the
+ *     integration in device memory (allocated when this engine is selected). */
+enum {
+  XC_ENGINE_TENSOR = 0,
+  XC_ENGINE_FP32 = 1,
+  XC_ENGINE_TENSOR_2PASS = 2,
+  XC_ENGINE_TENSOR_1CTA = 3,
+  XC_ENGINE_TENSOR_PAIR = 4
+};
 
 xc_status xc_set_option(xc_handle* h, int key, long long value);
 

@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -79,9 +80,18 @@ struct xc_handle {
   int accumulate = 0;
   unsigned long long timeout_ns = 2000ull * 1000000ull;
   int num_sms = 0;
-  void* ws = nullptr;  // fp16 operands [F][R][Tp]
-  int* d_status = nullptr;
+  // Fused engine: ring of fp16 operand slots [ring_slots][R][Tp] + counters.
+  void* ring = nullptr;
+  int ring_slots = 0;
+  unsigned* counters = nullptr;
+  unsigned* chan_amax = nullptr;  // [F] per-channel max |x| (planar engine)
+  CUtensorMap ring_tmap;     // interleaved form: {Tp, R, ring_slots}
+  int planar_slots = 0;
+  CUtensorMap planar_tmap;   // planar form: {Tp, n, 2 * planar_slots}
+  // Two-pass engine (allocated when selected): fp16 operands [F][R][Tp].
+  void* ws = nullptr;
   CUtensorMap tmap;
+  int* d_status = nullptr;
   // Integrated pipeline (allocated on first use).
   void* stage[2] = {nullptr, nullptr};
   cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
@@ -101,6 +111,9 @@ struct xc_handle {
 };
 
 namespace {
+
+xc_status encode_operand_map(CUtensorMap* map, void* base, int64_t R, int64_t Tp, int64_t n);
+xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g);
 
 void release(xc_handle* h) {
   if (!h) return;
@@ -125,8 +138,11 @@ void release(xc_handle* h) {
   if (h->ev_d2h) cudaEventDestroy(h->ev_d2h);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
-  if (h->ws || h->d_status) cudaDeviceSynchronize();
+  if (h->ws || h->d_status || h->ring) cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
+  if (h->ring) cudaFree(h->ring);
+  if (h->counters) cudaFree(h->counters);
+  if (h->chan_amax) cudaFree(h->chan_amax);
   if (h->d_status) cudaFree(h->d_status);
   cudaSetDevice(cur);
   delete h;
@@ -159,6 +175,54 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     if (tm) cudaEventRecord(tm->ev[1], s);
     return succeed();
   }
+  if (h->engine == XC_ENGINE_TENSOR) {
+    xc::XeLaunch X;
+    X.g = h->g;
+    X.in = in;
+    X.in_dtype = static_cast<int>(h->dtype);
+    X.out = out;
+    X.accumulate = h->accumulate;
+    X.ring = h->ring;
+    X.ring_slots = h->planar_slots;
+    X.counters = h->counters;
+    X.amax = h->chan_amax;
+    X.grid = h->num_sms;
+    X.timeout_ns = h->timeout_ns;
+    X.status = h->d_status;
+    // 8-bit input in 128-row x 64-sample TMA boxes when rows are 16-byte strided.
+    CUtensorMap in_map;
+    const CUtensorMap* im = nullptr;
+    if (h->dtype == XC_CI8 && h->g.R % 16 == 0) {
+      if (encode_input_map(&in_map, in, h->g) != XC_OK) return t_status;
+      im = &in_map;
+    }
+    if (tm) tm->nkern = 1;
+    e = xc::launch_planar(&h->planar_tmap, im, X, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core X-engine launch");
+    if (tm) cudaEventRecord(tm->ev[1], s);
+    return succeed();
+  }
+  if (h->engine == XC_ENGINE_TENSOR_PAIR || h->engine == XC_ENGINE_TENSOR_1CTA) {
+    xc::XeLaunch X;
+    X.g = h->g;
+    X.in = in;
+    X.in_dtype = static_cast<int>(h->dtype);
+    X.out = out;
+    X.accumulate = h->accumulate;
+    X.ring = h->ring;
+    X.ring_slots = h->ring_slots;
+    X.counters = h->counters;
+    X.amax = nullptr;
+    X.grid = h->num_sms;
+    X.timeout_ns = h->timeout_ns;
+    X.status = h->d_status;
+    if (tm) tm->nkern = 1;
+    e = h->engine == XC_ENGINE_TENSOR_PAIR ? xc::launch_xengine_pair(&h->ring_tmap, X, s)
+                                          : xc::launch_xengine(&h->ring_tmap, X, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core X-engine launch");
+    if (tm) cudaEventRecord(tm->ev[1], s);
+    return succeed();
+  }
   e = xc::launch_form_operands(in, static_cast<int>(h->dtype), h->ws, h->g, s);
   if (e != cudaSuccess) return cuda_fail(e, "operand formation launch");
   if (tm) cudaEventRecord(tm->ev[1], s);
@@ -174,6 +238,60 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core X-engine launch");
   if (tm) cudaEventRecord(tm->ev[2], s);
   return succeed();
+}
+
+// TMA view of fp16 operands {t (Tp), row (R), channel/slot (n)}, loaded in
+// boxes of 64 samples x 128 rows x 1 with 128-byte swizzle.
+xc_status encode_operand_map(CUtensorMap* map, void* base, int64_t R, int64_t Tp, int64_t n) {
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(Tp), static_cast<cuuint64_t>(R),
+                              static_cast<cuuint64_t>(n)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(Tp) * 2,
+                                 static_cast<cuuint64_t>(R) * Tp * 2};
+  const cuuint32_t box[3] = {64, 128, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(cr));
+  return XC_OK;
+}
+
+// 8-bit input [T][F][R] as a 3-D tensor {R, F, T}, loaded in boxes of
+// 128 rows x 1 channel x 64 samples (zero fill past R and T).
+xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g) {
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(g.R), static_cast<cuuint64_t>(g.F),
+                              static_cast<cuuint64_t>(g.T)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(g.R),
+                                 static_cast<cuuint64_t>(g.R) * g.F};
+  const cuuint32_t box[3] = {128, 1, 64};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(in), dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS)
+    return fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled (input) failed (%d)", static_cast<int>(cr));
+  return XC_OK;
+}
+
+// Full fp16 operand copy for the two-pass engine, allocated on first use.
+xc_status ensure_two_pass_workspace(xc_handle* h) {
+  if (h->ws) return XC_OK;
+  const size_t bytes = static_cast<size_t>(h->g.F) * h->g.R * h->g.Tp * 2;
+  cudaError_t e = cudaMalloc(&h->ws, bytes);
+  if (e != cudaSuccess) {
+    h->ws = nullptr;
+    return cuda_fail(e, "two-pass workspace allocation");
+  }
+  xc_status st = encode_operand_map(&h->tmap, h->ws, h->g.R, h->g.Tp, h->g.F);
+  if (st != XC_OK) {
+    cudaFree(h->ws);
+    h->ws = nullptr;
+  }
+  return st;
 }
 
 }  // namespace
@@ -296,13 +414,6 @@ xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_d
   h->in_bytes = static_cast<size_t>(ntime) * nfreq * nstation * npol * 2 * sample_bytes(in_dtype);
   h->out_bytes = static_cast<size_t>(nfreq) * h->g.NB * npol * npol * 2 * 4;
 
-  const size_t ws_bytes = static_cast<size_t>(nfreq) * R * Tp * 2;
-  e = cudaMalloc(&h->ws, ws_bytes);
-  if (e != cudaSuccess) {
-    cuda_fail(e, "workspace allocation");
-    release(h);
-    return nullptr;
-  }
   e = cudaMalloc(reinterpret_cast<void**>(&h->d_status), sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
   if (e != cudaSuccess) {
@@ -310,26 +421,21 @@ xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_d
     release(h);
     return nullptr;
   }
-
-  EncodeTiledFn enc = tensor_map_encoder();
-  if (!enc) {
-    fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  h->ring_slots = xc::xengine_ring_slots(h->g);
+  h->planar_slots = xc::planar_ring_slots(h->g);
+  const int slots = std::max(h->ring_slots, h->planar_slots);
+  e = cudaMalloc(&h->ring, static_cast<size_t>(slots) * R * Tp * 2);
+  if (e == cudaSuccess)
+    e = cudaMalloc(reinterpret_cast<void**>(&h->counters), 2 * sizeof(unsigned) * slots);
+  if (e == cudaSuccess)
+    e = cudaMalloc(reinterpret_cast<void**>(&h->chan_amax), sizeof(unsigned) * nfreq);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "operand ring allocation");
     release(h);
     return nullptr;
   }
-  // Operand workspace as a 3-D tensor {t (Tp), row (R), channel (F)} of fp16,
-  // loaded in boxes of 64 samples x 128 rows x 1 channel with 128-byte swizzle.
-  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(Tp), static_cast<cuuint64_t>(R),
-                              static_cast<cuuint64_t>(nfreq)};
-  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(Tp) * 2,
-                                 static_cast<cuuint64_t>(R) * Tp * 2};
-  const cuuint32_t box[3] = {64, 128, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult cr = enc(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, h->ws, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (cr != CUDA_SUCCESS) {
-    fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(cr));
+  if (encode_operand_map(&h->ring_tmap, h->ring, R, Tp, h->ring_slots) != XC_OK ||
+      encode_operand_map(&h->planar_tmap, h->ring, R / 2, Tp, 2LL * h->planar_slots) != XC_OK) {
     release(h);
     return nullptr;
   }
@@ -346,8 +452,13 @@ xc_status xc_set_option(xc_handle* h, int key, long long value) {
   if (!h) return fail(XC_ERR_INVALID_ARG, "NULL handle");
   switch (key) {
     case XC_OPT_ENGINE:
-      if (value != XC_ENGINE_TENSOR && value != XC_ENGINE_FP32)
+      if (value != XC_ENGINE_TENSOR && value != XC_ENGINE_FP32 && value != XC_ENGINE_TENSOR_2PASS &&
+          value != XC_ENGINE_TENSOR_1CTA && value != XC_ENGINE_TENSOR_PAIR)
         return fail(XC_ERR_INVALID_ARG, "unknown engine %lld", value);
+      if (value == XC_ENGINE_TENSOR_2PASS) {
+        xc_status st = ensure_two_pass_workspace(h);
+        if (st != XC_OK) return st;
+      }
       h->engine = static_cast<int>(value);
       return succeed();
     case XC_OPT_ACCUMULATE:

@@ -27,6 +27,36 @@ struct TcLaunch {
 cudaError_t launch_tc_xengine(const CUtensorMap* tmap, const TcLaunch& p, cudaStream_t s);
 int tc_smem_bytes();
 
+// Fused persistent tensor-core X-engine: converter warps form the fp16
+// operands into a ring of channel slots (`ring`, [ring_slots][R][Tp]) read
+// through `tmap` ({Tp, R, ring_slots}, 64 x 128 x 1 boxes, 128B swizzle).
+struct XeLaunch {
+  Geometry g;
+  const void* in;
+  int in_dtype;  // 0 int8 (int32 out, exact), 1 fp16, 2 fp32
+  void* out;
+  int accumulate;
+  void* ring;
+  int ring_slots;
+  unsigned* counters;  // 2 * ring_slots, zeroed by the launcher on `s`
+  unsigned* amax;      // [F] per-channel max |x| (planar engine, 8-bit input)
+  int grid;
+  unsigned long long timeout_ns;
+  int* status;
+};
+cudaError_t launch_xengine(const CUtensorMap* tmap, const XeLaunch& p, cudaStream_t s);
+// Planar complex form (separate real/imaginary fp16 planes, 4 MMAs per step
+// into D_re/D_im): `ring_map` is {Tp, n, 2*ring_slots} over the ring
+// [slots][2][n][Tp]; `in_map` (8-bit input only, may be NULL) is {R, F, T}
+// int8 in 128 x 1 x 64 boxes.
+cudaError_t launch_planar(const CUtensorMap* ring_map, const CUtensorMap* in_map, const XeLaunch& p,
+                          cudaStream_t s);
+int planar_ring_slots(const Geometry& g);
+// Same as launch_xengine, on CTA pairs (tcgen05 cta_group::2, 256 x 256 blocks).
+cudaError_t launch_xengine_pair(const CUtensorMap* tmap, const XeLaunch& p, cudaStream_t s);
+// Ring slots for a geometry (2..16 channels, about 32 MiB).
+int xengine_ring_slots(const Geometry& g);
+
 // FP32 CUDA-core X-engine (comparator) directly from the input.
 cudaError_t launch_fp32_xengine(const void* in, int in_dtype, void* out, const Geometry& g,
                                 int accumulate, cudaStream_t s);

@@ -1,0 +1,845 @@
+// xc_planar.cu -- fused persistent tensor-core X-engine, planar complex form.
+//
+// Eq. (outer) of Sec. 2.1 per channel f: V_f = sum_t x_f(t) x_f(t)^H over
+// n = N*P complex inputs.  With the real and imaginary parts of the inputs
+// as separate fp16 operand planes Xr, Xi (n rows x T samples, K-major),
+//
+//     Re V = Xr Xr^T + Xi Xi^T,      Im V = Xi Xr^T - Xr Xi^T,
+//
+// so a 128 x 128 block of V (rows a, columns b) is four tcgen05 MMAs per
+// 16-sample step into two TMEM accumulators,
+//     D_re += Ar Br^T,  D_re += Ai Bi^T,  D_im += Ai Br^T,  D_im += Ar (-Bi)^T,
+// the last with the instruction descriptor's negate-B bit.  Four operand
+// tiles feed 4 MMAs (half the shared-memory and L2 bytes per MAC of the
+// interleaved real form) and every TMEM column is a finished visibility
+// component: the epilogue converts and stores, with no lane exchange.
+//
+// Exact 8-bit input: int8 is exact in fp16, products are exact in fp32, and
+// every partial sum of an accumulator is an integer bounded by the sum of
+// |products| so far: at most 2 m^2 per sample, m = max |x| of the channel.
+// The converters record m per channel; a chunk of S samples with
+// 2 m^2 S <= 2^24 is exact in fp32 in any summation order (S >= 512 for any
+// int8 data, the whole integration for typical 4-6 bit signal levels).  Each
+// chunk is drained into int32 and added into the output (stored for the
+// first chunk).  Float input accumulates in fp32 over the whole integration.
+//
+// Blocks (Sec. 4.2): 128 x 128 blocks of V on or below the block diagonal,
+// g = by(by+1)/2 + bx; block edges fall on station boundaries (128 inputs =
+// 128/P stations).  Diagonal blocks load one pair of planes for both
+// operands and store only their lower station triangle (Sec. 4.4).
+//
+// Operand formation (Sec. 4.1 input order, Sec. 5 8-bit samples): converter
+// warps form each channel's planes once into a ring of channel slots in
+// global memory that stays in L2 (the blocks of a channel read it back
+// through TMA): 8-bit input arrives by TMA in 128-row x 64-sample boxes,
+// other types and row counts by direct loads; a lane turns 4 rows (2 complex
+// inputs) x 64 samples into four 128-byte plane rows.  Ring protocol:
+//   ready[slot] counts converted units (128 rows x 64 samples); channel c
+//     (generation c / slots of slot c % slots) is complete at
+//     ready >= (gen + 1) * units_per_channel;
+//   done[slot] counts blocks whose operands have landed in shared memory;
+//     slot s may take channel c once done >= gen(c) * blocks_per_channel.
+// Dependencies point only to lower channels and all CTAs are co-resident,
+// so the ring cannot deadlock; every wait is bounded regardless.
+//
+// CTA roles (persistent, one CTA per SM, channel-major items):
+//   warp 0      TMA producer: 3 stages x (Ar, Ai, Br, Bi) 64-sample tiles
+//   warp 1      MMA issuer; owns TMEM (2 sets x {D_re, D_im} x 128 columns)
+//   warps 2..5  epilogue
+//   warps 6..9  converters
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "xc_launch.h"
+#include "xc_ptx.cuh"
+
+namespace xc {
+namespace {
+
+constexpr int kBlk = 128;      // complex inputs per block side
+constexpr int kBK = 64;        // samples per stage
+constexpr int kStages = 3;
+constexpr int kNumEpiWarps = 4;
+constexpr int kNumConvWarps = 4;
+constexpr int kThreads = 32 * (2 + kNumEpiWarps + kNumConvWarps);
+constexpr int kTileBytes = kBlk * kBK * 2;  // 16 KiB: one plane tile
+constexpr int kStageBytes = 4 * kTileBytes;
+constexpr uint32_t kTmemCols = 512;         // 2 sets x (D_re, D_im) x 128
+constexpr uint32_t kIdesc = ptx::idesc_f16_f32(kBlk, kBlk);
+constexpr uint32_t kIdescNegB = kIdesc | (1u << 14);
+constexpr int kUnitRows = 128;  // converter unit: 128 real rows x 64 samples
+constexpr int kUnitT = 64;
+constexpr int kConvBufBytes = kUnitRows * kUnitT;  // int8 staging per converter warp
+constexpr int kConvBarrier = 1;
+
+constexpr int kConvOff = kStages * kStageBytes;
+constexpr int kBarOff = kConvOff + kNumConvWarps * kConvBufBytes;
+constexpr int kNumBars = 2 * kStages + 5 + kNumConvWarps;
+constexpr int kSmemBytes = kBarOff + kNumBars * 8 + 16 + 1024;
+static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+struct Params {
+  Geometry g;
+  int n;               // complex inputs per channel = N * P
+  const void* in;
+  void* out;
+  int accumulate;
+  int ntiles;          // lower blocks per channel
+  long long nitems;    // ntiles * F
+  int nkb;             // Tp / 64
+  int is_int;          // 8-bit input: exact chunks from the channel's max |x|
+  unsigned* amax;      // [F] max |x| per channel (8-bit input), zeroed by the host
+  __half* ring;        // [slots][2][n][Tp]
+  int ring_slots;
+  unsigned* ready;
+  unsigned* done;
+  int row_units;       // ceil(R / 128)
+  int units_per_chan;  // row_units * Tp / 64
+  int tma_in;          // 8-bit input staged by TMA (else direct loads)
+  int vec4;            // R % 4 == 0 (direct-load path)
+  unsigned long long timeout_ns;
+  int* status;
+};
+
+// ------------------------------------------------------------ global sync
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __noinline__ bool wait_counter(const unsigned* p, unsigned target, const Params& prm,
+                                          volatile int* abort_flag) {
+  if (ld_acquire(p) >= target) return true;
+  const uint64_t t0 = ptx::globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    __nanosleep(64);
+    if (ld_acquire(p) >= target) return true;
+    if ((it & 15u) == 0) {
+      if (*abort_flag) return false;
+      if (*reinterpret_cast<volatile int*>(prm.status) != 0) {
+        *abort_flag = 1;
+        return false;
+      }
+      if (ptx::globaltimer() - t0 > prm.timeout_ns) {
+        *abort_flag = 1;
+        atomicOr(prm.status, kStatusTimeout);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void item_coords(long long it, int ntiles, int* f, int* bx, int* by) {
+  *f = static_cast<int>(it / ntiles);
+  int64_t x, y;
+  tri_coords(it % ntiles, &x, &y);
+  *bx = static_cast<int>(x);
+  *by = static_cast<int>(y);
+}
+
+// K-blocks per exact fp32 accumulation chunk for channel f (all K-blocks for
+// float input).  Called after the channel is known to be fully converted.
+__device__ __forceinline__ int chunk_kblocks(const Params& p, int f) {
+  if (!p.is_int) return p.nkb;
+  const unsigned m = *reinterpret_cast<volatile const unsigned*>(p.amax + f);
+  if (m == 0) return p.nkb;
+  const unsigned long long per_block = 2ull * m * m * kBK;  // |partial| growth per K-block
+  const unsigned long long kb = (1ull << 24) / per_block;
+  return static_cast<int>(kb < 1 ? 1 : (kb > static_cast<unsigned long long>(p.nkb) ? p.nkb : kb));
+}
+
+// Wait (bounded) until channel f is fully converted into its ring slot.
+__device__ __forceinline__ bool channel_ready(const Params& p, int f, volatile int* abort_flag) {
+  const unsigned gen = static_cast<unsigned>(f / p.ring_slots);
+  return wait_counter(p.ready + f % p.ring_slots, (gen + 1) * static_cast<unsigned>(p.units_per_chan),
+                      p, abort_flag);
+}
+
+// -------------------------------------------------------------- converter
+
+template <int DT>
+struct Quad;
+template <>
+struct Quad<0> {
+  uint32_t w;
+};
+template <>
+struct Quad<1> {
+  uint2 w;
+};
+template <>
+struct Quad<2> {
+  float4 w;
+};
+
+template <int DT>
+__device__ __forceinline__ void load_quad(const void* in, int64_t idx, Quad<DT>& q) {
+  if constexpr (DT == 0) {
+    q.w = __ldg(reinterpret_cast<const uint32_t*>(static_cast<const int8_t*>(in) + idx));
+  } else if constexpr (DT == 1) {
+    q.w = __ldg(reinterpret_cast<const uint2*>(static_cast<const __half*>(in) + idx));
+  } else {
+    q.w = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(in) + idx));
+  }
+}
+
+template <int DT>
+__device__ __forceinline__ void zero_quad(Quad<DT>& q) {
+  if constexpr (DT == 0) {
+    q.w = 0u;
+  } else if constexpr (DT == 1) {
+    q.w = make_uint2(0u, 0u);
+  } else {
+    q.w = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// fp16x2 of (component j of sample a, component j of sample b).
+__device__ __forceinline__ uint32_t pair_i8(uint32_t a, uint32_t b, int j) {
+  // Byte j of a into byte 0 and byte j of b into byte 2; 0x6400 | (x ^ 0x80)
+  // is the fp16 value 1152 + x, so subtracting 1152 gives x exactly.
+  uint32_t d = __byte_perm(a, b, static_cast<uint32_t>(j) | (static_cast<uint32_t>(j + 4) << 8));
+  d = (d & 0x00FF00FFu) ^ 0x64806480u;
+  __half2 h = *reinterpret_cast<__half2*>(&d);
+  h = __hsub2(h, __half2(__float2half_rn(1152.f), __float2half_rn(1152.f)));
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+template <int DT>
+__device__ __forceinline__ uint32_t pair_half2(const Quad<DT>& a, const Quad<DT>& b, int j) {
+  if constexpr (DT == 0) {
+    return pair_i8(a.w, b.w, j);
+  } else if constexpr (DT == 1) {
+    const uint32_t wa = (j < 2) ? a.w.x : a.w.y;
+    const uint32_t wb = (j < 2) ? b.w.x : b.w.y;
+    return __byte_perm(wa, wb, (j & 1) ? 0x7632u : 0x5410u);
+  } else {
+    const float fa = (j == 0) ? a.w.x : (j == 1) ? a.w.y : (j == 2) ? a.w.z : a.w.w;
+    const float fb = (j == 0) ? b.w.x : (j == 1) ? b.w.y : (j == 2) ? b.w.z : b.w.w;
+    __half2 h = __floats2half2_rn(fa, fb);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+template <int DT>
+__device__ __forceinline__ __half scalar_half(const void* in, int64_t idx) {
+  if constexpr (DT == 0) {
+    return __int2half_rn(static_cast<int>(static_cast<const int8_t*>(in)[idx]));
+  } else if constexpr (DT == 1) {
+    return static_cast<const __half*>(in)[idx];
+  } else {
+    return __float2half_rn(static_cast<const float*>(in)[idx]);
+  }
+}
+
+// Plane row of real input row r (r = 2a + c): ring row (slot, c, a).
+__device__ __forceinline__ __half* plane_row(const Params& p, int slot, int r) {
+  return p.ring + ((static_cast<int64_t>(slot) * 2 + (r & 1)) * p.n + (r >> 1)) * p.g.Tp;
+}
+
+// A batch: up to 4 consecutive 64-sample units of one channel and 128-row
+// block, one per converter warp; batches b = blockIdx.x + k * gridDim.x.
+struct Batch {
+  int c, slot, rb, tb0, n;
+};
+
+__device__ __forceinline__ Batch batch_of(const Params& p, long long b) {
+  const int tblocks = p.g.Tp / kUnitT;
+  const int bpr = (tblocks + kNumConvWarps - 1) / kNumConvWarps;
+  const int bpc = bpr * p.row_units;
+  Batch x;
+  x.c = static_cast<int>(b / bpc);
+  const int j = static_cast<int>(b % bpc);
+  x.slot = x.c % p.ring_slots;
+  x.rb = j / bpr;
+  x.tb0 = (j % bpr) * kNumConvWarps;
+  x.n = min(kNumConvWarps, tblocks - x.tb0);
+  return x;
+}
+
+__device__ __forceinline__ void conv_sync() {
+  asm volatile("bar.sync %0, %1;" ::"r"(kConvBarrier), "r"(32 * kNumConvWarps));
+}
+
+__device__ __forceinline__ bool claim_slot(const Params& p, int c, int cw, int lane,
+                                           volatile int* abort_flag) {
+  const unsigned gen = static_cast<unsigned>(c / p.ring_slots);
+  if (gen > 0) {
+    if (cw == 0 && lane == 0)
+      wait_counter(p.done + (c % p.ring_slots), gen * static_cast<unsigned>(p.ntiles), p, abort_flag);
+    conv_sync();
+    if (*abort_flag) return false;
+  }
+  fence_proxy_async_global();
+  return true;
+}
+
+// Write 4 real rows (r .. r+3) x 16 samples from 16 quads into the planes.
+template <int DT>
+__device__ __forceinline__ void store_group(const Params& p, int slot, int r, int tb,
+                                            const Quad<DT> (&q)[16]) {
+  if (r >= p.g.R) return;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint32_t h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = pair_half2<DT>(q[2 * i], q[2 * i + 1], j);
+    uint4* dst = reinterpret_cast<uint4*>(plane_row(p, slot, r + j) + tb);
+    dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+    dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+  }
+}
+
+template <int DT>
+__device__ __forceinline__ void load_group(const Params& p, int c, int r, int tb, Quad<DT> (&q)[16]) {
+  const Geometry& g = p.g;
+  const bool row_ok = r < g.R;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int t = tb + i;
+    if (row_ok && t < g.T)
+      load_quad<DT>(p.in, (static_cast<int64_t>(t) * g.F + c) * g.R + r, q[i]);
+    else
+      zero_quad<DT>(q[i]);
+  }
+}
+
+template <int DT>
+__device__ __forceinline__ void convert_unit_scalar(const Params& p, int c, int slot, int r0, int t0) {
+  const Geometry& g = p.g;
+  for (int j = 0; j < 4; ++j) {
+    const int rr = r0 + j;
+    if (rr >= g.R) break;
+    __half* dst = plane_row(p, slot, rr) + t0;
+    for (int i = 0; i < kUnitT; ++i) {
+      const int t = t0 + i;
+      dst[i] = (t < g.T) ? scalar_half<DT>(p.in, (static_cast<int64_t>(t) * g.F + c) * g.R + rr)
+                         : __float2half_rn(0.f);
+    }
+  }
+}
+
+// Direct-load converter (any input type / row count).
+template <int DT>
+__device__ void converter_direct(const Params& p, int cw, int lane, volatile int* abort_flag) {
+  const int tblocks = p.g.Tp / kUnitT;
+  const int bpr = (tblocks + kNumConvWarps - 1) / kNumConvWarps;
+  const long long total = static_cast<long long>(p.g.F) * bpr * p.row_units;
+  int claimed = -1;
+  for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+    const Batch x = batch_of(p, b);
+    if (x.c != claimed) {
+      if (!claim_slot(p, x.c, cw, lane, abort_flag)) return;
+      claimed = x.c;
+    }
+    if (cw < x.n) {
+      const int r = x.rb * kUnitRows + 4 * lane;
+      const int t0 = (x.tb0 + cw) * kUnitT;
+      if (p.vec4) {
+        Quad<DT> qa[16], qb[16];
+        load_group<DT>(p, x.c, r, t0, qa);
+        load_group<DT>(p, x.c, r, t0 + 16, qb);
+        store_group<DT>(p, x.slot, r, t0, qa);
+        load_group<DT>(p, x.c, r, t0 + 32, qa);
+        store_group<DT>(p, x.slot, r, t0 + 16, qb);
+        load_group<DT>(p, x.c, r, t0 + 48, qb);
+        store_group<DT>(p, x.slot, r, t0 + 32, qa);
+        store_group<DT>(p, x.slot, r, t0 + 48, qb);
+      } else {
+        convert_unit_scalar<DT>(p, x.c, x.slot, r, t0);
+      }
+    }
+    if (DT == 0 && cw == 0 && lane == 0) atomicMax(p.amax + x.c, 128u);  // no scan: worst case
+    fence_proxy_async_global();
+    conv_sync();
+    if (cw == 0 && lane == 0) red_release_add(p.ready + x.slot, static_cast<unsigned>(x.n));
+    if (*abort_flag) return;
+  }
+}
+
+// 8-bit converter with TMA-staged input: warp cw owns an 8 KiB staging
+// buffer ([64 samples][128 rows] int8) and always has its next unit's box in
+// flight while it converts the current one.
+__device__ void converter_tma(const Params& p, const CUtensorMap* in_map, uint32_t buf,
+                              uint32_t bar, int cw, int lane, volatile int* abort_flag) {
+  const int tblocks = p.g.Tp / kUnitT;
+  const int bpr = (tblocks + kNumConvWarps - 1) / kNumConvWarps;
+  const long long total = static_cast<long long>(p.g.F) * bpr * p.row_units;
+  const ptx::WaitCtl wc{p.timeout_ns, p.status, abort_flag};
+  auto issue = [&](const Batch& x) {
+    if (lane == 0) {
+      ptx::mbar_arrive_expect_tx(bar, kConvBufBytes);
+      ptx::tma_load_3d(buf, in_map, bar, x.rb * kUnitRows, x.c, (x.tb0 + cw) * kUnitT);
+    }
+  };
+  uint32_t phase = 0;
+  int claimed = -1;
+  long long b = blockIdx.x;
+  if (b < total) {
+    const Batch x0 = batch_of(p, b);
+    if (cw < x0.n) issue(x0);
+  }
+  for (; b < total; b += gridDim.x) {
+    const Batch x = batch_of(p, b);
+    const long long bn = b + gridDim.x;
+    const bool has_next = bn < total;
+    const Batch xn = batch_of(p, has_next ? bn : b);
+    if (x.c != claimed) {
+      if (!claim_slot(p, x.c, cw, lane, abort_flag)) return;
+      claimed = x.c;
+    }
+    if (cw < x.n) {
+      const bool got = ptx::wait_bounded(bar, phase, wc);
+      if (!__all_sync(0xffffffffu, got)) return;
+      phase ^= 1u;
+      // 64 samples of rows 4*lane .. 4*lane+3.
+      uint32_t w[kUnitT];
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(
+          __cvta_shared_to_generic(static_cast<size_t>(buf)));
+#pragma unroll
+      for (int i = 0; i < kUnitT; ++i) w[i] = src[i * (kUnitRows / 4) + lane];
+      __syncwarp();
+      ptx::fence_proxy_async_smem();
+      if (has_next && cw < xn.n) issue(xn);
+      // max |x| over the unit (zero-filled rows and samples contribute 0).
+      unsigned m = 0;
+#pragma unroll
+      for (int i = 0; i < kUnitT; ++i) {
+        const uint32_t v = w[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int b = static_cast<int>(static_cast<int8_t>((v >> (8 * j)) & 0xffu));
+          m = max(m, static_cast<unsigned>(b < 0 ? -b : b));
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) atomicMax(p.amax + x.c, m);
+      const int r = x.rb * kUnitRows + 4 * lane;
+      if (r < p.g.R) {
+        const int t0 = (x.tb0 + cw) * kUnitT;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint4* dst = reinterpret_cast<uint4*>(plane_row(p, x.slot, r + j) + t0);
+#pragma unroll
+          for (int s = 0; s < kUnitT / 8; ++s) {
+            dst[s] = make_uint4(pair_i8(w[8 * s + 0], w[8 * s + 1], j), pair_i8(w[8 * s + 2], w[8 * s + 3], j),
+                                pair_i8(w[8 * s + 4], w[8 * s + 5], j), pair_i8(w[8 * s + 6], w[8 * s + 7], j));
+          }
+        }
+      }
+    } else if (has_next && cw < xn.n) {
+      issue(xn);
+    }
+    fence_proxy_async_global();
+    conv_sync();
+    if (cw == 0 && lane == 0) red_release_add(p.ready + x.slot, static_cast<unsigned>(x.n));
+    if (*abort_flag) return;
+  }
+}
+
+// --------------------------------------------------------------- epilogue
+
+// Store one 32-column piece: values v_re[j], v_im[j] of V(a, b0 + j).
+template <bool IS_INT>
+__device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint32_t (&im)[32],
+                                            const Params& p, int f, int a, int b0, bool add) {
+  using T = typename std::conditional<IS_INT, int, float>::type;
+  const Geometry& g = p.g;
+  T* out = static_cast<T*>(p.out);
+  auto val = [&](uint32_t u) -> T {
+    if constexpr (IS_INT) {
+      return __float2int_rn(__uint_as_float(u));
+    } else {
+      return __uint_as_float(u);
+    }
+  };
+  if (a >= p.n) return;
+  if (g.P == 2) {
+    const int s1 = a >> 1, p1 = a & 1;
+    const int64_t krow = static_cast<int64_t>(f) * g.NB + static_cast<int64_t>(s1) * (s1 + 1) / 2;
+    const int s2_0 = b0 >> 1;
+    using V4 = typename std::conditional<IS_INT, int4, float4>::type;
+    V4* o4 = reinterpret_cast<V4*>(out + (krow * 4 + p1 * 2) * 2) + (s2_0 * 2);  // (p1,0),(p1,1) of s2_0
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      V4 old[8];
+      if (add) {
+        // Loads of a half first: independent of the stores that follow.
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (s2_0 + 8 * h + j <= s1) old[j] = o4[2 * (8 * h + j)];
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int jj = 8 * h + j;
+        if (s2_0 + jj <= s1) {
+          V4 v;
+          v.x = val(re[2 * jj]);
+          v.y = val(im[2 * jj]);
+          v.z = val(re[2 * jj + 1]);
+          v.w = val(im[2 * jj + 1]);
+          if (add) {
+            v.x += old[j].x;
+            v.y += old[j].y;
+            v.z += old[j].z;
+            v.w += old[j].w;
+          }
+          o4[2 * jj] = v;
+        }
+      }
+    }
+  } else {
+    const int s1 = a;
+    const int64_t krow = static_cast<int64_t>(f) * g.NB + static_cast<int64_t>(s1) * (s1 + 1) / 2;
+    using V2 = typename std::conditional<IS_INT, int2, float2>::type;
+    V2* o2 = reinterpret_cast<V2*>(out + krow * 2) + b0;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      V2 old[8];
+      if (add) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (b0 + 8 * h + j <= s1) old[j] = o2[8 * h + j];
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int jj = 8 * h + j;
+        if (b0 + jj <= s1) {
+          V2 v;
+          v.x = val(re[jj]);
+          v.y = val(im[jj]);
+          if (add) {
+            v.x += old[j].x;
+            v.y += old[j].y;
+          }
+          o2[jj] = v;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ kernel
+
+template <bool IS_INT, int DT>
+__global__ void __launch_bounds__(kThreads, 1)
+    planar_kernel(const __grid_constant__ CUtensorMap ring_map,
+                  const __grid_constant__ CUtensorMap in_map, const Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  const uint32_t sbase = ptx::smem_u32(smem);
+  const uint32_t bar0 = sbase + kBarOff;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
+  auto accf_bar = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
+  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * kStages + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
+  auto conv_bar = [&](int w) { return bar0 + 8u * (2 * kStages + 5 + w); };
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + kBarOff + kNumBars * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      ptx::mbar_init(full_bar(s), 1);
+      ptx::mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(accf_bar(b), 1);
+      ptx::mbar_init(acce_bar(b), kNumEpiWarps);
+    }
+    ptx::mbar_init(drain_bar, 1);
+    for (int w = 0; w < kNumConvWarps; ++w) ptx::mbar_init(conv_bar(w), 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+    ptx::fence_proxy_async_smem();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_holder), kTmemCols);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  const ptx::WaitCtl wc{p.timeout_ns, p.status, abort_flag};
+  const unsigned upc = static_cast<unsigned>(p.units_per_chan);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      ptx::prefetch_tmap(&ring_map);
+      int stage = 0;
+      uint32_t phase = 0;
+      int issued_phase[kStages];
+      for (int s = 0; s < kStages; ++s) issued_phase[s] = -1;
+      bool ok = true;
+      int ready_chan = -1;
+      for (long long it = blockIdx.x; ok && it < p.nitems; it += gridDim.x) {
+        int f, bx, by;
+        item_coords(it, p.ntiles, &f, &bx, &by);
+        const int slot = f % p.ring_slots;
+        if (f != ready_chan) {
+          const unsigned gen = static_cast<unsigned>(f / p.ring_slots);
+          if (!wait_counter(p.ready + slot, (gen + 1) * upc, p, abort_flag)) {
+            ok = false;
+            break;
+          }
+          ready_chan = f;
+        }
+        const bool diag = bx == by;
+        for (int kb = 0; kb < p.nkb; ++kb) {
+          if (!ptx::wait_bounded(empty_bar(stage), phase ^ 1u, wc)) {
+            ok = false;
+            break;
+          }
+          const uint32_t dst = sbase + stage * kStageBytes;
+          const uint32_t fb = full_bar(stage);
+          ptx::mbar_arrive_expect_tx(fb, diag ? 2 * kTileBytes : 4 * kTileBytes);
+          ptx::tma_load_3d(dst, &ring_map, fb, kb * kBK, by * kBlk, 2 * slot);
+          ptx::tma_load_3d(dst + kTileBytes, &ring_map, fb, kb * kBK, by * kBlk, 2 * slot + 1);
+          if (!diag) {
+            ptx::tma_load_3d(dst + 2 * kTileBytes, &ring_map, fb, kb * kBK, bx * kBlk, 2 * slot);
+            ptx::tma_load_3d(dst + 3 * kTileBytes, &ring_map, fb, kb * kBK, bx * kBlk, 2 * slot + 1);
+          }
+          issued_phase[stage] = static_cast<int>(phase);
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        for (int s = 0; s < kStages; ++s) {
+          if (issued_phase[s] < 0) continue;
+          const uint64_t t0 = ptx::globaltimer();
+          while (!ptx::mbar_try_wait(full_bar(s), static_cast<uint32_t>(issued_phase[s])) &&
+                 ptx::globaltimer() - t0 < p.timeout_ns) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t u = 0;
+      bool ok = true;
+      bool issued_any = false;
+      for (long long it = blockIdx.x; ok && it < p.nitems; it += gridDim.x) {
+        int f, bx, by;
+        item_coords(it, p.ntiles, &f, &bx, &by);
+        const bool diag = bx == by;
+        if (!channel_ready(p, f, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const int chunk_kb = chunk_kblocks(p, f);
+        const int nchunks = (p.nkb + chunk_kb - 1) / chunk_kb;
+        for (int ch = 0; ok && ch < nchunks; ++ch) {
+          const int kb0 = ch * chunk_kb;
+          const int kb1 = min(p.nkb, kb0 + chunk_kb);
+          const uint32_t ab = u & 1u;
+          const uint32_t ap = (u >> 1) & 1u;
+          if (!ptx::wait_bounded(acce_bar(ab), ap ^ 1u, wc)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t d_re = tmem + ab * 256;
+          const uint32_t d_im = d_re + 128;
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!ptx::wait_bounded(full_bar(stage), phase, wc)) {
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t ar = sbase + stage * kStageBytes;
+            const uint32_t ai = ar + kTileBytes;
+            const uint32_t br = diag ? ar : ar + 2 * kTileBytes;
+            const uint32_t bi = diag ? ai : ar + 3 * kTileBytes;
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k) {
+              const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
+              const uint64_t dar = ptx::sw128_kmajor_desc(ar + k * 32);
+              const uint64_t dai = ptx::sw128_kmajor_desc(ai + k * 32);
+              const uint64_t dbr = ptx::sw128_kmajor_desc(br + k * 32);
+              const uint64_t dbi = ptx::sw128_kmajor_desc(bi + k * 32);
+              ptx::mma_f16_ss(d_re, dar, dbr, kIdesc, acc);       // Re += Ar Br^T
+              ptx::mma_f16_ss(d_re, dai, dbi, kIdesc, 1u);        // Re += Ai Bi^T
+              ptx::mma_f16_ss(d_im, dai, dbr, kIdesc, acc);       // Im += Ai Br^T
+              ptx::mma_f16_ss(d_im, dar, dbi, kIdescNegB, 1u);    // Im -= Ar Bi^T
+            }
+            issued_any = true;
+            ptx::mma_commit(empty_bar(stage));
+            if (++stage == kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (!ok) break;
+          ptx::mma_commit(accf_bar(ab));
+          ++u;
+        }
+        if (ok) red_release_add(p.done + (f % p.ring_slots), 1u);
+      }
+      if (!ok && issued_any) {
+        ptx::mma_commit(drain_bar);
+        const uint64_t t0 = ptx::globaltimer();
+        while (!ptx::mbar_try_wait(drain_bar, 0) && ptx::globaltimer() - t0 < p.timeout_ns) {
+        }
+      }
+    }
+  } else if (warp < 2 + kNumEpiWarps) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const uint32_t t_lanes = tmem + (static_cast<uint32_t>(q * 32) << 16);
+    const int P = p.g.P;
+    uint32_t u = 0;
+    bool ok = true;
+    for (long long it = blockIdx.x; ok && it < p.nitems; it += gridDim.x) {
+      int f, bx, by;
+      item_coords(it, p.ntiles, &f, &bx, &by);
+      const int a = by * kBlk + q * 32 + lane;  // this thread's row input
+      // Pieces 0..last can reach the lower station triangle for this warp.
+      const int s1_hi = min(p.g.N - 1, (by * kBlk + q * 32 + 31) / P);
+      int last = -1;
+      for (int piece = 0; piece < kBlk / 32; ++piece)
+        if ((bx * kBlk + piece * 32) / P <= s1_hi) last = piece;
+      const bool rdy = channel_ready(p, f, abort_flag);
+      if (!__all_sync(0xffffffffu, rdy)) {
+        ok = false;
+        break;
+      }
+      const int chunk_kb = chunk_kblocks(p, f);
+      const int nchunks = (p.nkb + chunk_kb - 1) / chunk_kb;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        const uint32_t ab = u & 1u;
+        const uint32_t ap = (u >> 1) & 1u;
+        const bool got = ptx::wait_bounded(accf_bar(ab), ap, wc);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const bool add = p.accumulate || ch > 0;
+        if (last < 0) {
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
+        }
+#pragma unroll 1
+        for (int piece = 0; piece <= last; ++piece) {
+          uint32_t vr[32], vi[32];
+          ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + piece * 32, vr);
+          ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + 128 + piece * 32, vi);
+          ptx::tmem_wait_ld();
+          if (piece == last) {
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
+          }
+          store_piece<IS_INT>(vr, vi, p, f, a, bx * kBlk + piece * 32, add);
+        }
+        ++u;
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- converters
+    const int cw = warp - (2 + kNumEpiWarps);
+    if constexpr (DT == 0) {
+      if (p.tma_in) {
+        converter_tma(p, &in_map, sbase + kConvOff + cw * kConvBufBytes, conv_bar(cw), cw, lane,
+                      abort_flag);
+      } else {
+        converter_direct<DT>(p, cw, lane, abort_flag);
+      }
+    } else {
+      converter_direct<DT>(p, cw, lane, abort_flag);
+    }
+  }
+
+  // ------------------------------------------------------------- teardown
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+template <bool IS_INT, int DT>
+cudaError_t launch_variant(const CUtensorMap* ring_map, const CUtensorMap* in_map, const Params& p,
+                           int grid, cudaStream_t s) {
+  auto kern = planar_kernel<IS_INT, DT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, kSmemBytes, s>>>(*ring_map, *in_map, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int planar_ring_slots(const Geometry& g) {
+  const int64_t per = 2LL * g.N * g.P * g.Tp * 2;
+  int64_t n = (32ll << 20) / std::max<int64_t>(per, 1);
+  n = std::max<int64_t>(2, std::min<int64_t>(16, n));
+  return static_cast<int>(std::min<int64_t>(n, g.F));
+}
+
+cudaError_t launch_planar(const CUtensorMap* ring_map, const CUtensorMap* in_map, const XeLaunch& L,
+                          cudaStream_t s) {
+  Params p;
+  p.g = L.g;
+  p.n = L.g.N * L.g.P;
+  p.in = L.in;
+  p.out = L.out;
+  p.accumulate = L.accumulate;
+  const int nb = (p.n + kBlk - 1) / kBlk;
+  p.ntiles = nb * (nb + 1) / 2;
+  p.nitems = static_cast<long long>(p.ntiles) * L.g.F;
+  p.nkb = L.g.Tp / kBK;
+  p.is_int = L.in_dtype == 0 ? 1 : 0;
+  p.amax = L.amax;
+  p.ring = static_cast<__half*>(L.ring);
+  p.ring_slots = L.ring_slots;
+  p.ready = L.counters;
+  p.done = L.counters + L.ring_slots;
+  p.row_units = (L.g.R + kUnitRows - 1) / kUnitRows;
+  p.units_per_chan = p.row_units * (L.g.Tp / kUnitT);
+  p.tma_in = (L.in_dtype == 0 && in_map != nullptr) ? 1 : 0;
+  p.vec4 = (L.g.R % 4 == 0) ? 1 : 0;
+  p.timeout_ns = L.timeout_ns;
+  p.status = L.status;
+  if (p.nitems == 0 || p.nkb == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(L.counters, 0, 2 * sizeof(unsigned) * L.ring_slots, s);
+  if (e == cudaSuccess && p.is_int) e = cudaMemsetAsync(L.amax, 0, sizeof(unsigned) * L.g.F, s);
+  if (e != cudaSuccess) return e;
+  const int grid = static_cast<int>(std::min<long long>(p.nitems, L.grid));
+  const CUtensorMap* im = in_map ? in_map : ring_map;  // unused when !tma_in
+  switch (L.in_dtype) {
+    case 0: return launch_variant<true, 0>(ring_map, im, p, grid, s);
+    case 1: return launch_variant<false, 1>(ring_map, im, p, grid, s);
+    case 2: return launch_variant<false, 2>(ring_map, im, p, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace xc

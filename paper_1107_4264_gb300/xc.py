@@ -26,7 +26,8 @@ XC_ERR_TIMEOUT = 6
 XC_ERR_OOM = 7
 XC_ERR_NO_DEVICE = 8
 XC_OPT_ENGINE, XC_OPT_ACCUMULATE, XC_OPT_TIMEOUT_MS, XC_OPT_PROFILE = 1, 2, 3, 4
-XC_ENGINE_TENSOR, XC_ENGINE_FP32 = 0, 1
+(XC_ENGINE_TENSOR, XC_ENGINE_FP32, XC_ENGINE_TENSOR_2PASS, XC_ENGINE_TENSOR_1CTA,
+ XC_ENGINE_TENSOR_PAIR) = 0, 1, 2, 3, 4
 XC_CI8_MAX_NTIME = 66572
 
 # Symbols declared in include/xc.h (checked by the tests against the header).

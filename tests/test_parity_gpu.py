@@ -1,5 +1,6 @@
-"""GPU parity: both engines (tcgen05 tensor-core and FP32 CUDA-core) against
-the CPU oracle through the C ABI.
+"""GPU parity: every engine (fused tcgen05 planar complex form, the fused
+interleaved form on single CTAs and on CTA pairs, the two-pass tensor-core
+form and the FP32 CUDA-core form) against the CPU oracle through the C ABI.
 
 Integer input must match bit for bit.  Cases span several 128-row tiles,
 ragged station counts (partial tiles), single polarisation, sample counts
@@ -18,7 +19,9 @@ from paper_1107_4264_gb300 import synth, xc
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = [("tensor", xc.XC_ENGINE_TENSOR), ("fp32", xc.XC_ENGINE_FP32)]
+ENGINES = [("tensor", xc.XC_ENGINE_TENSOR), ("fp32", xc.XC_ENGINE_FP32),
+           ("tensor_2pass", xc.XC_ENGINE_TENSOR_2PASS), ("tensor_1cta", xc.XC_ENGINE_TENSOR_1CTA),
+           ("tensor_pair", xc.XC_ENGINE_TENSOR_PAIR)]
 
 
 @pytest.fixture(scope="module")
@@ -59,6 +62,9 @@ INT_CASES = [
     int_case("drain_T1025", 64, 2, 2, 1025, 8, -128, 127),
     int_case("all_minus128_T4096", 33, 2, 1, 4096, 0, fill=-128),
     int_case("all_127_T2048", 33, 2, 1, 2048, 0, fill=127),
+    # many channels: the fused engine's operand ring wraps several times
+    int_case("ring_wrap_N64_F100_T200", 64, 2, 100, 200, 9, -128, 127),
+    int_case("ring_wrap_N160_F40_T1100", 160, 2, 40, 1100, 10, -128, 127),
 ]
 
 

@@ -68,12 +68,18 @@ def test_noalloc_matches_xc_correlate_two_calls(dev):
 
 
 def test_noalloc_float_input_matches(dev):
-    x = synth.sky_voltages(300, 6, 40, 2, noise_sigma=0.7, nsrc=2, src_amp=1.0, seed=5353,
+    """Float input: both calls use fp16 operands with fp32 accumulation but
+    may sum in different orders, so they agree to the float tolerance the
+    parity tests use (per-channel Frobenius and max-normalised 1e-3)."""
+    from tests.test_parity_gpu import frob_and_maxnorm
+    N, P = 40, 2
+    x = synth.sky_voltages(300, 6, N, P, noise_sigma=0.7, nsrc=2, src_amp=1.0, seed=5353,
                            device=dev)
-    want = reference_output(x, "float32")
+    want = reference_output(x, "float32").cpu().double().numpy()
     for _ in range(2):
-        got = noalloc_output(x, "float32", dev)
-        torch.testing.assert_close(got, want, rtol=0, atol=0)
+        got = noalloc_output(x, "float32", dev).cpu().double().numpy()
+        frob, mx = frob_and_maxnorm(got, want, N, P)
+        assert frob <= 1e-3 and mx <= 1e-3, (frob, mx)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(dev):
