@@ -86,8 +86,7 @@ struct xc_handle {
   unsigned* counters = nullptr;
   unsigned* chan_amax = nullptr;  // [F] per-channel max |x| (planar engine)
   CUtensorMap ring_tmap;     // interleaved form: {Tp, R, ring_slots}
-  int planar_slots = 0;
-  CUtensorMap planar_tmap;   // planar form: {Tp, n, 2 * planar_slots}
+  int planar_slots = 0;       // planar form: xc::planar_slot_bytes() per slot
   // Two-pass engine (allocated when selected): fp16 operands [F][R][Tp].
   void* ws = nullptr;
   CUtensorMap tmap;
@@ -197,7 +196,7 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
       im = &in_map;
     }
     if (tm) tm->nkern = 1;
-    e = xc::launch_planar(&h->planar_tmap, im, X, s);
+    e = xc::launch_planar(im, X, s);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core X-engine launch");
     if (tm) cudaEventRecord(tm->ev[1], s);
     return succeed();
@@ -424,7 +423,9 @@ xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_d
   h->ring_slots = xc::xengine_ring_slots(h->g);
   h->planar_slots = xc::planar_ring_slots(h->g);
   const int slots = std::max(h->ring_slots, h->planar_slots);
-  e = cudaMalloc(&h->ring, static_cast<size_t>(slots) * R * Tp * 2);
+  const size_t ring_bytes = std::max(static_cast<size_t>(h->ring_slots) * R * Tp * 2,
+                                     static_cast<size_t>(h->planar_slots) * xc::planar_slot_bytes(h->g));
+  e = cudaMalloc(&h->ring, ring_bytes);
   if (e == cudaSuccess)
     e = cudaMalloc(reinterpret_cast<void**>(&h->counters), 2 * sizeof(unsigned) * slots);
   if (e == cudaSuccess)
@@ -434,8 +435,7 @@ xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_d
     release(h);
     return nullptr;
   }
-  if (encode_operand_map(&h->ring_tmap, h->ring, R, Tp, h->ring_slots) != XC_OK ||
-      encode_operand_map(&h->planar_tmap, h->ring, R / 2, Tp, 2LL * h->planar_slots) != XC_OK) {
+  if (encode_operand_map(&h->ring_tmap, h->ring, R, Tp, h->ring_slots) != XC_OK) {
     release(h);
     return nullptr;
   }

@@ -262,7 +262,9 @@ __device__ __forceinline__ bool claim_slot(const XeParams& p, int c, int cw, int
     conv_sync();
     if (*abort_flag) return false;
   }
-  fence_proxy_async_global();
+  // No proxy fence here: every TMA read of the slot's previous channel has
+  // completed (its data sat in shared memory before the MMA thread released
+  // done[slot]), so the generic writes that follow cannot reach it.
   return true;
 }
 

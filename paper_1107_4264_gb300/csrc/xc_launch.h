@@ -46,12 +46,12 @@ struct XeLaunch {
 };
 cudaError_t launch_xengine(const CUtensorMap* tmap, const XeLaunch& p, cudaStream_t s);
 // Planar complex form (separate real/imaginary fp16 planes, 4 MMAs per step
-// into D_re/D_im): `ring_map` is {Tp, n, 2*ring_slots} over the ring
-// [slots][2][n][Tp]; `in_map` (8-bit input only, may be NULL) is {R, F, T}
-// int8 in 128 x 1 x 64 boxes.
-cudaError_t launch_planar(const CUtensorMap* ring_map, const CUtensorMap* in_map, const XeLaunch& p,
-                          cudaStream_t s);
+// into D_re/D_im).  The ring holds planar_slot_bytes() per channel slot;
+// `in_map` (8-bit input with R % 16 == 0, else NULL) is {R, F, T} int8 in
+// 128 x 1 x 64 boxes.
+cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& p, cudaStream_t s);
 int planar_ring_slots(const Geometry& g);
+int64_t planar_slot_bytes(const Geometry& g);
 // Same as launch_xengine, on CTA pairs (tcgen05 cta_group::2, 256 x 256 blocks).
 cudaError_t launch_xengine_pair(const CUtensorMap* tmap, const XeLaunch& p, cudaStream_t s);
 // Ring slots for a geometry (2..16 channels, about 32 MiB).

@@ -30,10 +30,15 @@
 //
 // Operand formation (Sec. 4.1 input order, Sec. 5 8-bit samples): converter
 // warps form each channel's planes once into a ring of channel slots in
-// global memory that stays in L2 (the blocks of a channel read it back
-// through TMA): 8-bit input arrives by TMA in 128-row x 64-sample boxes,
-// other types and row counts by direct loads; a lane turns 4 rows (2 complex
-// inputs) x 64 samples into four 128-byte plane rows.  Ring protocol:
+// global memory that stays in L2; the blocks of a channel read it back with
+// bulk copies.  The ring holds operand tiles exactly as the MMA reads them:
+// per (slot, plane, 64-sample K-block, 128-input block) one 16 KiB tile in
+// the no-swizzle K-major canonical layout [8-sample chunk][128 inputs][8],
+// so a stage is four contiguous 16 KiB copies and a converter lane writing
+// one input's 16-byte chunk next to its neighbours' fills whole lines.
+// 8-bit input arrives by TMA in 128-row x 64-sample boxes (other types and
+// row counts by direct loads); lane l converts inputs l and l + 32 of a
+// 64-input half block.  Ring protocol:
 //   ready[slot] counts converted units (128 rows x 64 samples); channel c
 //     (generation c / slots of slot c % slots) is complete at
 //     ready >= (gen + 1) * units_per_channel;
@@ -43,7 +48,7 @@
 // so the ring cannot deadlock; every wait is bounded regardless.
 //
 // CTA roles (persistent, one CTA per SM, channel-major items):
-//   warp 0      TMA producer: 3 stages x (Ar, Ai, Br, Bi) 64-sample tiles
+//   warp 0      producer: 3 stages x (Ar, Ai, Br, Bi) 64-sample tiles (bulk copies)
 //   warp 1      MMA issuer; owns TMEM (2 sets x {D_re, D_im} x 128 columns)
 //   warps 2..5  epilogue
 //   warps 6..9  converters
@@ -51,6 +56,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "xc_launch.h"
@@ -70,8 +76,10 @@ constexpr int kStageBytes = 4 * kTileBytes;
 constexpr uint32_t kTmemCols = 512;         // 2 sets x (D_re, D_im) x 128
 constexpr uint32_t kIdesc = ptx::idesc_f16_f32(kBlk, kBlk);
 constexpr uint32_t kIdescNegB = kIdesc | (1u << 14);
-constexpr int kUnitRows = 128;  // converter unit: 128 real rows x 64 samples
+constexpr int kUnitRows = 128;  // converter unit: 128 real rows (64 inputs) x 64 samples
 constexpr int kUnitT = 64;
+constexpr uint32_t kChunkStride = kBlk * 16;  // bytes between 8-sample chunks of a tile (K)
+constexpr uint32_t kGroupStride = 8 * 16;     // bytes between 8-input groups of a tile (M/N)
 constexpr int kConvBufBytes = kUnitRows * kUnitT;  // int8 staging per converter warp
 constexpr int kConvBarrier = 1;
 
@@ -92,14 +100,14 @@ struct Params {
   int nkb;             // Tp / 64
   int is_int;          // 8-bit input: exact chunks from the channel's max |x|
   unsigned* amax;      // [F] max |x| per channel (8-bit input), zeroed by the host
-  __half* ring;        // [slots][2][n][Tp]
+  uint8_t* ring;       // tiles [slots][2][nkb][nib][8][128][8] fp16
+  int nib;             // 128-input blocks per channel
   int ring_slots;
   unsigned* ready;
   unsigned* done;
-  int row_units;       // ceil(R / 128)
+  int row_units;       // 64-input half blocks per channel = 2 * nib
   int units_per_chan;  // row_units * Tp / 64
   int tma_in;          // 8-bit input staged by TMA (else direct loads)
-  int vec4;            // R % 4 == 0 (direct-load path)
   unsigned long long timeout_ns;
   int* status;
 };
@@ -168,103 +176,39 @@ __device__ __forceinline__ bool channel_ready(const Params& p, int f, volatile i
 
 // -------------------------------------------------------------- converter
 
-template <int DT>
-struct Quad;
-template <>
-struct Quad<0> {
-  uint32_t w;
-};
-template <>
-struct Quad<1> {
-  uint2 w;
-};
-template <>
-struct Quad<2> {
-  float4 w;
-};
-
-template <int DT>
-__device__ __forceinline__ void load_quad(const void* in, int64_t idx, Quad<DT>& q) {
-  if constexpr (DT == 0) {
-    q.w = __ldg(reinterpret_cast<const uint32_t*>(static_cast<const int8_t*>(in) + idx));
-  } else if constexpr (DT == 1) {
-    q.w = __ldg(reinterpret_cast<const uint2*>(static_cast<const __half*>(in) + idx));
-  } else {
-    q.w = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(in) + idx));
-  }
-}
-
-template <int DT>
-__device__ __forceinline__ void zero_quad(Quad<DT>& q) {
-  if constexpr (DT == 0) {
-    q.w = 0u;
-  } else if constexpr (DT == 1) {
-    q.w = make_uint2(0u, 0u);
-  } else {
-    q.w = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
-// fp16x2 of (component j of sample a, component j of sample b).
-__device__ __forceinline__ uint32_t pair_i8(uint32_t a, uint32_t b, int j) {
+// fp16x2 of (component j of sample a, component j of sample b), 8-bit input.
+__device__ __forceinline__ uint32_t pair_i8(uint32_t a, uint32_t b, uint32_t j) {
   // Byte j of a into byte 0 and byte j of b into byte 2; 0x6400 | (x ^ 0x80)
   // is the fp16 value 1152 + x, so subtracting 1152 gives x exactly.
-  uint32_t d = __byte_perm(a, b, static_cast<uint32_t>(j) | (static_cast<uint32_t>(j + 4) << 8));
+  uint32_t d = __byte_perm(a, b, j | ((j + 4u) << 8));
   d = (d & 0x00FF00FFu) ^ 0x64806480u;
   __half2 h = *reinterpret_cast<__half2*>(&d);
   h = __hsub2(h, __half2(__float2half_rn(1152.f), __float2half_rn(1152.f)));
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-template <int DT>
-__device__ __forceinline__ uint32_t pair_half2(const Quad<DT>& a, const Quad<DT>& b, int j) {
-  if constexpr (DT == 0) {
-    return pair_i8(a.w, b.w, j);
-  } else if constexpr (DT == 1) {
-    const uint32_t wa = (j < 2) ? a.w.x : a.w.y;
-    const uint32_t wb = (j < 2) ? b.w.x : b.w.y;
-    return __byte_perm(wa, wb, (j & 1) ? 0x7632u : 0x5410u);
-  } else {
-    const float fa = (j == 0) ? a.w.x : (j == 1) ? a.w.y : (j == 2) ? a.w.z : a.w.w;
-    const float fb = (j == 0) ? b.w.x : (j == 1) ? b.w.y : (j == 2) ? b.w.z : b.w.w;
-    __half2 h = __floats2half2_rn(fa, fb);
-    return *reinterpret_cast<uint32_t*>(&h);
-  }
+// Byte address of tile (slot, plane, kb, ib) in the ring.
+__device__ __forceinline__ uint8_t* ring_tile(const Params& p, int slot, int plane, int kb, int ib) {
+  return p.ring + ((((static_cast<int64_t>(slot) * 2 + plane) * p.nkb + kb) * p.nib + ib) << 14);
 }
 
-template <int DT>
-__device__ __forceinline__ __half scalar_half(const void* in, int64_t idx) {
-  if constexpr (DT == 0) {
-    return __int2half_rn(static_cast<int>(static_cast<const int8_t*>(in)[idx]));
-  } else if constexpr (DT == 1) {
-    return static_cast<const __half*>(in)[idx];
-  } else {
-    return __float2half_rn(static_cast<const float*>(in)[idx]);
-  }
-}
-
-// Plane row of real input row r (r = 2a + c): ring row (slot, c, a).
-__device__ __forceinline__ __half* plane_row(const Params& p, int slot, int r) {
-  return p.ring + ((static_cast<int64_t>(slot) * 2 + (r & 1)) * p.n + (r >> 1)) * p.g.Tp;
-}
-
-// A batch: up to 4 consecutive 64-sample units of one channel and 128-row
-// block, one per converter warp; batches b = blockIdx.x + k * gridDim.x.
+// A unit: 64 inputs (half block hb) x 64 samples (K-block kb) of channel c.
+// A batch: up to 4 consecutive K-blocks of one half block, one per converter
+// warp; batches b = blockIdx.x + k * gridDim.x, in channel order.
 struct Batch {
-  int c, slot, rb, tb0, n;
+  int c, slot, hb, kb0, n;
 };
 
 __device__ __forceinline__ Batch batch_of(const Params& p, long long b) {
-  const int tblocks = p.g.Tp / kUnitT;
-  const int bpr = (tblocks + kNumConvWarps - 1) / kNumConvWarps;
+  const int bpr = (p.nkb + kNumConvWarps - 1) / kNumConvWarps;  // batches per half block
   const int bpc = bpr * p.row_units;
   Batch x;
   x.c = static_cast<int>(b / bpc);
   const int j = static_cast<int>(b % bpc);
   x.slot = x.c % p.ring_slots;
-  x.rb = j / bpr;
-  x.tb0 = (j % bpr) * kNumConvWarps;
-  x.n = min(kNumConvWarps, tblocks - x.tb0);
+  x.hb = j / bpr;
+  x.kb0 = (j % bpr) * kNumConvWarps;
+  x.n = min(kNumConvWarps, p.nkb - x.kb0);
   return x;
 }
 
@@ -281,60 +225,32 @@ __device__ __forceinline__ bool claim_slot(const Params& p, int c, int cw, int l
     conv_sync();
     if (*abort_flag) return false;
   }
-  fence_proxy_async_global();
+  // No proxy fence here: every bulk read of the slot's previous channel has
+  // completed (its data sat in shared memory before the MMA thread released
+  // done[slot]), so the generic writes that follow cannot reach it.
   return true;
 }
 
-// Write 4 real rows (r .. r+3) x 16 samples from 16 quads into the planes.
+// Complex sample (re, im) of input a at sample t, channel c, as fp32.
 template <int DT>
-__device__ __forceinline__ void store_group(const Params& p, int slot, int r, int tb,
-                                            const Quad<DT> (&q)[16]) {
-  if (r >= p.g.R) return;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint32_t h[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) h[i] = pair_half2<DT>(q[2 * i], q[2 * i + 1], j);
-    uint4* dst = reinterpret_cast<uint4*>(plane_row(p, slot, r + j) + tb);
-    dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
-    dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+__device__ __forceinline__ float2 load_cx(const Params& p, int c, int a, int t) {
+  const int64_t idx = (static_cast<int64_t>(t) * p.g.F + c) * p.n + a;
+  if constexpr (DT == 0) {
+    const char2 v = static_cast<const char2*>(p.in)[idx];
+    return make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+  } else if constexpr (DT == 1) {
+    return __half22float2(static_cast<const __half2*>(p.in)[idx]);
+  } else {
+    return static_cast<const float2*>(p.in)[idx];
   }
 }
 
-template <int DT>
-__device__ __forceinline__ void load_group(const Params& p, int c, int r, int tb, Quad<DT> (&q)[16]) {
-  const Geometry& g = p.g;
-  const bool row_ok = r < g.R;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int t = tb + i;
-    if (row_ok && t < g.T)
-      load_quad<DT>(p.in, (static_cast<int64_t>(t) * g.F + c) * g.R + r, q[i]);
-    else
-      zero_quad<DT>(q[i]);
-  }
-}
-
-template <int DT>
-__device__ __forceinline__ void convert_unit_scalar(const Params& p, int c, int slot, int r0, int t0) {
-  const Geometry& g = p.g;
-  for (int j = 0; j < 4; ++j) {
-    const int rr = r0 + j;
-    if (rr >= g.R) break;
-    __half* dst = plane_row(p, slot, rr) + t0;
-    for (int i = 0; i < kUnitT; ++i) {
-      const int t = t0 + i;
-      dst[i] = (t < g.T) ? scalar_half<DT>(p.in, (static_cast<int64_t>(t) * g.F + c) * g.R + rr)
-                         : __float2half_rn(0.f);
-    }
-  }
-}
-
-// Direct-load converter (any input type / row count).
+// Direct-load converter (any input type and row count): lane l loads the
+// complex samples of inputs l and l + 32 of the half block, 8 samples at a
+// time, and writes one 16-byte chunk per (input, plane).
 template <int DT>
 __device__ void converter_direct(const Params& p, int cw, int lane, volatile int* abort_flag) {
-  const int tblocks = p.g.Tp / kUnitT;
-  const int bpr = (tblocks + kNumConvWarps - 1) / kNumConvWarps;
+  const int bpr = (p.nkb + kNumConvWarps - 1) / kNumConvWarps;
   const long long total = static_cast<long long>(p.g.F) * bpr * p.row_units;
   int claimed = -1;
   for (long long b = blockIdx.x; b < total; b += gridDim.x) {
@@ -344,20 +260,32 @@ __device__ void converter_direct(const Params& p, int cw, int lane, volatile int
       claimed = x.c;
     }
     if (cw < x.n) {
-      const int r = x.rb * kUnitRows + 4 * lane;
-      const int t0 = (x.tb0 + cw) * kUnitT;
-      if (p.vec4) {
-        Quad<DT> qa[16], qb[16];
-        load_group<DT>(p, x.c, r, t0, qa);
-        load_group<DT>(p, x.c, r, t0 + 16, qb);
-        store_group<DT>(p, x.slot, r, t0, qa);
-        load_group<DT>(p, x.c, r, t0 + 32, qa);
-        store_group<DT>(p, x.slot, r, t0 + 16, qb);
-        load_group<DT>(p, x.c, r, t0 + 48, qb);
-        store_group<DT>(p, x.slot, r, t0 + 32, qa);
-        store_group<DT>(p, x.slot, r, t0 + 48, qb);
-      } else {
-        convert_unit_scalar<DT>(p, x.c, x.slot, r, t0);
+      const int kb = x.kb0 + cw;
+      const int ib = x.hb >> 1;
+      uint8_t* tre = ring_tile(p, x.slot, 0, kb, ib);
+      uint8_t* tim = ring_tile(p, x.slot, 1, kb, ib);
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int row = (x.hb & 1) * 64 + h * 32 + lane;  // row in the 128-input tile
+        const int a = x.hb * 64 + h * 32 + lane;          // input index
+#pragma unroll 1
+        for (int cc = 0; cc < 8; ++cc) {
+          uint32_t hr[4], hi[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int t = kb * kBK + cc * 8 + 2 * i;
+            float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+            if (a < p.n && t < p.g.T) v0 = load_cx<DT>(p, x.c, a, t);
+            if (a < p.n && t + 1 < p.g.T) v1 = load_cx<DT>(p, x.c, a, t + 1);
+            __half2 r2 = __floats2half2_rn(v0.x, v1.x);
+            __half2 i2 = __floats2half2_rn(v0.y, v1.y);
+            hr[i] = *reinterpret_cast<uint32_t*>(&r2);
+            hi[i] = *reinterpret_cast<uint32_t*>(&i2);
+          }
+          const uint32_t off = cc * kChunkStride + row * 16;
+          *reinterpret_cast<uint4*>(tre + off) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+          *reinterpret_cast<uint4*>(tim + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        }
       }
     }
     if (DT == 0 && cw == 0 && lane == 0) atomicMax(p.amax + x.c, 128u);  // no scan: worst case
@@ -369,20 +297,24 @@ __device__ void converter_direct(const Params& p, int cw, int lane, volatile int
 }
 
 // 8-bit converter with TMA-staged input: warp cw owns an 8 KiB staging
-// buffer ([64 samples][128 rows] int8) and always has its next unit's box in
-// flight while it converts the current one.
+// buffer ([64 samples][128 rows] int8, rows = 64 inputs x {re, im}) and
+// always has its next unit's box in flight while it converts the current one.
 __device__ void converter_tma(const Params& p, const CUtensorMap* in_map, uint32_t buf,
                               uint32_t bar, int cw, int lane, volatile int* abort_flag) {
-  const int tblocks = p.g.Tp / kUnitT;
-  const int bpr = (tblocks + kNumConvWarps - 1) / kNumConvWarps;
+  const int bpr = (p.nkb + kNumConvWarps - 1) / kNumConvWarps;
   const long long total = static_cast<long long>(p.g.F) * bpr * p.row_units;
   const ptx::WaitCtl wc{p.timeout_ns, p.status, abort_flag};
   auto issue = [&](const Batch& x) {
     if (lane == 0) {
       ptx::mbar_arrive_expect_tx(bar, kConvBufBytes);
-      ptx::tma_load_3d(buf, in_map, bar, x.rb * kUnitRows, x.c, (x.tb0 + cw) * kUnitT);
+      ptx::tma_load_3d(buf, in_map, bar, x.hb * kUnitRows, x.c, (x.kb0 + cw) * kUnitT);
     }
   };
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(__cvta_shared_to_generic(static_cast<size_t>(buf)));
+  // Lane l converts inputs l and l + 32: words l/2 and 16 + l/2 of each
+  // sample row, bytes 2 (l & 1) (re) and 2 (l & 1) + 1 (im).
+  const uint32_t jre = 2u * (lane & 1);
+  const int w0 = lane >> 1;
   uint32_t phase = 0;
   int claimed = -1;
   long long b = blockIdx.x;
@@ -403,41 +335,52 @@ __device__ void converter_tma(const Params& p, const CUtensorMap* in_map, uint32
       const bool got = ptx::wait_bounded(bar, phase, wc);
       if (!__all_sync(0xffffffffu, got)) return;
       phase ^= 1u;
-      // 64 samples of rows 4*lane .. 4*lane+3.
-      uint32_t w[kUnitT];
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(
-          __cvta_shared_to_generic(static_cast<size_t>(buf)));
+      // Both inputs' 64 samples into registers, then release the buffer.
+      uint32_t wa[kUnitT], wb[kUnitT];
 #pragma unroll
-      for (int i = 0; i < kUnitT; ++i) w[i] = src[i * (kUnitRows / 4) + lane];
+      for (int t = 0; t < kUnitT; ++t) {
+        wa[t] = src[t * (kUnitRows / 4) + w0];
+        wb[t] = src[t * (kUnitRows / 4) + 16 + w0];
+      }
       __syncwarp();
       ptx::fence_proxy_async_smem();
       if (has_next && cw < xn.n) issue(xn);
       // max |x| over the unit (zero-filled rows and samples contribute 0).
       unsigned m = 0;
 #pragma unroll
-      for (int i = 0; i < kUnitT; ++i) {
-        const uint32_t v = w[i];
+      for (int t = 0; t < kUnitT; ++t) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int b = static_cast<int>(static_cast<int8_t>((v >> (8 * j)) & 0xffu));
-          m = max(m, static_cast<unsigned>(b < 0 ? -b : b));
+        for (int k = 0; k < 2; ++k) {
+          const int va = static_cast<int>(static_cast<int8_t>((wa[t] >> (8 * (jre + k))) & 0xffu));
+          const int vb = static_cast<int>(static_cast<int8_t>((wb[t] >> (8 * (jre + k))) & 0xffu));
+          m = max(m, static_cast<unsigned>(max(va < 0 ? -va : va, vb < 0 ? -vb : vb)));
         }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
       if (lane == 0) atomicMax(p.amax + x.c, m);
-      const int r = x.rb * kUnitRows + 4 * lane;
-      if (r < p.g.R) {
-        const int t0 = (x.tb0 + cw) * kUnitT;
+      const int kb = x.kb0 + cw;
+      const int ib = x.hb >> 1;
+      uint8_t* tre = ring_tile(p, x.slot, 0, kb, ib);
+      uint8_t* tim = ring_tile(p, x.slot, 1, kb, ib);
+      const int row = (x.hb & 1) * 64 + lane;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          uint4* dst = reinterpret_cast<uint4*>(plane_row(p, x.slot, r + j) + t0);
-#pragma unroll
-          for (int s = 0; s < kUnitT / 8; ++s) {
-            dst[s] = make_uint4(pair_i8(w[8 * s + 0], w[8 * s + 1], j), pair_i8(w[8 * s + 2], w[8 * s + 3], j),
-                                pair_i8(w[8 * s + 4], w[8 * s + 5], j), pair_i8(w[8 * s + 6], w[8 * s + 7], j));
-          }
-        }
+      for (int cc = 0; cc < 8; ++cc) {
+        const uint32_t off = cc * kChunkStride + row * 16;
+        const uint32_t* A = wa + 8 * cc;
+        const uint32_t* B = wb + 8 * cc;
+        *reinterpret_cast<uint4*>(tre + off) =
+            make_uint4(pair_i8(A[0], A[1], jre), pair_i8(A[2], A[3], jre), pair_i8(A[4], A[5], jre),
+                       pair_i8(A[6], A[7], jre));
+        *reinterpret_cast<uint4*>(tim + off) =
+            make_uint4(pair_i8(A[0], A[1], jre + 1), pair_i8(A[2], A[3], jre + 1),
+                       pair_i8(A[4], A[5], jre + 1), pair_i8(A[6], A[7], jre + 1));
+        *reinterpret_cast<uint4*>(tre + off + 32 * 16) =
+            make_uint4(pair_i8(B[0], B[1], jre), pair_i8(B[2], B[3], jre), pair_i8(B[4], B[5], jre),
+                       pair_i8(B[6], B[7], jre));
+        *reinterpret_cast<uint4*>(tim + off + 32 * 16) =
+            make_uint4(pair_i8(B[0], B[1], jre + 1), pair_i8(B[2], B[3], jre + 1),
+                       pair_i8(B[4], B[5], jre + 1), pair_i8(B[6], B[7], jre + 1));
       }
     } else if (has_next && cw < xn.n) {
       issue(xn);
@@ -535,8 +478,7 @@ __device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint
 
 template <bool IS_INT, int DT>
 __global__ void __launch_bounds__(kThreads, 1)
-    planar_kernel(const __grid_constant__ CUtensorMap ring_map,
-                  const __grid_constant__ CUtensorMap in_map, const Params p) {
+    planar_kernel(const __grid_constant__ CUtensorMap in_map, const Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -584,7 +526,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      ptx::prefetch_tmap(&ring_map);
       int stage = 0;
       uint32_t phase = 0;
       int issued_phase[kStages];
@@ -612,11 +553,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t dst = sbase + stage * kStageBytes;
           const uint32_t fb = full_bar(stage);
           ptx::mbar_arrive_expect_tx(fb, diag ? 2 * kTileBytes : 4 * kTileBytes);
-          ptx::tma_load_3d(dst, &ring_map, fb, kb * kBK, by * kBlk, 2 * slot);
-          ptx::tma_load_3d(dst + kTileBytes, &ring_map, fb, kb * kBK, by * kBlk, 2 * slot + 1);
+          ptx::bulk_load(dst, ring_tile(p, slot, 0, kb, by), kTileBytes, fb);
+          ptx::bulk_load(dst + kTileBytes, ring_tile(p, slot, 1, kb, by), kTileBytes, fb);
           if (!diag) {
-            ptx::tma_load_3d(dst + 2 * kTileBytes, &ring_map, fb, kb * kBK, bx * kBlk, 2 * slot);
-            ptx::tma_load_3d(dst + 3 * kTileBytes, &ring_map, fb, kb * kBK, bx * kBlk, 2 * slot + 1);
+            ptx::bulk_load(dst + 2 * kTileBytes, ring_tile(p, slot, 0, kb, bx), kTileBytes, fb);
+            ptx::bulk_load(dst + 3 * kTileBytes, ring_tile(p, slot, 1, kb, bx), kTileBytes, fb);
           }
           issued_phase[stage] = static_cast<int>(phase);
           if (++stage == kStages) {
@@ -678,10 +619,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k) {
               const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
-              const uint64_t dar = ptx::sw128_kmajor_desc(ar + k * 32);
-              const uint64_t dai = ptx::sw128_kmajor_desc(ai + k * 32);
-              const uint64_t dbr = ptx::sw128_kmajor_desc(br + k * 32);
-              const uint64_t dbi = ptx::sw128_kmajor_desc(bi + k * 32);
+              // K-step k covers 8-sample chunks 2k and 2k + 1.
+              const uint32_t ko = k * 2 * kChunkStride;
+              const uint64_t dar = ptx::interleave_kmajor_desc(ar + ko, kChunkStride, kGroupStride);
+              const uint64_t dai = ptx::interleave_kmajor_desc(ai + ko, kChunkStride, kGroupStride);
+              const uint64_t dbr = ptx::interleave_kmajor_desc(br + ko, kChunkStride, kGroupStride);
+              const uint64_t dbi = ptx::interleave_kmajor_desc(bi + ko, kChunkStride, kGroupStride);
               ptx::mma_f16_ss(d_re, dar, dbr, kIdesc, acc);       // Re += Ar Br^T
               ptx::mma_f16_ss(d_re, dai, dbi, kIdesc, 1u);        // Re += Ai Bi^T
               ptx::mma_f16_ss(d_im, dai, dbr, kIdesc, acc);       // Im += Ai Br^T
@@ -786,46 +729,47 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <bool IS_INT, int DT>
-cudaError_t launch_variant(const CUtensorMap* ring_map, const CUtensorMap* in_map, const Params& p,
-                           int grid, cudaStream_t s) {
+cudaError_t launch_variant(const CUtensorMap* in_map, const Params& p, int grid, cudaStream_t s) {
   auto kern = planar_kernel<IS_INT, DT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThreads, kSmemBytes, s>>>(*ring_map, *in_map, p);
+  kern<<<grid, kThreads, kSmemBytes, s>>>(*in_map, p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+int64_t planar_slot_bytes(const Geometry& g) {
+  const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
+  return 2 * (g.Tp / kBK) * nib * kTileBytes;
+}
+
 int planar_ring_slots(const Geometry& g) {
-  const int64_t per = 2LL * g.N * g.P * g.Tp * 2;
-  int64_t n = (32ll << 20) / std::max<int64_t>(per, 1);
+  int64_t n = (32ll << 20) / std::max<int64_t>(planar_slot_bytes(g), 1);
   n = std::max<int64_t>(2, std::min<int64_t>(16, n));
   return static_cast<int>(std::min<int64_t>(n, g.F));
 }
 
-cudaError_t launch_planar(const CUtensorMap* ring_map, const CUtensorMap* in_map, const XeLaunch& L,
-                          cudaStream_t s) {
+cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, cudaStream_t s) {
   Params p;
   p.g = L.g;
   p.n = L.g.N * L.g.P;
   p.in = L.in;
   p.out = L.out;
   p.accumulate = L.accumulate;
-  const int nb = (p.n + kBlk - 1) / kBlk;
-  p.ntiles = nb * (nb + 1) / 2;
+  p.nib = (p.n + kBlk - 1) / kBlk;
+  p.ntiles = p.nib * (p.nib + 1) / 2;
   p.nitems = static_cast<long long>(p.ntiles) * L.g.F;
   p.nkb = L.g.Tp / kBK;
   p.is_int = L.in_dtype == 0 ? 1 : 0;
   p.amax = L.amax;
-  p.ring = static_cast<__half*>(L.ring);
+  p.ring = static_cast<uint8_t*>(L.ring);
   p.ring_slots = L.ring_slots;
   p.ready = L.counters;
   p.done = L.counters + L.ring_slots;
-  p.row_units = (L.g.R + kUnitRows - 1) / kUnitRows;
-  p.units_per_chan = p.row_units * (L.g.Tp / kUnitT);
+  p.row_units = 2 * p.nib;
+  p.units_per_chan = p.row_units * p.nkb;
   p.tma_in = (L.in_dtype == 0 && in_map != nullptr) ? 1 : 0;
-  p.vec4 = (L.g.R % 4 == 0) ? 1 : 0;
   p.timeout_ns = L.timeout_ns;
   p.status = L.status;
   if (p.nitems == 0 || p.nkb == 0) return cudaSuccess;
@@ -833,11 +777,13 @@ cudaError_t launch_planar(const CUtensorMap* ring_map, const CUtensorMap* in_map
   if (e == cudaSuccess && p.is_int) e = cudaMemsetAsync(L.amax, 0, sizeof(unsigned) * L.g.F, s);
   if (e != cudaSuccess) return e;
   const int grid = static_cast<int>(std::min<long long>(p.nitems, L.grid));
-  const CUtensorMap* im = in_map ? in_map : ring_map;  // unused when !tma_in
+  CUtensorMap unused;
+  const CUtensorMap* im = in_map ? in_map : &unused;  // read only when p.tma_in
+  if (!in_map) memset(&unused, 0, sizeof(unused));
   switch (L.in_dtype) {
-    case 0: return launch_variant<true, 0>(ring_map, im, p, grid, s);
-    case 1: return launch_variant<false, 1>(ring_map, im, p, grid, s);
-    case 2: return launch_variant<false, 2>(ring_map, im, p, grid, s);
+    case 0: return launch_variant<true, 0>(im, p, grid, s);
+    case 1: return launch_variant<false, 1>(im, p, grid, s);
+    case 2: return launch_variant<false, 2>(im, p, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -216,6 +216,26 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
          (static_cast<uint64_t>(2) << 61);                  // 128-byte swizzle
 }
 
+// Shared-memory matrix descriptor for a K-major operand tile in the
+// no-swizzle ("interleaved") canonical layout: 8-row x 16-byte core matrices
+// stored contiguously (128 B each); `lbo` = byte distance between core
+// matrices adjacent in K, `sbo` = between core matrices adjacent in M/N.
+__device__ __forceinline__ uint64_t interleave_kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) |
+         (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) |
+         (static_cast<uint64_t>(1) << 46);                  // descriptor version; layout 0
+}
+
+// Bulk copy (no tensor map) of `bytes` contiguous bytes global -> shared,
+// completing on `bar` (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
 // Instruction descriptor, kind::f16: fp16 A and B (K-major), fp32 D, M x N.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
   return (1u << 4) |                                  // D format: f32
