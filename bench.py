@@ -342,7 +342,7 @@ def run_xc(args):
             "workload": w.name, "nstation": w.nstation, "npol": w.npol, "nfreq": w.nfreq,
             "ntime": w.ntime, "integrations_per_step": nint, "input": "complex int8 [T][F][N][P][2]",
             "output": "int32 [F][N(N+1)/2][4][2], bit-exact",
-            "arithmetic": "int8 exact in fp16, tcgen05 fp32 accumulation, int32 drain every 1024 samples",
+            "arithmetic": "planar complex: int8 exact in fp16, tcgen05 fp32 accumulation in chunks with 2*max|x|^2*S <= 2^24 (exact), int32 output",
             "l2": "inputs larger than L2 (%.2f GB per integration, %.1f GB per step)"
                   % (w.ntime * w.nfreq * w.nstation * w.npol * 2 / 1e9,
                      nint * w.ntime * w.nfreq * w.nstation * w.npol * 2 / 1e9),

@@ -421,7 +421,7 @@ xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_d
     return nullptr;
   }
   h->ring_slots = xc::xengine_ring_slots(h->g);
-  h->planar_slots = xc::planar_ring_slots(h->g);
+  h->planar_slots = xc::planar_ring_slots(h->g, h->num_sms);
   const int slots = std::max(h->ring_slots, h->planar_slots);
   const size_t ring_bytes = std::max(static_cast<size_t>(h->ring_slots) * R * Tp * 2,
                                      static_cast<size_t>(h->planar_slots) * xc::planar_slot_bytes(h->g));

@@ -50,7 +50,7 @@ cudaError_t launch_xengine(const CUtensorMap* tmap, const XeLaunch& p, cudaStrea
 // `in_map` (8-bit input with R % 16 == 0, else NULL) is {R, F, T} int8 in
 // 128 x 1 x 64 boxes.
 cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& p, cudaStream_t s);
-int planar_ring_slots(const Geometry& g);
+int planar_ring_slots(const Geometry& g, int grid);
 int64_t planar_slot_bytes(const Geometry& g);
 // Same as launch_xengine, on CTA pairs (tcgen05 cta_group::2, 256 x 256 blocks).
 cudaError_t launch_xengine_pair(const CUtensorMap* tmap, const XeLaunch& p, cudaStream_t s);

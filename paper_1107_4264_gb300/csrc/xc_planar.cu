@@ -38,7 +38,8 @@
 // one input's 16-byte chunk next to its neighbours' fills whole lines.
 // 8-bit input arrives by TMA in 128-row x 64-sample boxes (other types and
 // row counts by direct loads); lane l converts inputs l and l + 32 of a
-// 64-input half block.  Ring protocol:
+// 64-input half block; each converter warp works through its own stream of
+// units.  Ring protocol:
 //   ready[slot] counts converted units (128 rows x 64 samples); channel c
 //     (generation c / slots of slot c % slots) is complete at
 //     ready >= (gen + 1) * units_per_channel;
@@ -81,7 +82,6 @@ constexpr int kUnitT = 64;
 constexpr uint32_t kChunkStride = kBlk * 16;  // bytes between 8-sample chunks of a tile (K)
 constexpr uint32_t kGroupStride = 8 * 16;     // bytes between 8-input groups of a tile (M/N)
 constexpr int kConvBufBytes = kUnitRows * kUnitT;  // int8 staging per converter warp
-constexpr int kConvBarrier = 1;
 
 constexpr int kConvOff = kStages * kStageBytes;
 constexpr int kBarOff = kConvOff + kNumConvWarps * kConvBufBytes;
@@ -192,43 +192,42 @@ __device__ __forceinline__ uint8_t* ring_tile(const Params& p, int slot, int pla
   return p.ring + ((((static_cast<int64_t>(slot) * 2 + plane) * p.nkb + kb) * p.nib + ib) << 14);
 }
 
-// A unit: 64 inputs (half block hb) x 64 samples (K-block kb) of channel c.
-// A batch: up to 4 consecutive K-blocks of one half block, one per converter
-// warp; batches b = blockIdx.x + k * gridDim.x, in channel order.
-struct Batch {
-  int c, slot, hb, kb0, n;
+// A unit: 64 inputs (half block hb) x 64 samples (K-block kb) of channel c,
+// units numbered channel-major with the K-block fastest.
+struct Unit {
+  int c, slot, hb, kb;
 };
 
-__device__ __forceinline__ Batch batch_of(const Params& p, long long b) {
-  const int bpr = (p.nkb + kNumConvWarps - 1) / kNumConvWarps;  // batches per half block
-  const int bpc = bpr * p.row_units;
-  Batch x;
-  x.c = static_cast<int>(b / bpc);
-  const int j = static_cast<int>(b % bpc);
+__device__ __forceinline__ Unit unit_of(const Params& p, long long u) {
+  Unit x;
+  x.c = static_cast<int>(u / p.units_per_chan);
+  const int w = static_cast<int>(u % p.units_per_chan);
   x.slot = x.c % p.ring_slots;
-  x.hb = j / bpr;
-  x.kb0 = (j % bpr) * kNumConvWarps;
-  x.n = min(kNumConvWarps, p.nkb - x.kb0);
+  x.hb = w / p.nkb;
+  x.kb = w % p.nkb;
   return x;
 }
 
-__device__ __forceinline__ void conv_sync() {
-  asm volatile("bar.sync %0, %1;" ::"r"(kConvBarrier), "r"(32 * kNumConvWarps));
-}
-
-__device__ __forceinline__ bool claim_slot(const Params& p, int c, int cw, int lane,
-                                           volatile int* abort_flag) {
+// Before a warp first writes channel c into its slot: the slot's previous
+// channel (c - ring_slots) must have been read by all of its blocks.
+__device__ __forceinline__ bool claim_slot_warp(const Params& p, int c, int lane,
+                                                volatile int* abort_flag) {
   const unsigned gen = static_cast<unsigned>(c / p.ring_slots);
-  if (gen > 0) {
-    if (cw == 0 && lane == 0)
-      wait_counter(p.done + (c % p.ring_slots), gen * static_cast<unsigned>(p.ntiles), p, abort_flag);
-    conv_sync();
-    if (*abort_flag) return false;
-  }
+  bool ok = true;
+  if (gen > 0 && lane == 0)
+    ok = wait_counter(p.done + (c % p.ring_slots), gen * static_cast<unsigned>(p.ntiles), p, abort_flag);
   // No proxy fence here: every bulk read of the slot's previous channel has
   // completed (its data sat in shared memory before the MMA thread released
   // done[slot]), so the generic writes that follow cannot reach it.
-  return true;
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Publish one converted unit: every writing lane orders its generic stores
+// before later async-proxy (bulk copy) reads, then one release.
+__device__ __forceinline__ void publish_unit(const Params& p, int slot, int lane) {
+  fence_proxy_async_global();
+  __syncwarp();
+  if (lane == 0) red_release_add(p.ready + slot, 1u);
 }
 
 // Complex sample (re, im) of input a at sample t, channel c, as fp32.
@@ -245,69 +244,79 @@ __device__ __forceinline__ float2 load_cx(const Params& p, int c, int a, int t) 
   }
 }
 
-// Direct-load converter (any input type and row count): lane l loads the
-// complex samples of inputs l and l + 32 of the half block, 8 samples at a
-// time, and writes one 16-byte chunk per (input, plane).
+// Direct-load converter (any input type and row count), independent warps:
+// lane l loads the complex samples of inputs l and l + 32 of the half block,
+// 16 samples (32 loads) in flight at a time, and writes one 16-byte chunk
+// per (input, plane, 8 samples).
 template <int DT>
 __device__ void converter_direct(const Params& p, int cw, int lane, volatile int* abort_flag) {
-  const int bpr = (p.nkb + kNumConvWarps - 1) / kNumConvWarps;
-  const long long total = static_cast<long long>(p.g.F) * bpr * p.row_units;
+  const long long total = static_cast<long long>(p.g.F) * p.units_per_chan;
+  const long long stride = static_cast<long long>(gridDim.x) * kNumConvWarps;
   int claimed = -1;
-  for (long long b = blockIdx.x; b < total; b += gridDim.x) {
-    const Batch x = batch_of(p, b);
+  for (long long u = static_cast<long long>(blockIdx.x) * kNumConvWarps + cw; u < total; u += stride) {
+    const Unit x = unit_of(p, u);
     if (x.c != claimed) {
-      if (!claim_slot(p, x.c, cw, lane, abort_flag)) return;
+      if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
       claimed = x.c;
     }
-    if (cw < x.n) {
-      const int kb = x.kb0 + cw;
-      const int ib = x.hb >> 1;
-      uint8_t* tre = ring_tile(p, x.slot, 0, kb, ib);
-      uint8_t* tim = ring_tile(p, x.slot, 1, kb, ib);
+    const int ib = x.hb >> 1;
+    uint8_t* tre = ring_tile(p, x.slot, 0, x.kb, ib);
+    uint8_t* tim = ring_tile(p, x.slot, 1, x.kb, ib);
+    const int a0 = x.hb * 64 + lane, a1 = a0 + 32;
+    const int row0 = (x.hb & 1) * 64 + lane;
 #pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        const int row = (x.hb & 1) * 64 + h * 32 + lane;  // row in the 128-input tile
-        const int a = x.hb * 64 + h * 32 + lane;          // input index
-#pragma unroll 1
-        for (int cc = 0; cc < 8; ++cc) {
-          uint32_t hr[4], hi[4];
+    for (int g = 0; g < kUnitT / 16; ++g) {
+      float2 v0[16], v1[16];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int t = kb * kBK + cc * 8 + 2 * i;
-            float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-            if (a < p.n && t < p.g.T) v0 = load_cx<DT>(p, x.c, a, t);
-            if (a < p.n && t + 1 < p.g.T) v1 = load_cx<DT>(p, x.c, a, t + 1);
-            __half2 r2 = __floats2half2_rn(v0.x, v1.x);
-            __half2 i2 = __floats2half2_rn(v0.y, v1.y);
-            hr[i] = *reinterpret_cast<uint32_t*>(&r2);
-            hi[i] = *reinterpret_cast<uint32_t*>(&i2);
-          }
-          const uint32_t off = cc * kChunkStride + row * 16;
-          *reinterpret_cast<uint4*>(tre + off) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-          *reinterpret_cast<uint4*>(tim + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      for (int i = 0; i < 16; ++i) {
+        const int t = x.kb * kBK + g * 16 + i;
+        v0[i] = (a0 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a0, t) : make_float2(0.f, 0.f);
+        v1[i] = (a1 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a1, t) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t off = (2 * g + h) * kChunkStride + row0 * 16;
+        uint32_t r0[4], i0[4], r1[4], i1[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          __half2 q;
+          q = __floats2half2_rn(v0[8 * h + 2 * k].x, v0[8 * h + 2 * k + 1].x);
+          r0[k] = *reinterpret_cast<uint32_t*>(&q);
+          q = __floats2half2_rn(v0[8 * h + 2 * k].y, v0[8 * h + 2 * k + 1].y);
+          i0[k] = *reinterpret_cast<uint32_t*>(&q);
+          q = __floats2half2_rn(v1[8 * h + 2 * k].x, v1[8 * h + 2 * k + 1].x);
+          r1[k] = *reinterpret_cast<uint32_t*>(&q);
+          q = __floats2half2_rn(v1[8 * h + 2 * k].y, v1[8 * h + 2 * k + 1].y);
+          i1[k] = *reinterpret_cast<uint32_t*>(&q);
         }
+        *reinterpret_cast<uint4*>(tre + off) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+        *reinterpret_cast<uint4*>(tim + off) = make_uint4(i0[0], i0[1], i0[2], i0[3]);
+        *reinterpret_cast<uint4*>(tre + off + 32 * 16) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+        *reinterpret_cast<uint4*>(tim + off + 32 * 16) = make_uint4(i1[0], i1[1], i1[2], i1[3]);
       }
     }
-    if (DT == 0 && cw == 0 && lane == 0) atomicMax(p.amax + x.c, 128u);  // no scan: worst case
-    fence_proxy_async_global();
-    conv_sync();
-    if (cw == 0 && lane == 0) red_release_add(p.ready + x.slot, static_cast<unsigned>(x.n));
+    if (DT == 0 && lane == 0) atomicMax(p.amax + x.c, 128u);  // no scan: worst case
+    publish_unit(p, x.slot, lane);
     if (*abort_flag) return;
   }
 }
 
-// 8-bit converter with TMA-staged input: warp cw owns an 8 KiB staging
-// buffer ([64 samples][128 rows] int8, rows = 64 inputs x {re, im}) and
-// always has its next unit's box in flight while it converts the current one.
+// 8-bit converter with TMA-staged input.  Each converter warp is an
+// independent worker on its own stream of units (u = global warp id + k *
+// warps, channel-major), with an 8 KiB staging buffer ([64 samples][128
+// rows] int8 = 64 inputs x {re, im}) that always holds its next unit's box
+// in flight while the current one is converted.  A warp claims a slot for
+// itself and publishes each unit on its own: no barrier couples the warps.
 __device__ void converter_tma(const Params& p, const CUtensorMap* in_map, uint32_t buf,
                               uint32_t bar, int cw, int lane, volatile int* abort_flag) {
-  const int bpr = (p.nkb + kNumConvWarps - 1) / kNumConvWarps;
-  const long long total = static_cast<long long>(p.g.F) * bpr * p.row_units;
+  const long long total = static_cast<long long>(p.g.F) * p.units_per_chan;
+  const long long stride = static_cast<long long>(gridDim.x) * kNumConvWarps;
   const ptx::WaitCtl wc{p.timeout_ns, p.status, abort_flag};
-  auto issue = [&](const Batch& x) {
+  auto issue = [&](long long u) {
+    const Unit x = unit_of(p, u);
     if (lane == 0) {
       ptx::mbar_arrive_expect_tx(bar, kConvBufBytes);
-      ptx::tma_load_3d(buf, in_map, bar, x.hb * kUnitRows, x.c, (x.kb0 + cw) * kUnitT);
+      ptx::tma_load_3d(buf, in_map, bar, x.hb * kUnitRows, x.c, x.kb * kUnitT);
     }
   };
   const uint32_t* src = reinterpret_cast<const uint32_t*>(__cvta_shared_to_generic(static_cast<size_t>(buf)));
@@ -317,77 +326,64 @@ __device__ void converter_tma(const Params& p, const CUtensorMap* in_map, uint32
   const int w0 = lane >> 1;
   uint32_t phase = 0;
   int claimed = -1;
-  long long b = blockIdx.x;
-  if (b < total) {
-    const Batch x0 = batch_of(p, b);
-    if (cw < x0.n) issue(x0);
-  }
-  for (; b < total; b += gridDim.x) {
-    const Batch x = batch_of(p, b);
-    const long long bn = b + gridDim.x;
-    const bool has_next = bn < total;
-    const Batch xn = batch_of(p, has_next ? bn : b);
+  long long u = static_cast<long long>(blockIdx.x) * kNumConvWarps + cw;
+  if (u < total) issue(u);
+  for (; u < total; u += stride) {
+    const Unit x = unit_of(p, u);
     if (x.c != claimed) {
-      if (!claim_slot(p, x.c, cw, lane, abort_flag)) return;
+      if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
       claimed = x.c;
     }
-    if (cw < x.n) {
-      const bool got = ptx::wait_bounded(bar, phase, wc);
-      if (!__all_sync(0xffffffffu, got)) return;
-      phase ^= 1u;
-      // Both inputs' 64 samples into registers, then release the buffer.
-      uint32_t wa[kUnitT], wb[kUnitT];
+    const bool got = ptx::wait_bounded(bar, phase, wc);
+    if (!__all_sync(0xffffffffu, got)) return;
+    phase ^= 1u;
+    // Both inputs' 64 samples into registers, then refill the buffer.
+    uint32_t wa[kUnitT], wb[kUnitT];
 #pragma unroll
-      for (int t = 0; t < kUnitT; ++t) {
-        wa[t] = src[t * (kUnitRows / 4) + w0];
-        wb[t] = src[t * (kUnitRows / 4) + 16 + w0];
-      }
-      __syncwarp();
-      ptx::fence_proxy_async_smem();
-      if (has_next && cw < xn.n) issue(xn);
-      // max |x| over the unit (zero-filled rows and samples contribute 0).
-      unsigned m = 0;
-#pragma unroll
-      for (int t = 0; t < kUnitT; ++t) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int va = static_cast<int>(static_cast<int8_t>((wa[t] >> (8 * (jre + k))) & 0xffu));
-          const int vb = static_cast<int>(static_cast<int8_t>((wb[t] >> (8 * (jre + k))) & 0xffu));
-          m = max(m, static_cast<unsigned>(max(va < 0 ? -va : va, vb < 0 ? -vb : vb)));
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) atomicMax(p.amax + x.c, m);
-      const int kb = x.kb0 + cw;
-      const int ib = x.hb >> 1;
-      uint8_t* tre = ring_tile(p, x.slot, 0, kb, ib);
-      uint8_t* tim = ring_tile(p, x.slot, 1, kb, ib);
-      const int row = (x.hb & 1) * 64 + lane;
-#pragma unroll
-      for (int cc = 0; cc < 8; ++cc) {
-        const uint32_t off = cc * kChunkStride + row * 16;
-        const uint32_t* A = wa + 8 * cc;
-        const uint32_t* B = wb + 8 * cc;
-        *reinterpret_cast<uint4*>(tre + off) =
-            make_uint4(pair_i8(A[0], A[1], jre), pair_i8(A[2], A[3], jre), pair_i8(A[4], A[5], jre),
-                       pair_i8(A[6], A[7], jre));
-        *reinterpret_cast<uint4*>(tim + off) =
-            make_uint4(pair_i8(A[0], A[1], jre + 1), pair_i8(A[2], A[3], jre + 1),
-                       pair_i8(A[4], A[5], jre + 1), pair_i8(A[6], A[7], jre + 1));
-        *reinterpret_cast<uint4*>(tre + off + 32 * 16) =
-            make_uint4(pair_i8(B[0], B[1], jre), pair_i8(B[2], B[3], jre), pair_i8(B[4], B[5], jre),
-                       pair_i8(B[6], B[7], jre));
-        *reinterpret_cast<uint4*>(tim + off + 32 * 16) =
-            make_uint4(pair_i8(B[0], B[1], jre + 1), pair_i8(B[2], B[3], jre + 1),
-                       pair_i8(B[4], B[5], jre + 1), pair_i8(B[6], B[7], jre + 1));
-      }
-    } else if (has_next && cw < xn.n) {
-      issue(xn);
+    for (int t = 0; t < kUnitT; ++t) {
+      wa[t] = src[t * (kUnitRows / 4) + w0];
+      wb[t] = src[t * (kUnitRows / 4) + 16 + w0];
     }
-    fence_proxy_async_global();
-    conv_sync();
-    if (cw == 0 && lane == 0) red_release_add(p.ready + x.slot, static_cast<unsigned>(x.n));
+    __syncwarp();
+    ptx::fence_proxy_async_smem();
+    if (u + stride < total) issue(u + stride);
+    // max |x| over the unit (zero-filled rows and samples contribute 0).
+    unsigned m = 0;
+#pragma unroll
+    for (int t = 0; t < kUnitT; ++t) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int va = static_cast<int>(static_cast<int8_t>((wa[t] >> (8 * (jre + k))) & 0xffu));
+        const int vb = static_cast<int>(static_cast<int8_t>((wb[t] >> (8 * (jre + k))) & 0xffu));
+        m = max(m, static_cast<unsigned>(max(va < 0 ? -va : va, vb < 0 ? -vb : vb)));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) atomicMax(p.amax + x.c, m);
+    const int ib = x.hb >> 1;
+    uint8_t* tre = ring_tile(p, x.slot, 0, x.kb, ib);
+    uint8_t* tim = ring_tile(p, x.slot, 1, x.kb, ib);
+    const int row = (x.hb & 1) * 64 + lane;
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const uint32_t off = cc * kChunkStride + row * 16;
+      const uint32_t* A = wa + 8 * cc;
+      const uint32_t* B = wb + 8 * cc;
+      *reinterpret_cast<uint4*>(tre + off) =
+          make_uint4(pair_i8(A[0], A[1], jre), pair_i8(A[2], A[3], jre), pair_i8(A[4], A[5], jre),
+                     pair_i8(A[6], A[7], jre));
+      *reinterpret_cast<uint4*>(tim + off) =
+          make_uint4(pair_i8(A[0], A[1], jre + 1), pair_i8(A[2], A[3], jre + 1),
+                     pair_i8(A[4], A[5], jre + 1), pair_i8(A[6], A[7], jre + 1));
+      *reinterpret_cast<uint4*>(tre + off + 32 * 16) =
+          make_uint4(pair_i8(B[0], B[1], jre), pair_i8(B[2], B[3], jre), pair_i8(B[4], B[5], jre),
+                     pair_i8(B[6], B[7], jre));
+      *reinterpret_cast<uint4*>(tim + off + 32 * 16) =
+          make_uint4(pair_i8(B[0], B[1], jre + 1), pair_i8(B[2], B[3], jre + 1),
+                     pair_i8(B[4], B[5], jre + 1), pair_i8(B[6], B[7], jre + 1));
+    }
+    publish_unit(p, x.slot, lane);
     if (*abort_flag) return;
   }
 }
@@ -744,9 +740,15 @@ int64_t planar_slot_bytes(const Geometry& g) {
   return 2 * (g.Tp / kBK) * nib * kTileBytes;
 }
 
-int planar_ring_slots(const Geometry& g) {
-  int64_t n = (32ll << 20) / std::max<int64_t>(planar_slot_bytes(g), 1);
-  n = std::max<int64_t>(2, std::min<int64_t>(16, n));
+int planar_ring_slots(const Geometry& g, int grid) {
+  // The persistent CTAs keep about grid / blocks_per_channel channels in
+  // flight; the converters need room ahead of them.
+  const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
+  const int64_t blocks = std::max<int64_t>(1, nib * (nib + 1) / 2);
+  const int64_t inflight = (grid + blocks - 1) / blocks;
+  int64_t n = (inflight * 8 + 4) / 5 + 4;
+  const int64_t cap = std::max<int64_t>(2, (256ll << 20) / std::max<int64_t>(planar_slot_bytes(g), 1));
+  n = std::max<int64_t>(4, std::min<int64_t>(std::min<int64_t>(64, cap), n));
   return static_cast<int>(std::min<int64_t>(n, g.F));
 }
 
