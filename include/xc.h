@@ -111,11 +111,32 @@ xc_status xc_correlate(xc_handle* h, const void* in, void* out, void* stream);
  * holding grad_out on the stored (lower-triangle) entries and zero elsewhere,
  * H = G + G^H and y = g*x (gains, unit unless set):
  *     grad_in[t][f] = conj(g) * (H_f y_f(t)).
- *   grad_out: device fp32, layout of `out`; grad_in: device fp32, layout of
- *   `in`.  Returns XC_ERR_UNSUPPORTED for XC_CI8 handles.
+ *   grad_out: device fp32, layout of `out`; in: the forward's input
+ *   (re-read, nothing of the forward is stored); grad_in: device fp32,
+ *   layout of `in`.  The gain gradient is kept for xc_get_grad_gains.
+ *   FP32 arithmetic.  Allocates an F*n*n complex workspace on first use.
+ *   Needs XC_CF32 input (XC_ERR_UNSUPPORTED otherwise).
  */
 xc_status xc_correlate_backward(xc_handle* h, const void* grad_out, const void* in, void* grad_in,
                                 void* stream);
+
+/*
+ * Complex gains (not in the paper; the calibration term of the
+ * differentiable form): one gain per (station, polarisation), applied to the
+ * voltages before correlation, y = g x, so that V_ab = g_a conj(g_b) V_ab
+ * of the ungained input.  Float input only (XC_CI8 handles return
+ * XC_ERR_UNSUPPORTED); used by the planar tensor-core and the FP32 engines.
+ *   gains: device cf32 [N][P] {re, im}, copied into the handle (synchronous);
+ *          NULL clears them (unit gains).
+ */
+xc_status xc_set_gains(xc_handle* h, const void* gains);
+
+/*
+ * Gradient of the loss with respect to the gains from the last
+ * xc_correlate_backward on `stream`: grad_g_a = sum_{f,t} conj(x_a) (H_f y)_a.
+ *   grad_gains: device cf32 [N][P] (written, stream-ordered).
+ */
+xc_status xc_get_grad_gains(xc_handle* h, void* grad_gains, void* stream);
 
 /* Free a handle (NULL-safe).  Synchronises the handle's own streams first. */
 void xc_destroy(xc_handle* h);

@@ -87,6 +87,11 @@ struct xc_handle {
   unsigned* chan_amax = nullptr;  // [F] per-channel max |x| (planar engine)
   CUtensorMap ring_tmap;     // interleaved form: {Tp, R, ring_slots}
   int planar_slots = 0;       // planar form: xc::planar_slot_bytes() per slot
+  // Complex gains (float input) and the adjoint's buffers, allocated on use.
+  void* gains = nullptr;     // cf32 [n]
+  int gains_set = 0;
+  void* adj_ws = nullptr;    // cf32 [F][n][n]: H_f = G_f + G_f^H
+  float* grad_g = nullptr;   // cf32 [n]
   // Two-pass engine (allocated when selected): fp16 operands [F][R][Tp].
   void* ws = nullptr;
   CUtensorMap tmap;
@@ -139,6 +144,9 @@ void release(xc_handle* h) {
   if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
   if (h->ws || h->d_status || h->ring) cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
+  if (h->gains) cudaFree(h->gains);
+  if (h->adj_ws) cudaFree(h->adj_ws);
+  if (h->grad_g) cudaFree(h->grad_g);
   if (h->ring) cudaFree(h->ring);
   if (h->counters) cudaFree(h->counters);
   if (h->chan_amax) cudaFree(h->chan_amax);
@@ -168,8 +176,11 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     if (!tm) return fail(XC_ERR_CUDA, "profiling event creation failed");
     cudaEventRecord(tm->ev[0], s);
   }
+  const void* gains = h->gains_set ? h->gains : nullptr;
+  if (gains && h->engine != XC_ENGINE_FP32 && h->engine != XC_ENGINE_TENSOR)
+    return fail(XC_ERR_UNSUPPORTED, "gains need the planar tensor-core or the FP32 engine");
   if (h->engine == XC_ENGINE_FP32) {
-    e = xc::launch_fp32_xengine(in, static_cast<int>(h->dtype), out, h->g, h->accumulate, s);
+    e = xc::launch_fp32_xengine(in, static_cast<int>(h->dtype), out, h->g, h->accumulate, gains, s);
     if (e != cudaSuccess) return cuda_fail(e, "fp32 X-engine launch");
     if (tm) cudaEventRecord(tm->ev[1], s);
     return succeed();
@@ -185,6 +196,7 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     X.ring_slots = h->planar_slots;
     X.counters = h->counters;
     X.amax = h->chan_amax;
+    X.gains = gains;
     X.grid = h->num_sms;
     X.timeout_ns = h->timeout_ns;
     X.status = h->d_status;
@@ -212,6 +224,7 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     X.ring_slots = h->ring_slots;
     X.counters = h->counters;
     X.amax = nullptr;
+    X.gains = nullptr;
     X.grid = h->num_sms;
     X.timeout_ns = h->timeout_ns;
     X.status = h->d_status;
@@ -487,10 +500,47 @@ xc_status xc_correlate(xc_handle* h, const void* in, void* out, void* stream) {
 
 xc_status xc_correlate_backward(xc_handle* h, const void* grad_out, const void* in, void* grad_in,
                                 void* stream) {
-  (void)stream;
   if (!h || !grad_out || !in || !grad_in) return fail(XC_ERR_INVALID_ARG, "NULL handle or buffer");
-  if (h->dtype == XC_CI8) return fail(XC_ERR_UNSUPPORTED, "backward needs float input");
-  return fail(XC_ERR_UNSUPPORTED, "backward is not built in this version");
+  if (h->dtype != XC_CF32) return fail(XC_ERR_UNSUPPORTED, "backward needs XC_CF32 input");
+  if (!aligned16(grad_out) || !aligned16(in) || !aligned16(grad_in))
+    return fail(XC_ERR_ALIGNMENT, "buffers must be 16-byte aligned");
+  const int64_t n = static_cast<int64_t>(h->g.N) * h->g.P;
+  cudaError_t e = cudaSuccess;
+  if (!h->adj_ws) e = cudaMalloc(&h->adj_ws, static_cast<size_t>(h->g.F) * n * n * 8);
+  if (e == cudaSuccess && !h->grad_g) e = cudaMalloc(reinterpret_cast<void**>(&h->grad_g), 8 * n);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint workspace");
+  e = xc::launch_adjoint(grad_out, in, h->gains_set ? h->gains : nullptr, grad_in, h->grad_g,
+                         h->adj_ws, h->g, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  return succeed();
+}
+
+xc_status xc_set_gains(xc_handle* h, const void* gains) {
+  if (!h) return fail(XC_ERR_INVALID_ARG, "NULL handle");
+  if (!gains) {
+    h->gains_set = 0;
+    return succeed();
+  }
+  if (h->dtype == XC_CI8) return fail(XC_ERR_UNSUPPORTED, "gains need float input");
+  const size_t bytes = static_cast<size_t>(h->g.N) * h->g.P * 8;
+  cudaError_t e = cudaSuccess;
+  if (!h->gains) e = cudaMalloc(&h->gains, bytes);
+  // Work already queued may still read the previous gains.
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(h->gains, gains, bytes, cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "set gains");
+  h->gains_set = 1;
+  return succeed();
+}
+
+xc_status xc_get_grad_gains(xc_handle* h, void* grad_gains, void* stream) {
+  if (!h || !grad_gains) return fail(XC_ERR_INVALID_ARG, "NULL handle or buffer");
+  const size_t bytes = static_cast<size_t>(h->g.N) * h->g.P * 8;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = h->grad_g ? cudaMemcpyAsync(grad_gains, h->grad_g, bytes, cudaMemcpyDeviceToDevice, s)
+                            : cudaMemsetAsync(grad_gains, 0, bytes, s);
+  if (e != cudaSuccess) return cuda_fail(e, "grad gains");
+  return succeed();
 }
 
 xc_status xc_kernel_times(xc_handle* h, double* ms, long long* launches, int reset) {

@@ -93,7 +93,7 @@ __device__ __forceinline__ void fetch8(const void* in, const Geometry& g, int n,
 template <int DT>
 __global__ void __launch_bounds__(kThreads, 2)
     fp32_xengine_kernel(const void* __restrict__ in, void* __restrict__ out, Geometry g,
-                        int accumulate, int vec) {
+                        int accumulate, int vec, const float2* __restrict__ gains) {
   extern __shared__ __align__(16) float2 sm[];  // [buf][row|col][kTK][kTile]
   const int tx = threadIdx.x & 15;
   const int ty = threadIdx.x >> 4;
@@ -110,9 +110,26 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int seg = threadIdx.x & 7;
 
   float2 pre_r[8], pre_c[8];
+  // Gains (float input only) y = g x, applied as samples are fetched.
+  float2 gr[8], gc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int ar = row0 + seg * 8 + i, ac = col0 + seg * 8 + i;
+    gr[i] = (gains && ar < n) ? gains[ar] : make_float2(1.f, 0.f);
+    gc[i] = (gains && ac < n) ? gains[ac] : make_float2(1.f, 0.f);
+  }
+  auto apply = [&](float2 (&v)[8], const float2 (&gv)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      v[i] = make_float2(gv[i].x * v[i].x - gv[i].y * v[i].y, gv[i].x * v[i].y + gv[i].y * v[i].x);
+  };
   auto fetch = [&](int t0) {
     fetch8<DT>(in, g, n, f, t0 + lt, row0 + seg * 8, vec, pre_r);
     if (!diag) fetch8<DT>(in, g, n, f, t0 + lt, col0 + seg * 8, vec, pre_c);
+    if (DT != 0 && gains) {
+      apply(pre_r, gr);
+      if (!diag) apply(pre_c, gc);
+    }
   };
   auto stash = [&](int buf) {
     float2* rdst = sm + ((buf * 2 + 0) * kTK + lt) * kTile + seg * 8;
@@ -221,7 +238,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 }  // namespace
 
 cudaError_t launch_fp32_xengine(const void* in, int in_dtype, void* out, const Geometry& g,
-                                int accumulate, cudaStream_t s) {
+                                int accumulate, const void* gains_v, cudaStream_t s) {
+  const float2* gains = static_cast<const float2*>(gains_v);
   const int n = g.N * g.P;
   const int nb = (n + kTile - 1) / kTile;
   const long long ntiles = static_cast<long long>(nb) * (nb + 1) / 2;
@@ -236,17 +254,17 @@ cudaError_t launch_fp32_xengine(const void* in, int in_dtype, void* out, const G
     case 0:
       e = cudaFuncSetAttribute(fp32_xengine_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
       if (e != cudaSuccess) return e;
-      fp32_xengine_kernel<0><<<grid, kThreads, kSmemBytes, s>>>(in, out, g, accumulate, vec);
+      fp32_xengine_kernel<0><<<grid, kThreads, kSmemBytes, s>>>(in, out, g, accumulate, vec, gains);
       break;
     case 1:
       e = cudaFuncSetAttribute(fp32_xengine_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
       if (e != cudaSuccess) return e;
-      fp32_xengine_kernel<1><<<grid, kThreads, kSmemBytes, s>>>(in, out, g, accumulate, vec);
+      fp32_xengine_kernel<1><<<grid, kThreads, kSmemBytes, s>>>(in, out, g, accumulate, vec, gains);
       break;
     case 2:
       e = cudaFuncSetAttribute(fp32_xengine_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
       if (e != cudaSuccess) return e;
-      fp32_xengine_kernel<2><<<grid, kThreads, kSmemBytes, s>>>(in, out, g, accumulate, vec);
+      fp32_xengine_kernel<2><<<grid, kThreads, kSmemBytes, s>>>(in, out, g, accumulate, vec, gains);
       break;
     default:
       return cudaErrorInvalidValue;

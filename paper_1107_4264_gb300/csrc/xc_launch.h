@@ -40,6 +40,7 @@ struct XeLaunch {
   int ring_slots;
   unsigned* counters;  // 2 * ring_slots, zeroed by the launcher on `s`
   unsigned* amax;      // [F] per-channel max |x| (planar engine, 8-bit input)
+  const void* gains;   // cf32 [N][P] applied to float input (planar engine), or NULL
   int grid;
   unsigned long long timeout_ns;
   int* status;
@@ -57,9 +58,16 @@ cudaError_t launch_xengine_pair(const CUtensorMap* tmap, const XeLaunch& p, cuda
 // Ring slots for a geometry (2..16 channels, about 32 MiB).
 int xengine_ring_slots(const Geometry& g);
 
-// FP32 CUDA-core X-engine (comparator) directly from the input.
+// FP32 CUDA-core X-engine (comparator) directly from the input; `gains`
+// (cf32 [N][P], float input only) may be NULL.
 cudaError_t launch_fp32_xengine(const void* in, int in_dtype, void* out, const Geometry& g,
-                                int accumulate, cudaStream_t s);
+                                int accumulate, const void* gains, cudaStream_t s);
+
+// Adjoint of the float forward: H_f = G_f + G_f^H into `h_ws` ([F][n][n]
+// cf32), grad_in = conj(g) H_f (g x) (cf32, layout of the input) and
+// grad_g = sum conj(x) H_f (g x) (cf32 [n], may be NULL).
+cudaError_t launch_adjoint(const void* grad_out, const void* in, const void* gains, void* grad_in,
+                           float* grad_g, void* h_ws, const Geometry& g, cudaStream_t s);
 
 // Record `s` and a printf-style message as this thread's last error
 // (xc_last_error / xc_last_error_message); returns s.

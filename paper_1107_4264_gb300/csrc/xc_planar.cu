@@ -100,6 +100,7 @@ struct Params {
   int nkb;             // Tp / 64
   int is_int;          // 8-bit input: exact chunks from the channel's max |x|
   unsigned* amax;      // [F] max |x| per channel (8-bit input), zeroed by the host
+  const float2* gains; // [n] complex gains applied to float input (y = g x), or NULL
   uint8_t* ring;       // tiles [slots][2][nkb][nib][8][128][8] fp16
   int nib;             // 128-input blocks per channel
   int ring_slots;
@@ -272,6 +273,16 @@ __device__ void converter_direct(const Params& p, int cw, int lane, volatile int
         const int t = x.kb * kBK + g * 16 + i;
         v0[i] = (a0 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a0, t) : make_float2(0.f, 0.f);
         v1[i] = (a1 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a1, t) : make_float2(0.f, 0.f);
+      }
+      if (DT != 0 && p.gains) {
+        // y = g x for float input (gains are not defined for 8-bit input).
+        const float2 g0 = a0 < p.n ? p.gains[a0] : make_float2(0.f, 0.f);
+        const float2 g1 = a1 < p.n ? p.gains[a1] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          v0[i] = make_float2(g0.x * v0[i].x - g0.y * v0[i].y, g0.x * v0[i].y + g0.y * v0[i].x);
+          v1[i] = make_float2(g1.x * v1[i].x - g1.y * v1[i].y, g1.x * v1[i].y + g1.y * v1[i].x);
+        }
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -765,6 +776,7 @@ cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, cudaStre
   p.nkb = L.g.Tp / kBK;
   p.is_int = L.in_dtype == 0 ? 1 : 0;
   p.amax = L.amax;
+  p.gains = static_cast<const float2*>(L.gains);
   p.ring = static_cast<uint8_t*>(L.ring);
   p.ring_slots = L.ring_slots;
   p.ready = L.counters;

@@ -35,7 +35,7 @@ EXPORTS = [
     "xc_create", "xc_correlate", "xc_correlate_backward", "xc_destroy", "xc_last_error",
     "xc_last_error_message", "xc_status_string", "xc_set_option", "xc_synchronize",
     "xc_correlate_stream", "xc_input_bytes", "xc_output_bytes", "xc_tri_index", "xc_tri_coords",
-    "xc_version", "xc_kernel_times", "xc_correlate_noalloc",
+    "xc_version", "xc_kernel_times", "xc_correlate_noalloc", "xc_set_gains", "xc_get_grad_gains",
 ]
 
 _lib: Optional[ctypes.CDLL] = None
@@ -68,6 +68,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "xc_kernel_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                              i32], i32),
         "xc_correlate_noalloc": ([i32, i32, i32, i32, i32, vp, vp, vp, vp], i32),
+        "xc_set_gains": ([vp, vp], i32),
+        "xc_get_grad_gains": ([vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -169,6 +171,14 @@ def xc_kernel_times(h: int, reset: bool = True):
     return (ms[0], ms[1]), (n[0], n[1])
 
 
+def xc_set_gains(h: int, gains_ptr: int) -> int:
+    return load().xc_set_gains(h, gains_ptr or None)
+
+
+def xc_get_grad_gains(h: int, grad_ptr: int, stream: int = 0) -> int:
+    return load().xc_get_grad_gains(h, grad_ptr, stream)
+
+
 XC_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 
@@ -254,6 +264,32 @@ class Correlator:
                                    self._stream(stream)))
         return out
 
+    def set_gains(self, gains) -> None:
+        """Complex gains [N][P][2] float32 on the device (None clears them)."""
+        if gains is None:
+            _check(xc_set_gains(self.h, 0))
+            return
+        g = gains.detach().to(self._torch.float32).contiguous()
+        assert g.is_cuda and tuple(g.shape) == (self.nstation, self.npol, 2), g.shape
+        _check(xc_set_gains(self.h, g.data_ptr()))
+
+    def correlate_backward(self, grad_out, x, grad_in=None, stream=None):
+        """grad_in = conj(g) (G + G^H)(g x) for float32 input; returns grad_in."""
+        assert grad_out.is_cuda and grad_out.is_contiguous() and grad_out.dtype == self._torch.float32
+        assert x.is_cuda and x.is_contiguous() and x.dtype == self._torch.float32
+        if grad_in is None:
+            grad_in = self._torch.empty_like(x)
+        _check(xc_correlate_backward(self.h, grad_out.data_ptr(), x.data_ptr(), grad_in.data_ptr(),
+                                     self._stream(stream)))
+        return grad_in
+
+    def grad_gains(self, stream=None):
+        """Gain gradient [N][P][2] from the last correlate_backward."""
+        out = self._torch.empty((self.nstation, self.npol, 2), dtype=self._torch.float32,
+                                device=self._torch.device("cuda"))
+        _check(xc_get_grad_gains(self.h, out.data_ptr(), self._stream(stream)))
+        return out
+
     def kernel_times(self, reset: bool = True):
         return xc_kernel_times(self.h, reset)
 
@@ -270,3 +306,32 @@ class Correlator:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ autograd
+
+
+def correlate_autograd(engine: "Correlator", x, gains):
+    """Visibilities of float32 voltages ``x[T][F][N][P][2]`` with complex gains
+    ``gains[N][P][2]`` applied first, differentiable in both (backward through
+    the library's adjoint kernel; the forward's input is re-read, nothing
+    else is stored)."""
+    import torch
+
+    class _Correlate(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, xx, gg):
+            engine.set_gains(gg)
+            out = engine.correlate(xx.detach().contiguous())
+            ctx.save_for_backward(xx, gg)
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            xx, gg = ctx.saved_tensors
+            engine.set_gains(gg)
+            grad_x = engine.correlate_backward(grad_out.contiguous(), xx.detach().contiguous())
+            grad_g = engine.grad_gains()
+            return grad_x, grad_g
+
+    return _Correlate.apply(x, gains)
