@@ -155,8 +155,28 @@ enum {
   XC_OPT_ENGINE = 1,     /* XC_ENGINE_TENSOR (default) or XC_ENGINE_FP32 */
   XC_OPT_ACCUMULATE = 2, /* 0: out = V (default); 1: out += V */
   XC_OPT_TIMEOUT_MS = 3, /* bound on any in-kernel wait, milliseconds (default 2000) */
-  XC_OPT_PROFILE = 4     /* 1: time every kernel with CUDA events (see xc_kernel_times) */
+  XC_OPT_PROFILE = 4,    /* 1: time every kernel with CUDA events (see xc_kernel_times) */
+  XC_OPT_PRECISION = 5,  /* float input, XC_ENGINE_TENSOR: XC_PREC_* (default FP16) */
+  XC_OPT_FP64_BLOCK = 6  /* float input, XC_ENGINE_TENSOR: T_blk > 0 enables FP64 block sums */
 };
+/* Operand precision of float input on XC_ENGINE_TENSOR (Sec. 5 leaves the
+ * precision of float voltages open; 8-bit input is always exact).  Every
+ * form scales each (channel, input) by a power of two 2^-e chosen from a
+ * pre-pass over the integration (largest component of g x), so any finite
+ * fp32 input is in range, and undoes it exactly in the epilogue; all forms
+ * accumulate in fp32.
+ *   XC_PREC_FP16: fp16 operands (11-bit significand).
+ *   XC_PREC_HILO: y 2^-e = h + l with h, l fp16; V from h h^H + l h^H + h l^H
+ *     (the l l^H term is dropped): about 22 significant bits, 3x the MMAs.
+ *   XC_PREC_FP8 : e4m3 operands (4-bit significand), tcgen05 kind::f8f6f4.
+ * FP64 block sums (XC_OPT_FP64_BLOCK = T_blk, a multiple of 64, 0 = off):
+ * the fp32 accumulator of each T_blk-sample block is added into a float64
+ * running sum that the handle owns (allocated on first use, 16 bytes per
+ * visibility); `out` receives its fp32 rounding after every call.  With
+ * XC_OPT_ACCUMULATE = 1 the running sum continues across calls (the caller's
+ * `out` is not read); with 0 it restarts every call.  Setting the option to a
+ * positive value zeroes the running sum (after waiting for the device). */
+enum { XC_PREC_FP16 = 0, XC_PREC_HILO = 1, XC_PREC_FP8 = 2 };
 /* Engines:
  *   XC_ENGINE_TENSOR (default): one fused persistent tcgen05 kernel in
  *     planar complex form (real and imaginary fp16 operand planes, four MMAs

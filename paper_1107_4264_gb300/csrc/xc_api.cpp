@@ -87,6 +87,13 @@ struct xc_handle {
   unsigned* chan_amax = nullptr;  // [F] per-channel max |x| (planar engine)
   CUtensorMap ring_tmap;     // interleaved form: {Tp, R, ring_slots}
   int planar_slots = 0;       // planar form: xc::planar_slot_bytes() per slot
+  size_t ring_bytes = 0;
+  // Float input on the planar engine: operand precision, scale pre-pass
+  // buffer [F][n] and the FP64 block sums (allocated on use).
+  int precision = XC_PREC_FP16;
+  int fp64_block = 0;
+  unsigned* in_amax = nullptr;
+  double* acc64 = nullptr;
   // Complex gains (float input) and the adjoint's buffers, allocated on use.
   void* gains = nullptr;     // cf32 [n]
   int gains_set = 0;
@@ -150,6 +157,8 @@ void release(xc_handle* h) {
   if (h->ring) cudaFree(h->ring);
   if (h->counters) cudaFree(h->counters);
   if (h->chan_amax) cudaFree(h->chan_amax);
+  if (h->in_amax) cudaFree(h->in_amax);
+  if (h->acc64) cudaFree(h->acc64);
   if (h->d_status) cudaFree(h->d_status);
   cudaSetDevice(cur);
   delete h;
@@ -179,6 +188,8 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
   const void* gains = h->gains_set ? h->gains : nullptr;
   if (gains && h->engine != XC_ENGINE_FP32 && h->engine != XC_ENGINE_TENSOR)
     return fail(XC_ERR_UNSUPPORTED, "gains need the planar tensor-core or the FP32 engine");
+  if ((h->precision != XC_PREC_FP16 || h->fp64_block) && h->engine != XC_ENGINE_TENSOR)
+    return fail(XC_ERR_UNSUPPORTED, "precision forms and FP64 block sums need XC_ENGINE_TENSOR");
   if (h->engine == XC_ENGINE_FP32) {
     e = xc::launch_fp32_xengine(in, static_cast<int>(h->dtype), out, h->g, h->accumulate, gains, s);
     if (e != cudaSuccess) return cuda_fail(e, "fp32 X-engine launch");
@@ -197,6 +208,10 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     X.counters = h->counters;
     X.amax = h->chan_amax;
     X.gains = gains;
+    X.fmt = h->precision;
+    X.in_amax = h->in_amax;
+    X.acc64 = h->fp64_block ? h->acc64 : nullptr;
+    X.f64_block = h->fp64_block;
     X.grid = h->num_sms;
     X.timeout_ns = h->timeout_ns;
     X.status = h->d_status;
@@ -434,15 +449,19 @@ xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_d
     return nullptr;
   }
   h->ring_slots = xc::xengine_ring_slots(h->g);
-  h->planar_slots = xc::planar_ring_slots(h->g, h->num_sms);
-  const int slots = std::max(h->ring_slots, h->planar_slots);
-  const size_t ring_bytes = std::max(static_cast<size_t>(h->ring_slots) * R * Tp * 2,
-                                     static_cast<size_t>(h->planar_slots) * xc::planar_slot_bytes(h->g));
-  e = cudaMalloc(&h->ring, ring_bytes);
+  h->planar_slots = xc::planar_ring_slots(h->g, h->num_sms, XC_PREC_FP16);
+  const int slots = std::max({h->ring_slots, h->planar_slots, xc::kMaxRingSlots});
+  h->ring_bytes = std::max(static_cast<size_t>(h->ring_slots) * R * Tp * 2,
+                           static_cast<size_t>(h->planar_slots) *
+                               xc::planar_slot_bytes(h->g, XC_PREC_FP16));
+  e = cudaMalloc(&h->ring, h->ring_bytes);
   if (e == cudaSuccess)
     e = cudaMalloc(reinterpret_cast<void**>(&h->counters), 2 * sizeof(unsigned) * slots);
   if (e == cudaSuccess)
     e = cudaMalloc(reinterpret_cast<void**>(&h->chan_amax), sizeof(unsigned) * nfreq);
+  if (e == cudaSuccess && in_dtype != XC_CI8)
+    e = cudaMalloc(reinterpret_cast<void**>(&h->in_amax),
+                   sizeof(unsigned) * static_cast<size_t>(nfreq) * nstation * npol);
   if (e != cudaSuccess) {
     cuda_fail(e, "operand ring allocation");
     release(h);
@@ -486,6 +505,53 @@ xc_status xc_set_option(xc_handle* h, int key, long long value) {
       if (value <= 0 || value > 3600LL * 1000) return fail(XC_ERR_INVALID_ARG, "bad timeout");
       h->timeout_ns = static_cast<unsigned long long>(value) * 1000000ull;
       return succeed();
+    case XC_OPT_PRECISION: {
+      if (value != XC_PREC_FP16 && value != XC_PREC_HILO && value != XC_PREC_FP8)
+        return fail(XC_ERR_INVALID_ARG, "unknown precision %lld", value);
+      if (h->dtype == XC_CI8 && value != XC_PREC_FP16)
+        return fail(XC_ERR_UNSUPPORTED, "8-bit input is exact; precision forms apply to float input");
+      const int fmt = static_cast<int>(value);
+      const int slots = xc::planar_ring_slots(h->g, h->num_sms, fmt);
+      const size_t need = static_cast<size_t>(slots) * xc::planar_slot_bytes(h->g, fmt);
+      if (need > h->ring_bytes) {
+        // Work already queued may still use the ring.
+        cudaError_t e = cudaDeviceSynchronize();
+        void* ring = nullptr;
+        if (e == cudaSuccess) e = cudaMalloc(&ring, need);
+        if (e != cudaSuccess) return cuda_fail(e, "operand ring reallocation");
+        xc_status st = encode_operand_map(&h->ring_tmap, ring, h->g.R, h->g.Tp, h->ring_slots);
+        if (st != XC_OK) {
+          cudaFree(ring);
+          return st;
+        }
+        cudaFree(h->ring);
+        h->ring = ring;
+        h->ring_bytes = need;
+      }
+      h->precision = fmt;
+      h->planar_slots = slots;
+      return succeed();
+    }
+    case XC_OPT_FP64_BLOCK: {
+      if (value < 0 || value % 64 != 0 || value > (1LL << 30))
+        return fail(XC_ERR_INVALID_ARG, "FP64_BLOCK must be 0 or a positive multiple of 64");
+      if (value > 0 && h->dtype == XC_CI8)
+        return fail(XC_ERR_UNSUPPORTED, "8-bit input is exact in int32; FP64 block sums apply to float input");
+      if (value > 0) {
+        // The running sum starts at zero whenever block sums are (re)enabled.
+        cudaError_t e = cudaSuccess;
+        if (!h->acc64) {
+          e = cudaMalloc(reinterpret_cast<void**>(&h->acc64), h->out_bytes * 2);
+          if (e != cudaSuccess) h->acc64 = nullptr;
+        } else {
+          e = cudaDeviceSynchronize();  // queued work may still use the sums
+        }
+        if (e == cudaSuccess) e = cudaMemset(h->acc64, 0, h->out_bytes * 2);
+        if (e != cudaSuccess) return cuda_fail(e, "FP64 block-sum buffer");
+      }
+      h->fp64_block = static_cast<int>(value);
+      return succeed();
+    }
     default:
       return fail(XC_ERR_INVALID_ARG, "unknown option key %d", key);
   }

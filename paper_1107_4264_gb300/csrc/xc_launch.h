@@ -41,6 +41,11 @@ struct XeLaunch {
   unsigned* counters;  // 2 * ring_slots, zeroed by the launcher on `s`
   unsigned* amax;      // [F] per-channel max |x| (planar engine, 8-bit input)
   const void* gains;   // cf32 [N][P] applied to float input (planar engine), or NULL
+  // Planar engine, float input:
+  int fmt = 0;              // operand format: 0 fp16, 1 split hi/lo fp16, 2 e4m3
+  unsigned* in_amax = nullptr;  // [F][N*P] scale pre-pass buffer (NULL: unscaled)
+  double* acc64 = nullptr;  // FP64 block sums in the output layout (NULL: off)
+  int f64_block = 0;        // samples per fp32 block when acc64 is set (multiple of 64)
   int grid;
   unsigned long long timeout_ns;
   int* status;
@@ -51,8 +56,9 @@ cudaError_t launch_xengine(const CUtensorMap* tmap, const XeLaunch& p, cudaStrea
 // `in_map` (8-bit input with R % 16 == 0, else NULL) is {R, F, T} int8 in
 // 128 x 1 x 64 boxes.
 cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& p, cudaStream_t s);
-int planar_ring_slots(const Geometry& g, int grid);
-int64_t planar_slot_bytes(const Geometry& g);
+constexpr int kMaxRingSlots = 64;
+int planar_ring_slots(const Geometry& g, int grid, int fmt);
+int64_t planar_slot_bytes(const Geometry& g, int fmt);
 // Same as launch_xengine, on CTA pairs (tcgen05 cta_group::2, 256 x 256 blocks).
 cudaError_t launch_xengine_pair(const CUtensorMap* tmap, const XeLaunch& p, cudaStream_t s);
 // Ring slots for a geometry (2..16 channels, about 32 MiB).

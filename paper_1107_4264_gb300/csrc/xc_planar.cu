@@ -23,6 +23,18 @@
 // chunk is drained into int32 and added into the output (stored for the
 // first chunk).  Float input accumulates in fp32 over the whole integration.
 //
+// Float input (Sec. 5 leaves its precision open): each (channel, input) gets
+// a power-of-two scale 2^e from a pre-pass over the integration (max
+// component of g x), so y 2^-e spans the operand format's range and the
+// epilogue multiplies by 2^(e_a + e_b) exactly.  Three operand formats:
+//   FP16   one fp16 plane pair, 4 MMAs per 16 samples;
+//   HI/LO  y 2^-e = h + l with h = fp16(.) and l = fp16(. - h); the ring
+//          holds H and L tiles and each 64-sample block runs three steps
+//          (H H^T, L H^T, H L^T; the l l^T term is dropped), 3x the MMAs;
+//   FP8    e4m3 planes (kind::f8f6f4, K = 32), half the operand bytes.
+// Optionally (FP64 block sums) the fp32 accumulator is drained every
+// T_blk samples into a float64 running sum; the output is its rounding.
+//
 // Blocks (Sec. 4.2): 128 x 128 blocks of V on or below the block diagonal,
 // g = by(by+1)/2 + bx; block edges fall on station boundaries (128 inputs =
 // 128/P stations).  Diagonal blocks load one pair of planes for both
@@ -55,6 +67,7 @@
 //   warps 6..9  converters
 #include <cuda.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstring>
@@ -89,6 +102,18 @@ constexpr int kNumBars = 2 * kStages + 5 + kNumConvWarps;
 constexpr int kSmemBytes = kBarOff + kNumBars * 8 + 16 + 1024;
 static_assert(kSmemBytes <= 232448, "shared memory budget");
 
+// Operand formats: tile size (log2 bytes), 16-byte K chunks per tile,
+// MMA steps per 64-sample block and ring K-tiles per 64-sample block.
+enum : int { kFmtF16 = 0, kFmtHiLo = 1, kFmtF8 = 2 };
+template <int FMT>
+struct FmtT {
+  static constexpr int kTileShift = FMT == kFmtF8 ? 13 : 14;
+  static constexpr int kTile = 1 << kTileShift;
+  static constexpr int kChunks = FMT == kFmtF8 ? 4 : 8;
+  static constexpr int kSteps = FMT == kFmtHiLo ? 3 : 1;
+  static constexpr int kKt = FMT == kFmtHiLo ? 2 : 1;
+};
+
 struct Params {
   Geometry g;
   int n;               // complex inputs per channel = N * P
@@ -101,7 +126,11 @@ struct Params {
   int is_int;          // 8-bit input: exact chunks from the channel's max |x|
   unsigned* amax;      // [F] max |x| per channel (8-bit input), zeroed by the host
   const float2* gains; // [n] complex gains applied to float input (y = g x), or NULL
-  uint8_t* ring;       // tiles [slots][2][nkb][nib][8][128][8] fp16
+  const unsigned* in_amax;  // [F][n] max component of g x (float bits), float input
+  double* acc64;       // FP64 block sums: running visibility sums (output layout), or NULL
+  int f_chunk_kb;      // float input: K-blocks per fp32 accumulation chunk
+  uint8_t* ring;       // tiles [slots][2][nkt][nib][chunks][128][16 B]
+  int nkt;             // K-tiles per plane per input block of a slot (nkb or 2 nkb)
   int nib;             // 128-input blocks per channel
   int ring_slots;
   unsigned* ready;
@@ -160,7 +189,7 @@ __device__ __forceinline__ void item_coords(long long it, int ntiles, int* f, in
 // K-blocks per exact fp32 accumulation chunk for channel f (all K-blocks for
 // float input).  Called after the channel is known to be fully converted.
 __device__ __forceinline__ int chunk_kblocks(const Params& p, int f) {
-  if (!p.is_int) return p.nkb;
+  if (!p.is_int) return p.f_chunk_kb;
   const unsigned m = *reinterpret_cast<volatile const unsigned*>(p.amax + f);
   if (m == 0) return p.nkb;
   const unsigned long long per_block = 2ull * m * m * kBK;  // |partial| growth per K-block
@@ -188,10 +217,26 @@ __device__ __forceinline__ uint32_t pair_i8(uint32_t a, uint32_t b, uint32_t j) 
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Byte address of tile (slot, plane, kb, ib) in the ring.
-__device__ __forceinline__ uint8_t* ring_tile(const Params& p, int slot, int plane, int kb, int ib) {
-  return p.ring + ((((static_cast<int64_t>(slot) * 2 + plane) * p.nkb + kb) * p.nib + ib) << 14);
+// Byte address of tile (slot, plane, K-tile kt, ib) in the ring.
+template <int FMT>
+__device__ __forceinline__ uint8_t* ring_tile(const Params& p, int slot, int plane, int kt, int ib) {
+  return p.ring + ((((static_cast<int64_t>(slot) * 2 + plane) * p.nkt + kt) * p.nib + ib)
+                   << FmtT<FMT>::kTileShift);
 }
+
+// Power-of-two scale exponent e for an input whose largest component is
+// `bits` (fp32 bits): max |y| 2^-e lies in [2^14, 2^15) for the fp16 forms
+// and in (2^7, 448] for e4m3.  Zero or subnormal maxima are not scaled;
+// e is clamped to [-60, 60] so that 2^(e_a + e_b) is a normal float.
+template <int FMT>
+__device__ __forceinline__ int scale_exp(unsigned bits) {
+  const int E = static_cast<int>((bits >> 23) & 0xffu);
+  if (E == 0) return 0;
+  int e = E - 127 - (FMT == kFmtF8 ? 8 : 14);
+  if (FMT == kFmtF8 && (bits & 0x7fffffu) > 0x600000u) ++e;  // 256 (1 + m) > 448
+  return max(-60, min(60, e));
+}
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }
 
 // A unit: 64 inputs (half block hb) x 64 samples (K-block kb) of channel c,
 // units numbered channel-major with the K-block fastest.
@@ -245,11 +290,31 @@ __device__ __forceinline__ float2 load_cx(const Params& p, int c, int a, int t) 
   }
 }
 
+// fp16x2 bits of (a, b).
+__device__ __forceinline__ uint32_t h2bits(float a, float b) {
+  __half2 q = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&q);
+}
+// fp16x2 bits of the residuals (a - fp16(a), b - fp16(b)) given h = fp16x2(a, b).
+__device__ __forceinline__ uint32_t lo2bits(float a, float b, uint32_t h) {
+  const __half2 hh = *reinterpret_cast<const __half2*>(&h);
+  return h2bits(a - __low2float(hh), b - __high2float(hh));
+}
+// Four e4m3 bytes (a, b, c, d), a in the low byte, rounded to nearest with
+// saturation to +-448.
+__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xffffu) | (hi << 16);
+}
+
 // Direct-load converter (any input type and row count), independent warps:
 // lane l loads the complex samples of inputs l and l + 32 of the half block,
-// 16 samples (32 loads) in flight at a time, and writes one 16-byte chunk
-// per (input, plane, 8 samples).
-template <int DT>
+// 16 samples (32 loads) in flight at a time, applies the gains and the
+// input's power-of-two scale (float input) and writes 16-byte chunks: per
+// (input, plane) two fp16 chunks (8 samples each; HI/LO: two more into the
+// L tile) or one e4m3 chunk (16 samples).
+template <int DT, int FMT>
 __device__ void converter_direct(const Params& p, int cw, int lane, volatile int* abort_flag) {
   const long long total = static_cast<long long>(p.g.F) * p.units_per_chan;
   const long long stride = static_cast<long long>(gridDim.x) * kNumConvWarps;
@@ -261,10 +326,26 @@ __device__ void converter_direct(const Params& p, int cw, int lane, volatile int
       claimed = x.c;
     }
     const int ib = x.hb >> 1;
-    uint8_t* tre = ring_tile(p, x.slot, 0, x.kb, ib);
-    uint8_t* tim = ring_tile(p, x.slot, 1, x.kb, ib);
+    uint8_t* tre = ring_tile<FMT>(p, x.slot, 0, x.kb, ib);
+    uint8_t* tim = ring_tile<FMT>(p, x.slot, 1, x.kb, ib);
     const int a0 = x.hb * 64 + lane, a1 = a0 + 32;
     const int row0 = (x.hb & 1) * 64 + lane;
+    // y = g x 2^-e (float input; gains are not defined for 8-bit input).
+    float2 g0 = make_float2(1.f, 0.f), g1 = make_float2(1.f, 0.f);
+    if (DT != 0) {
+      if (p.gains) {
+        g0 = a0 < p.n ? p.gains[a0] : make_float2(0.f, 0.f);
+        g1 = a1 < p.n ? p.gains[a1] : make_float2(0.f, 0.f);
+      }
+      if (p.in_amax) {
+        const unsigned* am = p.in_amax + static_cast<int64_t>(x.c) * p.n;
+        const float s0 = a0 < p.n ? exp2i(-scale_exp<FMT>(am[a0])) : 0.f;
+        const float s1 = a1 < p.n ? exp2i(-scale_exp<FMT>(am[a1])) : 0.f;
+        g0 = make_float2(g0.x * s0, g0.y * s0);  // exact: s is a power of two
+        g1 = make_float2(g1.x * s1, g1.y * s1);
+      }
+    }
+    const bool apply = DT != 0 && (p.gains || p.in_amax);
 #pragma unroll 1
     for (int g = 0; g < kUnitT / 16; ++g) {
       float2 v0[16], v1[16];
@@ -274,36 +355,68 @@ __device__ void converter_direct(const Params& p, int cw, int lane, volatile int
         v0[i] = (a0 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a0, t) : make_float2(0.f, 0.f);
         v1[i] = (a1 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a1, t) : make_float2(0.f, 0.f);
       }
-      if (DT != 0 && p.gains) {
-        // y = g x for float input (gains are not defined for 8-bit input).
-        const float2 g0 = a0 < p.n ? p.gains[a0] : make_float2(0.f, 0.f);
-        const float2 g1 = a1 < p.n ? p.gains[a1] : make_float2(0.f, 0.f);
+      if (apply) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           v0[i] = make_float2(g0.x * v0[i].x - g0.y * v0[i].y, g0.x * v0[i].y + g0.y * v0[i].x);
           v1[i] = make_float2(g1.x * v1[i].x - g1.y * v1[i].y, g1.x * v1[i].y + g1.y * v1[i].x);
         }
       }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t off = (2 * g + h) * kChunkStride + row0 * 16;
+      if constexpr (FMT == kFmtF8) {
+        const uint32_t off = g * kChunkStride + row0 * 16;
         uint32_t r0[4], i0[4], r1[4], i1[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          __half2 q;
-          q = __floats2half2_rn(v0[8 * h + 2 * k].x, v0[8 * h + 2 * k + 1].x);
-          r0[k] = *reinterpret_cast<uint32_t*>(&q);
-          q = __floats2half2_rn(v0[8 * h + 2 * k].y, v0[8 * h + 2 * k + 1].y);
-          i0[k] = *reinterpret_cast<uint32_t*>(&q);
-          q = __floats2half2_rn(v1[8 * h + 2 * k].x, v1[8 * h + 2 * k + 1].x);
-          r1[k] = *reinterpret_cast<uint32_t*>(&q);
-          q = __floats2half2_rn(v1[8 * h + 2 * k].y, v1[8 * h + 2 * k + 1].y);
-          i1[k] = *reinterpret_cast<uint32_t*>(&q);
+          const float2* A = v0 + 4 * k;
+          const float2* B = v1 + 4 * k;
+          r0[k] = e4m3x4(A[0].x, A[1].x, A[2].x, A[3].x);
+          i0[k] = e4m3x4(A[0].y, A[1].y, A[2].y, A[3].y);
+          r1[k] = e4m3x4(B[0].x, B[1].x, B[2].x, B[3].x);
+          i1[k] = e4m3x4(B[0].y, B[1].y, B[2].y, B[3].y);
         }
         *reinterpret_cast<uint4*>(tre + off) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
         *reinterpret_cast<uint4*>(tim + off) = make_uint4(i0[0], i0[1], i0[2], i0[3]);
         *reinterpret_cast<uint4*>(tre + off + 32 * 16) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
         *reinterpret_cast<uint4*>(tim + off + 32 * 16) = make_uint4(i1[0], i1[1], i1[2], i1[3]);
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t off = (2 * g + h) * kChunkStride + row0 * 16;
+          uint32_t r0[4], i0[4], r1[4], i1[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 a = v0[8 * h + 2 * k], b = v0[8 * h + 2 * k + 1];
+            const float2 c = v1[8 * h + 2 * k], d = v1[8 * h + 2 * k + 1];
+            r0[k] = h2bits(a.x, b.x);
+            i0[k] = h2bits(a.y, b.y);
+            r1[k] = h2bits(c.x, d.x);
+            i1[k] = h2bits(c.y, d.y);
+          }
+          *reinterpret_cast<uint4*>(tre + off) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+          *reinterpret_cast<uint4*>(tim + off) = make_uint4(i0[0], i0[1], i0[2], i0[3]);
+          *reinterpret_cast<uint4*>(tre + off + 32 * 16) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+          *reinterpret_cast<uint4*>(tim + off + 32 * 16) = make_uint4(i1[0], i1[1], i1[2], i1[3]);
+          if constexpr (FMT == kFmtHiLo) {
+            // Residual tile of the same K-block: K-tile nkb + kb.
+            const int64_t lo_off = static_cast<int64_t>(p.nkb) * p.nib << FmtT<FMT>::kTileShift;
+            uint32_t l0[4], m0[4], l1[4], m1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float2 a = v0[8 * h + 2 * k], b = v0[8 * h + 2 * k + 1];
+              const float2 c = v1[8 * h + 2 * k], d = v1[8 * h + 2 * k + 1];
+              l0[k] = lo2bits(a.x, b.x, r0[k]);
+              m0[k] = lo2bits(a.y, b.y, i0[k]);
+              l1[k] = lo2bits(c.x, d.x, r1[k]);
+              m1[k] = lo2bits(c.y, d.y, i1[k]);
+            }
+            *reinterpret_cast<uint4*>(tre + lo_off + off) = make_uint4(l0[0], l0[1], l0[2], l0[3]);
+            *reinterpret_cast<uint4*>(tim + lo_off + off) = make_uint4(m0[0], m0[1], m0[2], m0[3]);
+            *reinterpret_cast<uint4*>(tre + lo_off + off + 32 * 16) =
+                make_uint4(l1[0], l1[1], l1[2], l1[3]);
+            *reinterpret_cast<uint4*>(tim + lo_off + off + 32 * 16) =
+                make_uint4(m1[0], m1[1], m1[2], m1[3]);
+          }
+        }
       }
     }
     if (DT == 0 && lane == 0) atomicMax(p.amax + x.c, 128u);  // no scan: worst case
@@ -373,8 +486,8 @@ __device__ void converter_tma(const Params& p, const CUtensorMap* in_map, uint32
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) atomicMax(p.amax + x.c, m);
     const int ib = x.hb >> 1;
-    uint8_t* tre = ring_tile(p, x.slot, 0, x.kb, ib);
-    uint8_t* tim = ring_tile(p, x.slot, 1, x.kb, ib);
+    uint8_t* tre = ring_tile<kFmtF16>(p, x.slot, 0, x.kb, ib);
+    uint8_t* tim = ring_tile<kFmtF16>(p, x.slot, 1, x.kb, ib);
     const int row = (x.hb & 1) * 64 + lane;
 #pragma unroll
     for (int cc = 0; cc < 8; ++cc) {
@@ -481,9 +594,54 @@ __device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint
   }
 }
 
+// Undo the operand scales of float input: V(a, b0 + j) *= 2^(e_a + e_b).
+template <int FMT>
+__device__ __forceinline__ void scale_piece(uint32_t (&re)[32], uint32_t (&im)[32], const Params& p,
+                                            int f, int a, int b0) {
+  const unsigned* am = p.in_amax + static_cast<int64_t>(f) * p.n;
+  const int ea = a < p.n ? scale_exp<FMT>(am[a]) : 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int b = b0 + j;
+    const float sc = exp2i(ea + (b < p.n ? scale_exp<FMT>(am[b]) : 0));
+    re[j] = __float_as_uint(__uint_as_float(re[j]) * sc);
+    im[j] = __float_as_uint(__uint_as_float(im[j]) * sc);
+  }
+}
+
+// FP64 block sums: acc64 = (first chunk and not accumulating ? 0 : acc64) +
+// piece; the last chunk of the integration also stores its fp32 rounding.
+__device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const uint32_t (&im)[32],
+                                                const Params& p, int f, int a, int b0, bool first,
+                                                bool last) {
+  if (a >= p.n) return;
+  const int P = p.g.P;
+  const int s1 = a / P, p1 = a - s1 * P;
+  const int64_t krow = static_cast<int64_t>(f) * p.g.NB + static_cast<int64_t>(s1) * (s1 + 1) / 2;
+  const bool load_old = !first || p.accumulate;
+  double2* ws = reinterpret_cast<double2*>(p.acc64);
+  float2* out = static_cast<float2*>(p.out);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int b = b0 + j;
+    const int s2 = b / P, p2 = b - s2 * P;
+    if (s2 > s1) continue;
+    const int64_t idx = (krow + s2) * P * P + p1 * P + p2;
+    double2 v = make_double2(static_cast<double>(__uint_as_float(re[j])),
+                             static_cast<double>(__uint_as_float(im[j])));
+    if (load_old) {
+      const double2 o = ws[idx];
+      v.x += o.x;
+      v.y += o.y;
+    }
+    ws[idx] = v;
+    if (last) out[idx] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+  }
+}
+
 // ------------------------------------------------------------------ kernel
 
-template <bool IS_INT, int DT>
+template <bool IS_INT, int DT, int FMT>
 __global__ void __launch_bounds__(kThreads, 1)
     planar_kernel(const __grid_constant__ CUtensorMap in_map, const Params p) {
   extern __shared__ uint8_t smem_raw[];
@@ -552,19 +710,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           ready_chan = f;
         }
         const bool diag = bx == by;
-        for (int kb = 0; kb < p.nkb; ++kb) {
+        constexpr int TB = FmtT<FMT>::kTile;
+        for (int st = 0; ok && st < p.nkb * FmtT<FMT>::kSteps; ++st) {
+          // Step st: K-block kb; HI/LO steps j = 0, 1, 2 take (H, H), (L, H), (H, L).
+          const int kb = st / FmtT<FMT>::kSteps, j = st - kb * FmtT<FMT>::kSteps;
+          const int kta = kb + (j == 1 ? p.nkb : 0);
+          const int ktb = kb + (j == 2 ? p.nkb : 0);
+          const bool same = diag && kta == ktb;
           if (!ptx::wait_bounded(empty_bar(stage), phase ^ 1u, wc)) {
             ok = false;
             break;
           }
           const uint32_t dst = sbase + stage * kStageBytes;
           const uint32_t fb = full_bar(stage);
-          ptx::mbar_arrive_expect_tx(fb, diag ? 2 * kTileBytes : 4 * kTileBytes);
-          ptx::bulk_load(dst, ring_tile(p, slot, 0, kb, by), kTileBytes, fb);
-          ptx::bulk_load(dst + kTileBytes, ring_tile(p, slot, 1, kb, by), kTileBytes, fb);
-          if (!diag) {
-            ptx::bulk_load(dst + 2 * kTileBytes, ring_tile(p, slot, 0, kb, bx), kTileBytes, fb);
-            ptx::bulk_load(dst + 3 * kTileBytes, ring_tile(p, slot, 1, kb, bx), kTileBytes, fb);
+          ptx::mbar_arrive_expect_tx(fb, same ? 2 * TB : 4 * TB);
+          ptx::bulk_load(dst, ring_tile<FMT>(p, slot, 0, kta, by), TB, fb);
+          ptx::bulk_load(dst + TB, ring_tile<FMT>(p, slot, 1, kta, by), TB, fb);
+          if (!same) {
+            ptx::bulk_load(dst + 2 * TB, ring_tile<FMT>(p, slot, 0, ktb, bx), TB, fb);
+            ptx::bulk_load(dst + 3 * TB, ring_tile<FMT>(p, slot, 1, ktb, bx), TB, fb);
           }
           issued_phase[stage] = static_cast<int>(phase);
           if (++stage == kStages) {
@@ -613,29 +777,38 @@ __global__ void __launch_bounds__(kThreads, 1)
           ptx::tc_fence_after();
           const uint32_t d_re = tmem + ab * 256;
           const uint32_t d_im = d_re + 128;
-          for (int kb = kb0; kb < kb1; ++kb) {
+          constexpr int TB = FmtT<FMT>::kTile;
+          for (int st = kb0 * FmtT<FMT>::kSteps; st < kb1 * FmtT<FMT>::kSteps; ++st) {
             if (!ptx::wait_bounded(full_bar(stage), phase, wc)) {
               ok = false;
               break;
             }
             ptx::tc_fence_after();
+            const bool same = diag && (FMT != kFmtHiLo || st % 3 == 0);
             const uint32_t ar = sbase + stage * kStageBytes;
-            const uint32_t ai = ar + kTileBytes;
-            const uint32_t br = diag ? ar : ar + 2 * kTileBytes;
-            const uint32_t bi = diag ? ai : ar + 3 * kTileBytes;
+            const uint32_t ai = ar + TB;
+            const uint32_t br = same ? ar : ar + 2 * TB;
+            const uint32_t bi = same ? ai : ar + 3 * TB;
 #pragma unroll
-            for (int k = 0; k < kBK / 16; ++k) {
-              const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
-              // K-step k covers 8-sample chunks 2k and 2k + 1.
+            for (int k = 0; k < FmtT<FMT>::kChunks / 2; ++k) {
+              const uint32_t acc = (st > kb0 * FmtT<FMT>::kSteps || k > 0) ? 1u : 0u;
+              // K-step k covers 16-byte chunks 2k and 2k + 1 (16 fp16 or 32 e4m3 samples).
               const uint32_t ko = k * 2 * kChunkStride;
               const uint64_t dar = ptx::interleave_kmajor_desc(ar + ko, kChunkStride, kGroupStride);
               const uint64_t dai = ptx::interleave_kmajor_desc(ai + ko, kChunkStride, kGroupStride);
               const uint64_t dbr = ptx::interleave_kmajor_desc(br + ko, kChunkStride, kGroupStride);
               const uint64_t dbi = ptx::interleave_kmajor_desc(bi + ko, kChunkStride, kGroupStride);
-              ptx::mma_f16_ss(d_re, dar, dbr, kIdesc, acc);       // Re += Ar Br^T
-              ptx::mma_f16_ss(d_re, dai, dbi, kIdesc, 1u);        // Re += Ai Bi^T
-              ptx::mma_f16_ss(d_im, dai, dbr, kIdesc, acc);       // Im += Ai Br^T
-              ptx::mma_f16_ss(d_im, dar, dbi, kIdescNegB, 1u);    // Im -= Ar Bi^T
+              if constexpr (FMT == kFmtF8) {
+                ptx::mma_f8_ss(d_re, dar, dbr, kIdesc, acc);      // Re += Ar Br^T
+                ptx::mma_f8_ss(d_re, dai, dbi, kIdesc, 1u);       // Re += Ai Bi^T
+                ptx::mma_f8_ss(d_im, dai, dbr, kIdesc, acc);      // Im += Ai Br^T
+                ptx::mma_f8_ss(d_im, dar, dbi, kIdescNegB, 1u);   // Im -= Ar Bi^T
+              } else {
+                ptx::mma_f16_ss(d_re, dar, dbr, kIdesc, acc);     // Re += Ar Br^T
+                ptx::mma_f16_ss(d_re, dai, dbi, kIdesc, 1u);      // Re += Ai Bi^T
+                ptx::mma_f16_ss(d_im, dai, dbr, kIdesc, acc);     // Im += Ai Br^T
+                ptx::mma_f16_ss(d_im, dar, dbi, kIdescNegB, 1u);  // Im -= Ar Bi^T
+              }
             }
             issued_any = true;
             ptx::mma_commit(empty_bar(stage));
@@ -690,6 +863,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ptx::tc_fence_after();
         const bool add = p.accumulate || ch > 0;
+        const bool first = ch == 0, last_chunk = ch == nchunks - 1;
         if (last < 0) {
           ptx::tc_fence_before();
           __syncwarp();
@@ -706,7 +880,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
           }
-          store_piece<IS_INT>(vr, vi, p, f, a, bx * kBlk + piece * 32, add);
+          const int b0 = bx * kBlk + piece * 32;
+          if constexpr (IS_INT) {
+            store_piece<true>(vr, vi, p, f, a, b0, add);
+          } else {
+            if (p.in_amax) scale_piece<FMT>(vr, vi, p, f, a, b0);
+            if (p.acc64) {
+              store_piece_f64(vr, vi, p, f, a, b0, first, last_chunk);
+            } else {
+              store_piece<false>(vr, vi, p, f, a, b0, add);
+            }
+          }
         }
         ++u;
       }
@@ -719,10 +903,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         converter_tma(p, &in_map, sbase + kConvOff + cw * kConvBufBytes, conv_bar(cw), cw, lane,
                       abort_flag);
       } else {
-        converter_direct<DT>(p, cw, lane, abort_flag);
+        converter_direct<DT, FMT>(p, cw, lane, abort_flag);
       }
     } else {
-      converter_direct<DT>(p, cw, lane, abort_flag);
+      converter_direct<DT, FMT>(p, cw, lane, abort_flag);
     }
   }
 
@@ -735,31 +919,77 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <bool IS_INT, int DT>
+template <bool IS_INT, int DT, int FMT>
 cudaError_t launch_variant(const CUtensorMap* in_map, const Params& p, int grid, cudaStream_t s) {
-  auto kern = planar_kernel<IS_INT, DT>;
+  auto kern = planar_kernel<IS_INT, DT, FMT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, kSmemBytes, s>>>(*in_map, p);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-int64_t planar_slot_bytes(const Geometry& g) {
-  const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
-  return 2 * (g.Tp / kBK) * nib * kTileBytes;
+template <int DT>
+cudaError_t launch_float(const CUtensorMap* in_map, const Params& p, int fmt, int grid,
+                         cudaStream_t s) {
+  switch (fmt) {
+    case kFmtF16: return launch_variant<false, DT, kFmtF16>(in_map, p, grid, s);
+    case kFmtHiLo: return launch_variant<false, DT, kFmtHiLo>(in_map, p, grid, s);
+    case kFmtF8: return launch_variant<false, DT, kFmtF8>(in_map, p, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-int planar_ring_slots(const Geometry& g, int grid) {
+// Scale pre-pass for float input: amax[f][a] = max over t of the largest
+// component of g_a x_a(t) (fp32 bits; non-negative floats order as
+// unsigned integers).  A thread per (input, channel, 128-sample range);
+// a warp reads 32 consecutive inputs of one sample row.
+template <int DT>
+__global__ void __launch_bounds__(128) input_amax_kernel(const void* __restrict__ in,
+                                                         const float2* __restrict__ gains,
+                                                         unsigned* __restrict__ amax, Geometry g,
+                                                         int n) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (a >= n) return;
+  const int t0 = blockIdx.z * 128;
+  const int t1 = min(g.T, t0 + 128);
+  const float2 ga = gains ? gains[a] : make_float2(1.f, 0.f);
+  float m = 0.f;
+#pragma unroll 8
+  for (int t = t0; t < t1; ++t) {
+    const int64_t idx = (static_cast<int64_t>(t) * g.F + f) * n + a;
+    float2 v;
+    if constexpr (DT == 1) {
+      v = __half22float2(static_cast<const __half2*>(in)[idx]);
+    } else {
+      v = static_cast<const float2*>(in)[idx];
+    }
+    if (gains) v = make_float2(ga.x * v.x - ga.y * v.y, ga.x * v.y + ga.y * v.x);
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  atomicMax(amax + static_cast<int64_t>(f) * n + a, __float_as_uint(m));
+}
+
+int fmt_kt(int fmt) { return fmt == kFmtHiLo ? 2 : 1; }
+int fmt_tile_bytes(int fmt) { return fmt == kFmtF8 ? (1 << 13) : (1 << 14); }
+
+}  // namespace
+
+int64_t planar_slot_bytes(const Geometry& g, int fmt) {
+  const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
+  return 2 * fmt_kt(fmt) * (g.Tp / kBK) * nib * fmt_tile_bytes(fmt);
+}
+
+int planar_ring_slots(const Geometry& g, int grid, int fmt) {
   // The persistent CTAs keep about grid / blocks_per_channel channels in
   // flight; the converters need room ahead of them.
   const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
   const int64_t blocks = std::max<int64_t>(1, nib * (nib + 1) / 2);
   const int64_t inflight = (grid + blocks - 1) / blocks;
   int64_t n = (inflight * 8 + 4) / 5 + 4;
-  const int64_t cap = std::max<int64_t>(2, (256ll << 20) / std::max<int64_t>(planar_slot_bytes(g), 1));
-  n = std::max<int64_t>(4, std::min<int64_t>(std::min<int64_t>(64, cap), n));
+  const int64_t cap =
+      std::max<int64_t>(2, (256ll << 20) / std::max<int64_t>(planar_slot_bytes(g, fmt), 1));
+  n = std::max<int64_t>(4, std::min<int64_t>(std::min<int64_t>(kMaxRingSlots, cap), n));
   return static_cast<int>(std::min<int64_t>(n, g.F));
 }
 
@@ -775,8 +1005,14 @@ cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, cudaStre
   p.nitems = static_cast<long long>(p.ntiles) * L.g.F;
   p.nkb = L.g.Tp / kBK;
   p.is_int = L.in_dtype == 0 ? 1 : 0;
+  const int fmt = p.is_int ? kFmtF16 : L.fmt;
+  p.nkt = fmt_kt(fmt) * p.nkb;
   p.amax = L.amax;
   p.gains = static_cast<const float2*>(L.gains);
+  p.in_amax = p.is_int ? nullptr : L.in_amax;
+  p.acc64 = p.is_int ? nullptr : L.acc64;
+  p.f_chunk_kb = p.nkb;
+  if (p.acc64 && L.f64_block > 0) p.f_chunk_kb = std::max(1, std::min(p.nkb, L.f64_block / kBK));
   p.ring = static_cast<uint8_t*>(L.ring);
   p.ring_slots = L.ring_slots;
   p.ready = L.counters;
@@ -787,17 +1023,30 @@ cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, cudaStre
   p.timeout_ns = L.timeout_ns;
   p.status = L.status;
   if (p.nitems == 0 || p.nkb == 0) return cudaSuccess;
+  if (L.ring_slots > kMaxRingSlots) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(L.counters, 0, 2 * sizeof(unsigned) * L.ring_slots, s);
   if (e == cudaSuccess && p.is_int) e = cudaMemsetAsync(L.amax, 0, sizeof(unsigned) * L.g.F, s);
   if (e != cudaSuccess) return e;
+  if (p.in_amax) {
+    e = cudaMemsetAsync(L.in_amax, 0, sizeof(unsigned) * L.g.F * static_cast<size_t>(p.n), s);
+    if (e != cudaSuccess) return e;
+    const dim3 ag((p.n + 127) / 128, L.g.F, (L.g.T + 127) / 128);
+    if (ag.z > 65535u) return cudaErrorInvalidConfiguration;
+    if (L.in_dtype == 1)
+      input_amax_kernel<1><<<ag, 128, 0, s>>>(L.in, p.gains, L.in_amax, L.g, p.n);
+    else
+      input_amax_kernel<2><<<ag, 128, 0, s>>>(L.in, p.gains, L.in_amax, L.g, p.n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int grid = static_cast<int>(std::min<long long>(p.nitems, L.grid));
   CUtensorMap unused;
   const CUtensorMap* im = in_map ? in_map : &unused;  // read only when p.tma_in
   if (!in_map) memset(&unused, 0, sizeof(unused));
   switch (L.in_dtype) {
-    case 0: return launch_variant<true, 0>(im, p, grid, s);
-    case 1: return launch_variant<false, 1>(im, p, grid, s);
-    case 2: return launch_variant<false, 2>(im, p, grid, s);
+    case 0: return launch_variant<true, 0, kFmtF16>(im, p, grid, s);
+    case 1: return launch_float<1>(im, p, fmt, grid, s);
+    case 2: return launch_float<2>(im, p, fmt, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -26,6 +26,8 @@ XC_ERR_TIMEOUT = 6
 XC_ERR_OOM = 7
 XC_ERR_NO_DEVICE = 8
 XC_OPT_ENGINE, XC_OPT_ACCUMULATE, XC_OPT_TIMEOUT_MS, XC_OPT_PROFILE = 1, 2, 3, 4
+XC_OPT_PRECISION, XC_OPT_FP64_BLOCK = 5, 6
+XC_PREC_FP16, XC_PREC_HILO, XC_PREC_FP8 = 0, 1, 2
 (XC_ENGINE_TENSOR, XC_ENGINE_FP32, XC_ENGINE_TENSOR_2PASS, XC_ENGINE_TENSOR_1CTA,
  XC_ENGINE_TENSOR_PAIR) = 0, 1, 2, 3, 4
 XC_CI8_MAX_NTIME = 66572
@@ -211,7 +213,8 @@ class Correlator:
 
     def __init__(self, nstation: int, npol: int, nfreq: int, ntime: int, dtype: str = "int8",
                  engine: int = XC_ENGINE_TENSOR, accumulate: bool = False,
-                 timeout_ms: Optional[int] = None):
+                 timeout_ms: Optional[int] = None, precision: int = XC_PREC_FP16,
+                 fp64_block: int = 0):
         import torch
         self._torch = torch
         self.nstation, self.npol, self.nfreq, self.ntime = nstation, npol, nfreq, ntime
@@ -221,6 +224,10 @@ class Correlator:
         self.set_option(XC_OPT_ACCUMULATE, int(accumulate))
         if timeout_ms is not None:
             self.set_option(XC_OPT_TIMEOUT_MS, timeout_ms)
+        if precision != XC_PREC_FP16:
+            self.set_option(XC_OPT_PRECISION, precision)
+        if fp64_block:
+            self.set_option(XC_OPT_FP64_BLOCK, fp64_block)
 
     @property
     def in_shape(self):
