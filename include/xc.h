@@ -287,6 +287,41 @@ void xc_tri_coords(int64_t g, int64_t* bx, int64_t* by);
 xc_status xc_correlate_noalloc(int nstation, int npol, int nfreq, int ntime, xc_dtype in_dtype,
                                const void* in, void* out, int* status, void* stream);
 
+/*
+ * Batched form: many subarrays of uneven size correlated by ONE persistent
+ * tensor-core launch (Sec. 4.2's channel-major block raster continued from
+ * one subarray to the next), replayed from a CUDA graph captured on first
+ * use.  For an array split into independent subarrays, or many small arrays
+ * sharing one GPU (the small-N regime Sec. 6 discusses: small subarrays alone
+ * leave most SMs idle, together they fill the GPU).
+ *
+ * xc_batch_create: nsub in [1, XC_BATCH_MAX_SUB]; nstation / nfreq / ntime:
+ *   host arrays of nsub sizes (each as for xc_create); one npol and one input
+ *   type for all (XC_CI8 only: bit-exact int32 visibilities).  Returns NULL
+ *   on error (xc_last_error()).  The handle owns every subarray's operand
+ *   ring and counters; free it with xc_destroy.  xc_correlate on a batch
+ *   handle returns XC_ERR_UNSUPPORTED; xc_set_option accepts ACCUMULATE,
+ *   TIMEOUT_MS and PROFILE.
+ * xc_batch_correlate: in[i] / out[i] are device pointers (16-byte aligned)
+ *   in the layouts of xc_correlate for subarray i; arrays of nsub pointers
+ *   in host memory, read during the call.  Stream-ordered; one graph launch
+ *   per call.  Calls on one handle must be ordered with each other (they
+ *   share the rings and counters).
+ * xc_batch_tune: times each candidate schedule (work-list order: as given,
+ *   largest subarray first, smallest first; x operand-ring depth: 1x, 2x) on
+ *   the given buffers with `reps` timed launches each (after one warm-up),
+ *   keeps the fastest for later calls and writes the mean milliseconds of
+ *   every candidate to ms[XC_BATCH_CANDIDATES] and the winner to *best
+ *   (either may be NULL).  Synchronises `stream`.
+ */
+#define XC_BATCH_MAX_SUB 8
+#define XC_BATCH_CANDIDATES 6
+xc_handle* xc_batch_create(int nsub, const int* nstation, const int* nfreq, const int* ntime,
+                           int npol, xc_dtype in_dtype);
+xc_status xc_batch_correlate(xc_handle* h, const void* const* in, void* const* out, void* stream);
+xc_status xc_batch_tune(xc_handle* h, const void* const* in, void* const* out, void* stream,
+                        int reps, double* ms, int* best);
+
 /* Library version string. */
 const char* xc_version(void);
 

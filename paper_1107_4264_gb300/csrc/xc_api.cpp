@@ -71,8 +71,35 @@ size_t sample_bytes(xc_dtype d) { return d == XC_CI8 ? 1 : (d == XC_CF16 ? 2 : 4
 
 }  // namespace
 
+// Batched handle: every subarray's geometry and its region of the shared
+// operand ring, counters and per-channel maxima, the chosen schedule and the
+// captured graph (memsets + one persistent launch).
+struct BatchSub {
+  xc::Geometry g{};
+  size_t in_bytes = 0, out_bytes = 0;
+  void* ring = nullptr;
+  int slots_base = 0;  // ring depth 1x (xc::planar_ring_slots)
+  int max_slots = 0;   // slots the region holds (for the 2x candidate)
+  unsigned* counters = nullptr;
+  unsigned* amax = nullptr;
+};
+struct BatchState {
+  int nsub = 0;
+  BatchSub sub[XC_BATCH_MAX_SUB];
+  void* ring_all = nullptr;
+  unsigned* ctr_all = nullptr;
+  int order[XC_BATCH_MAX_SUB];
+  int depth = 1;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t knode = nullptr;
+  xc::PlanarKernel k;
+};
+
 struct xc_handle {
   int device = 0;
+  BatchState* batch = nullptr;
   xc::Geometry g{};
   xc_dtype dtype = XC_CI8;
   size_t in_bytes = 0, out_bytes = 0;
@@ -149,7 +176,7 @@ void release(xc_handle* h) {
   if (h->ev_d2h) cudaEventDestroy(h->ev_d2h);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
-  if (h->ws || h->d_status || h->ring) cudaDeviceSynchronize();
+  if (h->ws || h->d_status || h->ring || h->batch) cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
   if (h->gains) cudaFree(h->gains);
   if (h->adj_ws) cudaFree(h->adj_ws);
@@ -160,6 +187,14 @@ void release(xc_handle* h) {
   if (h->in_amax) cudaFree(h->in_amax);
   if (h->acc64) cudaFree(h->acc64);
   if (h->d_status) cudaFree(h->d_status);
+  if (BatchState* b = h->batch) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->ring_all) cudaFree(b->ring_all);
+    if (b->ctr_all) cudaFree(b->ctr_all);
+    delete b;
+  }
   cudaSetDevice(cur);
   delete h;
 }
@@ -178,6 +213,7 @@ xc_handle::Timed* next_timed(xc_handle* h, int nkern) {
 }
 
 xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
+  if (h->batch) return fail(XC_ERR_UNSUPPORTED, "batch handle: use xc_batch_correlate");
   cudaError_t e;
   xc_handle::Timed* tm = nullptr;
   if (h->profile) {
@@ -484,6 +520,8 @@ xc_status xc_set_option(xc_handle* h, int key, long long value) {
   if (!h) return fail(XC_ERR_INVALID_ARG, "NULL handle");
   switch (key) {
     case XC_OPT_ENGINE:
+      if (h->batch && value != XC_ENGINE_TENSOR)
+        return fail(XC_ERR_UNSUPPORTED, "batch handles run the tensor-core engine only");
       if (value != XC_ENGINE_TENSOR && value != XC_ENGINE_FP32 && value != XC_ENGINE_TENSOR_2PASS &&
           value != XC_ENGINE_TENSOR_1CTA && value != XC_ENGINE_TENSOR_PAIR)
         return fail(XC_ERR_INVALID_ARG, "unknown engine %lld", value);
@@ -559,6 +597,7 @@ xc_status xc_set_option(xc_handle* h, int key, long long value) {
 
 xc_status xc_correlate(xc_handle* h, const void* in, void* out, void* stream) {
   if (!h || !in || !out) return fail(XC_ERR_INVALID_ARG, "NULL handle or buffer");
+  if (h->batch) return fail(XC_ERR_UNSUPPORTED, "batch handle: use xc_batch_correlate");
   if (!aligned16(in) || !aligned16(out))
     return fail(XC_ERR_ALIGNMENT, "input and output must be 16-byte aligned");
   return launch_one(h, in, out, static_cast<cudaStream_t>(stream));
@@ -711,6 +750,281 @@ xc_status xc_correlate_stream(xc_handle* h, const void* host_in, int n_integrati
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_d2h, h->d2h_stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_d2h, 0);
   if (e != cudaSuccess) return cuda_fail(e, "integrated pipeline");
+  return succeed();
+}
+
+// ------------------------------------------------------------------ batch
+
+}  // extern "C"
+
+namespace {
+
+// Work of subarray i in MMA block-steps: blocks per channel x channels x K-blocks.
+double batch_work(const BatchSub& b) {
+  const double nib = (static_cast<double>(b.g.N) * b.g.P + 127) / 128;
+  return nib * (nib + 1) / 2 * b.g.F * (b.g.Tp / 64);
+}
+
+// Candidate c: work-list order (c % 3: as given, largest first, smallest
+// first) and ring depth (1 + c / 3).
+void batch_schedule(BatchState* b, int c, int* order, int* depth) {
+  for (int i = 0; i < b->nsub; ++i) order[i] = i;
+  const int kind = c % 3;
+  if (kind != 0)
+    std::stable_sort(order, order + b->nsub, [&](int x, int y) {
+      const double wx = batch_work(b->sub[x]), wy = batch_work(b->sub[y]);
+      return kind == 1 ? wx > wy : wx < wy;
+    });
+  *depth = 1 + c / 3;
+}
+
+void batch_drop_graph(BatchState* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->knode = nullptr;
+}
+
+// Launch descriptions of the subarrays in work-list order, their input
+// maps, and the kernel parameter block in b->k.
+xc_status batch_prepare(xc_handle* h, const void* const* in, void* const* out,
+                        const int* order, int depth, xc::XeLaunch* L) {
+  BatchState* b = h->batch;
+  if (!in || !out) return fail(XC_ERR_INVALID_ARG, "NULL pointer array");
+  CUtensorMap maps[XC_BATCH_MAX_SUB];
+  const CUtensorMap* mp[XC_BATCH_MAX_SUB];
+  for (int j = 0; j < b->nsub; ++j) {
+    const int i = order[j];
+    const BatchSub& s = b->sub[i];
+    if (!in[i] || !out[i]) return fail(XC_ERR_INVALID_ARG, "NULL buffer for subarray %d", i);
+    if (!aligned16(in[i]) || !aligned16(out[i]))
+      return fail(XC_ERR_ALIGNMENT, "subarray %d: buffers must be 16-byte aligned", i);
+    xc::XeLaunch& X = L[j];
+    X = xc::XeLaunch{};
+    X.g = s.g;
+    X.in = in[i];
+    X.in_dtype = static_cast<int>(h->dtype);
+    X.out = out[i];
+    X.accumulate = h->accumulate;
+    X.ring = s.ring;
+    X.ring_slots = std::min(s.max_slots, s.slots_base * depth);
+    X.counters = s.counters;
+    X.amax = s.amax;
+    X.gains = nullptr;
+    X.grid = h->num_sms;
+    X.timeout_ns = h->timeout_ns;
+    X.status = h->d_status;
+    mp[j] = nullptr;
+    if (h->dtype == XC_CI8 && s.g.R % 16 == 0) {
+      if (encode_input_map(&maps[j], in[i], s.g) != XC_OK) return t_status;
+      mp[j] = &maps[j];
+    }
+  }
+  cudaError_t e = xc::planar_prepare(L, mp, b->nsub, &b->k);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch preparation");
+  return XC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+xc_handle* xc_batch_create(int nsub, const int* nstation, const int* nfreq, const int* ntime,
+                           int npol, xc_dtype in_dtype) {
+  if (nsub < 1 || nsub > XC_BATCH_MAX_SUB || !nstation || !nfreq || !ntime) {
+    fail(XC_ERR_INVALID_ARG, "nsub must be in [1, %d] with size arrays", XC_BATCH_MAX_SUB);
+    return nullptr;
+  }
+  if (in_dtype != XC_CI8) {
+    fail(XC_ERR_UNSUPPORTED, "batched correlation takes 8-bit input");
+    return nullptr;
+  }
+  // Validate every subarray as xc_create would (and use the first as the
+  // handle's own geometry for its device state).
+  xc_handle* h = xc_create(nstation[0], npol, nfreq[0], ntime[0], in_dtype);
+  if (!h) return nullptr;
+  // The single-geometry operand ring is not used by a batch handle.
+  cudaFree(h->ring);
+  h->ring = nullptr;
+  for (int i = 1; i < nsub; ++i) {
+    const int N = nstation[i], F = nfreq[i], T = ntime[i];
+    if (N <= 0 || F <= 0 || T <= 0 || F > 65535 || T > XC_CI8_MAX_NTIME ||
+        2LL * npol * N > (1LL << 30)) {
+      release(h);
+      fail(XC_ERR_INVALID_ARG, "subarray %d: bad sizes (nstation=%d nfreq=%d ntime=%d)", i, N, F, T);
+      return nullptr;
+    }
+  }
+  BatchState* b = new (std::nothrow) BatchState();
+  if (!b) {
+    release(h);
+    fail(XC_ERR_OOM, "host allocation failed");
+    return nullptr;
+  }
+  h->batch = b;
+  b->nsub = nsub;
+  size_t ring_total = 0, in_total = 0, out_total = 0;
+  std::vector<size_t> ring_off(nsub);
+  for (int i = 0; i < nsub; ++i) {
+    BatchSub& s = b->sub[i];
+    s.g.N = nstation[i];
+    s.g.P = npol;
+    s.g.F = nfreq[i];
+    s.g.T = ntime[i];
+    s.g.R = 2 * npol * nstation[i];
+    s.g.Tp = (ntime[i] + kKBlock - 1) / kKBlock * kKBlock;
+    s.g.NB = static_cast<int64_t>(nstation[i]) * (nstation[i] + 1) / 2;
+    s.in_bytes = static_cast<size_t>(ntime[i]) * nfreq[i] * nstation[i] * npol * 2;
+    s.out_bytes = static_cast<size_t>(nfreq[i]) * s.g.NB * npol * npol * 2 * 4;
+    const int64_t slot_bytes = xc::planar_slot_bytes(s.g, XC_PREC_FP16);
+    s.slots_base = xc::planar_ring_slots(s.g, h->num_sms, XC_PREC_FP16);
+    const int64_t cap2 = std::max<int64_t>(s.slots_base, (512ll << 20) / std::max<int64_t>(slot_bytes, 1));
+    s.max_slots = static_cast<int>(std::min<int64_t>(
+        {static_cast<int64_t>(xc::kMaxRingSlots), static_cast<int64_t>(s.g.F), 2ll * s.slots_base, cap2}));
+    s.max_slots = std::max(s.max_slots, s.slots_base);
+    ring_off[i] = ring_total;
+    ring_total += static_cast<size_t>(s.max_slots) * slot_bytes;
+    in_total += s.in_bytes;
+    out_total += s.out_bytes;
+  }
+  h->in_bytes = in_total;
+  h->out_bytes = out_total;
+  size_t ctr_words = 0;
+  for (int i = 0; i < nsub; ++i) ctr_words += 2 * xc::kMaxRingSlots + b->sub[i].g.F;
+  cudaError_t e = cudaMalloc(&b->ring_all, ring_total);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->ctr_all), ctr_words * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "batch allocation");
+    release(h);
+    return nullptr;
+  }
+  unsigned* c = b->ctr_all;
+  for (int i = 0; i < nsub; ++i) {
+    BatchSub& s = b->sub[i];
+    s.ring = static_cast<char*>(b->ring_all) + ring_off[i];
+    s.counters = c;
+    c += 2 * xc::kMaxRingSlots;
+    s.amax = c;
+    c += s.g.F;
+    b->order[i] = i;
+  }
+  b->depth = 1;
+  succeed();
+  return h;
+}
+
+xc_status xc_batch_correlate(xc_handle* h, const void* const* in, void* const* out, void* stream) {
+  if (!h || !h->batch) return fail(XC_ERR_INVALID_ARG, "not a batch handle");
+  BatchState* b = h->batch;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  xc::XeLaunch L[XC_BATCH_MAX_SUB];
+  xc_status st = batch_prepare(h, in, out, b->order, b->depth, L);
+  if (st != XC_OK) return st;
+  if (b->k.grid <= 0) return succeed();
+  cudaError_t e = cudaSuccess;
+  if (!b->exec) {
+    // Capture set-up + the persistent launch once; later calls only update
+    // the kernel node's parameters (new buffers and input maps).
+    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    cudaError_t e1 = xc::planar_setup(L, b->nsub, b->cap_stream);
+    if (e1 == cudaSuccess) e1 = xc::planar_launch(b->k, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e1 != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e1 != cudaSuccess ? e1 : e, "graph capture");
+    }
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    size_t n = 0;
+    if (e == cudaSuccess) e = cudaGraphGetNodes(b->graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n) e = cudaGraphGetNodes(b->graph, nodes.data(), &n);
+    for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+        b->knode = nodes[i];
+    }
+    if (e == cudaSuccess && !b->knode) e = cudaErrorInvalidValue;
+    if (e != cudaSuccess) {
+      batch_drop_graph(b);
+      return cuda_fail(e, "graph instantiation");
+    }
+  } else {
+    cudaKernelNodeParams kp{};
+    void* args[1] = {b->k.args};
+    kp.func = const_cast<void*>(b->k.func);
+    kp.gridDim = dim3(b->k.grid);
+    kp.blockDim = dim3(b->k.block);
+    kp.sharedMemBytes = static_cast<unsigned>(b->k.smem);
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    e = cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp);
+    if (e != cudaSuccess) return cuda_fail(e, "graph update");
+  }
+  xc_handle::Timed* tm = nullptr;
+  if (h->profile) {
+    tm = next_timed(h, 1);
+    if (!tm) return fail(XC_ERR_CUDA, "profiling event creation failed");
+    cudaEventRecord(tm->ev[0], s);
+  }
+  e = cudaGraphLaunch(b->exec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  if (tm) cudaEventRecord(tm->ev[1], s);
+  return succeed();
+}
+
+xc_status xc_batch_tune(xc_handle* h, const void* const* in, void* const* out, void* stream,
+                        int reps, double* ms, int* best) {
+  if (!h || !h->batch) return fail(XC_ERR_INVALID_ARG, "not a batch handle");
+  if (reps < 1 || reps > 1000) return fail(XC_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+  BatchState* b = h->batch;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "tuning events");
+  double best_ms = 0.0;
+  int best_c = -1;
+  xc_status st = XC_OK;
+  for (int c = 0; c < XC_BATCH_CANDIDATES && st == XC_OK; ++c) {
+    int order[XC_BATCH_MAX_SUB], depth = 1;
+    batch_schedule(b, c, order, &depth);
+    xc::XeLaunch L[XC_BATCH_MAX_SUB];
+    st = batch_prepare(h, in, out, order, depth, L);
+    if (st != XC_OK) break;
+    float t = 0.f;
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+      if (r == 1) e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = xc::planar_setup(L, b->nsub, s);
+      if (e == cudaSuccess) e = xc::planar_launch(b->k, s);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "tuning launch");
+      break;
+    }
+    const double m = static_cast<double>(t) / reps;
+    if (ms) ms[c] = m;
+    if (best_c < 0 || m < best_ms) {
+      best_ms = m;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != XC_OK) return st;
+  // The device status word tells whether any candidate gave up on a wait.
+  st = xc_synchronize(h, stream);
+  if (st != XC_OK) return st;
+  batch_schedule(b, best_c, b->order, &b->depth);
+  batch_drop_graph(b);  // ring depths (memset sizes) may change: capture again
+  if (best) *best = best_c;
   return succeed();
 }
 

@@ -56,9 +56,27 @@ cudaError_t launch_xengine(const CUtensorMap* tmap, const XeLaunch& p, cudaStrea
 // `in_map` (8-bit input with R % 16 == 0, else NULL) is {R, F, T} int8 in
 // 128 x 1 x 64 boxes.
 cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& p, cudaStream_t s);
-constexpr int kMaxRingSlots = 64;
+constexpr int kMaxRingSlots = 256;
 int planar_ring_slots(const Geometry& g, int grid, int fmt);
 int64_t planar_slot_bytes(const Geometry& g, int fmt);
+
+// One planar launch over up to kMaxSub subarrays (same input type and
+// format; every subarray with its own ring region, counters and buffers).
+// planar_prepare fills the kernel and its parameter block (maps[i]: the
+// 8-bit input map of subarray i, or NULL; TMA staging is used only when all
+// subarrays have one); planar_setup issues the stream-ordered set-up
+// (counter zeroing, float scale pre-pass); planar_launch launches.
+constexpr int kMaxSub = 8;
+constexpr int kBatchArgBytes = 4096;
+struct PlanarKernel {
+  alignas(128) unsigned char args[kBatchArgBytes];  // holds the kernel's Batch (128-byte aligned)
+  const void* func = nullptr;
+  int grid = 0, block = 0, smem = 0;
+};
+cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps, int nsub,
+                           PlanarKernel* k);
+cudaError_t planar_setup(const XeLaunch* subs, int nsub, cudaStream_t s);
+cudaError_t planar_launch(PlanarKernel& k, cudaStream_t s);
 // Same as launch_xengine, on CTA pairs (tcgen05 cta_group::2, 256 x 256 blocks).
 cudaError_t launch_xengine_pair(const CUtensorMap* tmap, const XeLaunch& p, cudaStream_t s);
 // Ring slots for a geometry (2..16 channels, about 32 MiB).

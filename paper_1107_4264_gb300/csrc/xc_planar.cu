@@ -88,8 +88,6 @@ constexpr int kThreads = 32 * (2 + kNumEpiWarps + kNumConvWarps);
 constexpr int kTileBytes = kBlk * kBK * 2;  // 16 KiB: one plane tile
 constexpr int kStageBytes = 4 * kTileBytes;
 constexpr uint32_t kTmemCols = 512;         // 2 sets x (D_re, D_im) x 128
-constexpr uint32_t kIdesc = ptx::idesc_f16_f32(kBlk, kBlk);
-constexpr uint32_t kIdescNegB = kIdesc | (1u << 14);
 constexpr int kUnitRows = 128;  // converter unit: 128 real rows (64 inputs) x 64 samples
 constexpr int kUnitT = 64;
 constexpr uint32_t kChunkStride = kBlk * 16;  // bytes between 8-sample chunks of a tile (K)
@@ -102,8 +100,8 @@ constexpr int kNumBars = 2 * kStages + 5 + kNumConvWarps;
 constexpr int kSmemBytes = kBarOff + kNumBars * 8 + 16 + 1024;
 static_assert(kSmemBytes <= 232448, "shared memory budget");
 
-// Operand formats: tile size (log2 bytes), 16-byte K chunks per tile,
-// MMA steps per 64-sample block and ring K-tiles per 64-sample block.
+// Operand formats: tile size (log2 bytes), 16-byte K chunks per tile and
+// MMA steps per 64-sample block (ring K-tiles per block: fmt_kt()).
 enum : int { kFmtF16 = 0, kFmtHiLo = 1, kFmtF8 = 2 };
 template <int FMT>
 struct FmtT {
@@ -111,7 +109,6 @@ struct FmtT {
   static constexpr int kTile = 1 << kTileShift;
   static constexpr int kChunks = FMT == kFmtF8 ? 4 : 8;
   static constexpr int kSteps = FMT == kFmtHiLo ? 3 : 1;
-  static constexpr int kKt = FMT == kFmtHiLo ? 2 : 1;
 };
 
 struct Params {
@@ -141,6 +138,42 @@ struct Params {
   unsigned long long timeout_ns;
   int* status;
 };
+
+// One launch over up to kMaxSub subarrays (Sec. 4.2's channel-major raster
+// extended across subarrays): items and converter units are numbered
+// subarray by subarray; item_base / unit_base are their prefix sums.  Each
+// subarray has its own ring region and counters.
+struct Batch {
+  CUtensorMap maps[kMaxSub];  // 8-bit input of each subarray (read when tma_in)
+  Params sub[kMaxSub];
+  long long item_base[kMaxSub + 1];
+  long long unit_base[kMaxSub + 1];
+  int nsub;
+};
+static_assert(sizeof(Batch) <= kBatchArgBytes && alignof(Batch) <= 128, "batch parameter block");
+
+// Subarray holding global index i, starting the search at cursor s (every
+// role walks its items and units in increasing order).  Single-subarray
+// launches (MULTI = false) index subarray 0 at compile time.
+// End of a prefix-sum table (compile-time index for single launches).
+template <bool MULTI>
+__device__ __forceinline__ long long table_end(const long long* base, int nsub) {
+  if constexpr (!MULTI) {
+    return base[1];
+  } else {
+    return base[nsub];
+  }
+}
+
+template <bool MULTI>
+__device__ __forceinline__ int advance_sub(const long long* base, int nsub, long long i, int s) {
+  if constexpr (!MULTI) {
+    return 0;
+  } else {
+    while (s + 1 < nsub && i >= base[s + 1]) ++s;
+    return s;
+  }
+}
 
 // ------------------------------------------------------------ global sync
 
@@ -314,16 +347,19 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
 // input's power-of-two scale (float input) and writes 16-byte chunks: per
 // (input, plane) two fp16 chunks (8 samples each; HI/LO: two more into the
 // L tile) or one e4m3 chunk (16 samples).
-template <int DT, int FMT>
-__device__ void converter_direct(const Params& p, int cw, int lane, volatile int* abort_flag) {
-  const long long total = static_cast<long long>(p.g.F) * p.units_per_chan;
+template <int DT, int FMT, bool MULTI>
+__device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int* abort_flag) {
+  const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
   const long long stride = static_cast<long long>(gridDim.x) * kNumConvWarps;
-  int claimed = -1;
+  int sb = 0, claimed = -1, claimed_sb = -1;
   for (long long u = static_cast<long long>(blockIdx.x) * kNumConvWarps + cw; u < total; u += stride) {
-    const Unit x = unit_of(p, u);
-    if (x.c != claimed) {
+    sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
+    const Params& p = bt.sub[sb];
+    const Unit x = unit_of(p, u - bt.unit_base[sb]);
+    if (x.c != claimed || sb != claimed_sb) {
       if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
       claimed = x.c;
+      claimed_sb = sb;
     }
     const int ib = x.hb >> 1;
     uint8_t* tre = ring_tile<FMT>(p, x.slot, 0, x.kb, ib);
@@ -431,16 +467,19 @@ __device__ void converter_direct(const Params& p, int cw, int lane, volatile int
 // rows] int8 = 64 inputs x {re, im}) that always holds its next unit's box
 // in flight while the current one is converted.  A warp claims a slot for
 // itself and publishes each unit on its own: no barrier couples the warps.
-__device__ void converter_tma(const Params& p, const CUtensorMap* in_map, uint32_t buf,
-                              uint32_t bar, int cw, int lane, volatile int* abort_flag) {
-  const long long total = static_cast<long long>(p.g.F) * p.units_per_chan;
+template <bool MULTI>
+__device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int cw, int lane,
+                              volatile int* abort_flag) {
+  const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
   const long long stride = static_cast<long long>(gridDim.x) * kNumConvWarps;
-  const ptx::WaitCtl wc{p.timeout_ns, p.status, abort_flag};
+  const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
+  int sb_issue = 0;
   auto issue = [&](long long u) {
-    const Unit x = unit_of(p, u);
+    sb_issue = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb_issue);
+    const Unit x = unit_of(bt.sub[sb_issue], u - bt.unit_base[sb_issue]);
     if (lane == 0) {
       ptx::mbar_arrive_expect_tx(bar, kConvBufBytes);
-      ptx::tma_load_3d(buf, in_map, bar, x.hb * kUnitRows, x.c, x.kb * kUnitT);
+      ptx::tma_load_3d(buf, &bt.maps[sb_issue], bar, x.hb * kUnitRows, x.c, x.kb * kUnitT);
     }
   };
   const uint32_t* src = reinterpret_cast<const uint32_t*>(__cvta_shared_to_generic(static_cast<size_t>(buf)));
@@ -449,14 +488,17 @@ __device__ void converter_tma(const Params& p, const CUtensorMap* in_map, uint32
   const uint32_t jre = 2u * (lane & 1);
   const int w0 = lane >> 1;
   uint32_t phase = 0;
-  int claimed = -1;
+  int sb = 0, claimed = -1, claimed_sb = -1;
   long long u = static_cast<long long>(blockIdx.x) * kNumConvWarps + cw;
   if (u < total) issue(u);
   for (; u < total; u += stride) {
-    const Unit x = unit_of(p, u);
-    if (x.c != claimed) {
+    sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
+    const Params& p = bt.sub[sb];
+    const Unit x = unit_of(p, u - bt.unit_base[sb]);
+    if (x.c != claimed || sb != claimed_sb) {
       if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
       claimed = x.c;
+      claimed_sb = sb;
     }
     const bool got = ptx::wait_bounded(bar, phase, wc);
     if (!__all_sync(0xffffffffu, got)) return;
@@ -641,9 +683,9 @@ __device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const 
 
 // ------------------------------------------------------------------ kernel
 
-template <bool IS_INT, int DT, int FMT>
+template <bool IS_INT, int DT, int FMT, bool MULTI>
 __global__ void __launch_bounds__(kThreads, 1)
-    planar_kernel(const __grid_constant__ CUtensorMap in_map, const Params p) {
+    planar_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -685,8 +727,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
-  const ptx::WaitCtl wc{p.timeout_ns, p.status, abort_flag};
-  const unsigned upc = static_cast<unsigned>(p.units_per_chan);
+  const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
+  const long long nitems = table_end<MULTI>(bt.item_base, bt.nsub);
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -696,18 +738,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       int issued_phase[kStages];
       for (int s = 0; s < kStages; ++s) issued_phase[s] = -1;
       bool ok = true;
-      int ready_chan = -1;
-      for (long long it = blockIdx.x; ok && it < p.nitems; it += gridDim.x) {
+      int sb = 0, ready_chan = -1, ready_sb = -1;
+      for (long long it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+        sb = advance_sub<MULTI>(bt.item_base, bt.nsub, it, sb);
+        const Params& p = bt.sub[sb];
         int f, bx, by;
-        item_coords(it, p.ntiles, &f, &bx, &by);
+        item_coords(it - bt.item_base[sb], p.ntiles, &f, &bx, &by);
         const int slot = f % p.ring_slots;
-        if (f != ready_chan) {
+        if (f != ready_chan || sb != ready_sb) {
           const unsigned gen = static_cast<unsigned>(f / p.ring_slots);
-          if (!wait_counter(p.ready + slot, (gen + 1) * upc, p, abort_flag)) {
+          if (!wait_counter(p.ready + slot, (gen + 1) * static_cast<unsigned>(p.units_per_chan), p,
+                            abort_flag)) {
             ok = false;
             break;
           }
           ready_chan = f;
+          ready_sb = sb;
         }
         const bool diag = bx == by;
         constexpr int TB = FmtT<FMT>::kTile;
@@ -742,7 +788,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (issued_phase[s] < 0) continue;
           const uint64_t t0 = ptx::globaltimer();
           while (!ptx::mbar_try_wait(full_bar(s), static_cast<uint32_t>(issued_phase[s])) &&
-                 ptx::globaltimer() - t0 < p.timeout_ns) {
+                 ptx::globaltimer() - t0 < wc.timeout_ns) {
           }
         }
       }
@@ -755,10 +801,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t u = 0;
       bool ok = true;
       bool issued_any = false;
-      for (long long it = blockIdx.x; ok && it < p.nitems; it += gridDim.x) {
+      int sb = 0;
+      for (long long it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+        sb = advance_sub<MULTI>(bt.item_base, bt.nsub, it, sb);
+        const Params& p = bt.sub[sb];
         int f, bx, by;
-        item_coords(it, p.ntiles, &f, &bx, &by);
+        item_coords(it - bt.item_base[sb], p.ntiles, &f, &bx, &by);
         const bool diag = bx == by;
+        // Block shape: M = 128 rows; N trimmed to the block's valid columns
+        // (rounded up to 16), so ragged edge blocks skip the zero columns.
+        const int ncols = min(kBlk, p.n - bx * kBlk);
+        const uint32_t idesc = ptx::idesc_f16_f32(kBlk, (ncols + 15) & ~15);
+        const uint32_t idesc_negb = idesc | (1u << 14);
         if (!channel_ready(p, f, abort_flag)) {
           ok = false;
           break;
@@ -799,15 +853,15 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint64_t dbr = ptx::interleave_kmajor_desc(br + ko, kChunkStride, kGroupStride);
               const uint64_t dbi = ptx::interleave_kmajor_desc(bi + ko, kChunkStride, kGroupStride);
               if constexpr (FMT == kFmtF8) {
-                ptx::mma_f8_ss(d_re, dar, dbr, kIdesc, acc);      // Re += Ar Br^T
-                ptx::mma_f8_ss(d_re, dai, dbi, kIdesc, 1u);       // Re += Ai Bi^T
-                ptx::mma_f8_ss(d_im, dai, dbr, kIdesc, acc);      // Im += Ai Br^T
-                ptx::mma_f8_ss(d_im, dar, dbi, kIdescNegB, 1u);   // Im -= Ar Bi^T
+                ptx::mma_f8_ss(d_re, dar, dbr, idesc, acc);       // Re += Ar Br^T
+                ptx::mma_f8_ss(d_re, dai, dbi, idesc, 1u);        // Re += Ai Bi^T
+                ptx::mma_f8_ss(d_im, dai, dbr, idesc, acc);       // Im += Ai Br^T
+                ptx::mma_f8_ss(d_im, dar, dbi, idesc_negb, 1u);   // Im -= Ar Bi^T
               } else {
-                ptx::mma_f16_ss(d_re, dar, dbr, kIdesc, acc);     // Re += Ar Br^T
-                ptx::mma_f16_ss(d_re, dai, dbi, kIdesc, 1u);      // Re += Ai Bi^T
-                ptx::mma_f16_ss(d_im, dai, dbr, kIdesc, acc);     // Im += Ai Br^T
-                ptx::mma_f16_ss(d_im, dar, dbi, kIdescNegB, 1u);  // Im -= Ar Bi^T
+                ptx::mma_f16_ss(d_re, dar, dbr, idesc, acc);      // Re += Ar Br^T
+                ptx::mma_f16_ss(d_re, dai, dbi, idesc, 1u);       // Re += Ai Bi^T
+                ptx::mma_f16_ss(d_im, dai, dbr, idesc, acc);      // Im += Ai Br^T
+                ptx::mma_f16_ss(d_im, dar, dbi, idesc_negb, 1u);  // Im -= Ar Bi^T
               }
             }
             issued_any = true;
@@ -826,7 +880,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok && issued_any) {
         ptx::mma_commit(drain_bar);
         const uint64_t t0 = ptx::globaltimer();
-        while (!ptx::mbar_try_wait(drain_bar, 0) && ptx::globaltimer() - t0 < p.timeout_ns) {
+        while (!ptx::mbar_try_wait(drain_bar, 0) && ptx::globaltimer() - t0 < wc.timeout_ns) {
         }
       }
     }
@@ -834,12 +888,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;
     const uint32_t t_lanes = tmem + (static_cast<uint32_t>(q * 32) << 16);
-    const int P = p.g.P;
     uint32_t u = 0;
     bool ok = true;
-    for (long long it = blockIdx.x; ok && it < p.nitems; it += gridDim.x) {
+    int sb = 0;
+    for (long long it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+      sb = advance_sub<MULTI>(bt.item_base, bt.nsub, it, sb);
+      const Params& p = bt.sub[sb];
+      const int P = p.g.P;
       int f, bx, by;
-      item_coords(it, p.ntiles, &f, &bx, &by);
+      item_coords(it - bt.item_base[sb], p.ntiles, &f, &bx, &by);
       const int a = by * kBlk + q * 32 + lane;  // this thread's row input
       // Pieces 0..last can reach the lower station triangle for this warp.
       const int s1_hi = min(p.g.N - 1, (by * kBlk + q * 32 + 31) / P);
@@ -899,14 +956,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------------------------------------------------- converters
     const int cw = warp - (2 + kNumEpiWarps);
     if constexpr (DT == 0) {
-      if (p.tma_in) {
-        converter_tma(p, &in_map, sbase + kConvOff + cw * kConvBufBytes, conv_bar(cw), cw, lane,
-                      abort_flag);
+      if (bt.sub[0].tma_in) {  // set for every subarray or for none
+        converter_tma<MULTI>(bt, sbase + kConvOff + cw * kConvBufBytes, conv_bar(cw), cw, lane, abort_flag);
       } else {
-        converter_direct<DT, FMT>(p, cw, lane, abort_flag);
+        converter_direct<DT, FMT, MULTI>(bt, cw, lane, abort_flag);
       }
     } else {
-      converter_direct<DT, FMT>(p, cw, lane, abort_flag);
+      converter_direct<DT, FMT, MULTI>(bt, cw, lane, abort_flag);
     }
   }
 
@@ -919,23 +975,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <bool IS_INT, int DT, int FMT>
-cudaError_t launch_variant(const CUtensorMap* in_map, const Params& p, int grid, cudaStream_t s) {
-  auto kern = planar_kernel<IS_INT, DT, FMT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  if (e != cudaSuccess) return e;
-  kern<<<grid, kThreads, kSmemBytes, s>>>(*in_map, p);
-  return cudaGetLastError();
+template <bool IS_INT, int DT, int FMT, bool MULTI = false>
+const void* kernel_of() {
+  return reinterpret_cast<const void*>(planar_kernel<IS_INT, DT, FMT, MULTI>);
 }
 
-template <int DT>
-cudaError_t launch_float(const CUtensorMap* in_map, const Params& p, int fmt, int grid,
-                         cudaStream_t s) {
+// Batches of several subarrays take 8-bit input.
+const void* select_kernel(int in_dtype, int fmt, bool multi) {
+  if (in_dtype == 0) return multi ? kernel_of<true, 0, kFmtF16, true>() : kernel_of<true, 0, kFmtF16>();
+  if (multi) return nullptr;
+  if (in_dtype != 1 && in_dtype != 2) return nullptr;
+  const bool h = in_dtype == 1;
   switch (fmt) {
-    case kFmtF16: return launch_variant<false, DT, kFmtF16>(in_map, p, grid, s);
-    case kFmtHiLo: return launch_variant<false, DT, kFmtHiLo>(in_map, p, grid, s);
-    case kFmtF8: return launch_variant<false, DT, kFmtF8>(in_map, p, grid, s);
-    default: return cudaErrorInvalidValue;
+    case kFmtF16: return h ? kernel_of<false, 1, kFmtF16>() : kernel_of<false, 2, kFmtF16>();
+    case kFmtHiLo: return h ? kernel_of<false, 1, kFmtHiLo>() : kernel_of<false, 2, kFmtHiLo>();
+    case kFmtF8: return h ? kernel_of<false, 1, kFmtF8>() : kernel_of<false, 2, kFmtF8>();
+    default: return nullptr;
   }
 }
 
@@ -973,27 +1028,8 @@ __global__ void __launch_bounds__(128) input_amax_kernel(const void* __restrict_
 int fmt_kt(int fmt) { return fmt == kFmtHiLo ? 2 : 1; }
 int fmt_tile_bytes(int fmt) { return fmt == kFmtF8 ? (1 << 13) : (1 << 14); }
 
-}  // namespace
-
-int64_t planar_slot_bytes(const Geometry& g, int fmt) {
-  const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
-  return 2 * fmt_kt(fmt) * (g.Tp / kBK) * nib * fmt_tile_bytes(fmt);
-}
-
-int planar_ring_slots(const Geometry& g, int grid, int fmt) {
-  // The persistent CTAs keep about grid / blocks_per_channel channels in
-  // flight; the converters need room ahead of them.
-  const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
-  const int64_t blocks = std::max<int64_t>(1, nib * (nib + 1) / 2);
-  const int64_t inflight = (grid + blocks - 1) / blocks;
-  int64_t n = (inflight * 8 + 4) / 5 + 4;
-  const int64_t cap =
-      std::max<int64_t>(2, (256ll << 20) / std::max<int64_t>(planar_slot_bytes(g, fmt), 1));
-  n = std::max<int64_t>(4, std::min<int64_t>(std::min<int64_t>(kMaxRingSlots, cap), n));
-  return static_cast<int>(std::min<int64_t>(n, g.F));
-}
-
-cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, cudaStream_t s) {
+// Kernel parameters of one subarray.
+Params sub_params(const XeLaunch& L) {
   Params p;
   p.g = L.g;
   p.n = L.g.N * L.g.P;
@@ -1019,36 +1055,101 @@ cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, cudaStre
   p.done = L.counters + L.ring_slots;
   p.row_units = 2 * p.nib;
   p.units_per_chan = p.row_units * p.nkb;
-  p.tma_in = (L.in_dtype == 0 && in_map != nullptr) ? 1 : 0;
+  p.tma_in = 0;
   p.timeout_ns = L.timeout_ns;
   p.status = L.status;
-  if (p.nitems == 0 || p.nkb == 0) return cudaSuccess;
-  if (L.ring_slots > kMaxRingSlots) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(L.counters, 0, 2 * sizeof(unsigned) * L.ring_slots, s);
-  if (e == cudaSuccess && p.is_int) e = cudaMemsetAsync(L.amax, 0, sizeof(unsigned) * L.g.F, s);
-  if (e != cudaSuccess) return e;
-  if (p.in_amax) {
-    e = cudaMemsetAsync(L.in_amax, 0, sizeof(unsigned) * L.g.F * static_cast<size_t>(p.n), s);
-    if (e != cudaSuccess) return e;
-    const dim3 ag((p.n + 127) / 128, L.g.F, (L.g.T + 127) / 128);
-    if (ag.z > 65535u) return cudaErrorInvalidConfiguration;
-    if (L.in_dtype == 1)
-      input_amax_kernel<1><<<ag, 128, 0, s>>>(L.in, p.gains, L.in_amax, L.g, p.n);
-    else
-      input_amax_kernel<2><<<ag, 128, 0, s>>>(L.in, p.gains, L.in_amax, L.g, p.n);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+  return p;
+}
+
+}  // namespace
+
+int64_t planar_slot_bytes(const Geometry& g, int fmt) {
+  const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
+  return 2 * fmt_kt(fmt) * (g.Tp / kBK) * nib * fmt_tile_bytes(fmt);
+}
+
+int planar_ring_slots(const Geometry& g, int grid, int fmt) {
+  // The persistent CTAs keep about grid / blocks_per_channel channels in
+  // flight; the converters need room ahead of them.
+  const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
+  const int64_t blocks = std::max<int64_t>(1, nib * (nib + 1) / 2);
+  const int64_t inflight = (grid + blocks - 1) / blocks;
+  int64_t n = (inflight * 8 + 4) / 5 + 4;
+  const int64_t cap =
+      std::max<int64_t>(2, (256ll << 20) / std::max<int64_t>(planar_slot_bytes(g, fmt), 1));
+  n = std::max<int64_t>(4, std::min<int64_t>(std::min<int64_t>(kMaxRingSlots, cap), n));
+  return static_cast<int>(std::min<int64_t>(n, g.F));
+}
+
+cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps, int nsub,
+                           PlanarKernel* k) {
+  if (nsub < 1 || nsub > kMaxSub || !subs || !k) return cudaErrorInvalidValue;
+  const int dt = subs[0].in_dtype;
+  const int fmt = dt == 0 ? kFmtF16 : subs[0].fmt;
+  Batch* b = reinterpret_cast<Batch*>(k->args);
+  memset(b, 0, sizeof(Batch));
+  b->nsub = nsub;
+  bool all_tma = dt == 0;
+  for (int i = 0; i < nsub; ++i) {
+    if (subs[i].in_dtype != dt || (dt != 0 && subs[i].fmt != fmt)) return cudaErrorInvalidValue;
+    if (subs[i].ring_slots < 1 || subs[i].ring_slots > kMaxRingSlots) return cudaErrorInvalidValue;
+    b->sub[i] = sub_params(subs[i]);
+    if (maps && maps[i]) {
+      b->maps[i] = *maps[i];
+    } else {
+      all_tma = false;
+    }
+    b->item_base[i + 1] = b->item_base[i] + (b->sub[i].nkb > 0 ? b->sub[i].nitems : 0);
+    b->unit_base[i + 1] = b->unit_base[i] +
+                          (b->sub[i].nkb > 0 ? static_cast<long long>(subs[i].g.F) * b->sub[i].units_per_chan : 0);
   }
-  const int grid = static_cast<int>(std::min<long long>(p.nitems, L.grid));
-  CUtensorMap unused;
-  const CUtensorMap* im = in_map ? in_map : &unused;  // read only when p.tma_in
-  if (!in_map) memset(&unused, 0, sizeof(unused));
-  switch (L.in_dtype) {
-    case 0: return launch_variant<true, 0, kFmtF16>(im, p, grid, s);
-    case 1: return launch_float<1>(im, p, fmt, grid, s);
-    case 2: return launch_float<2>(im, p, fmt, grid, s);
-    default: return cudaErrorInvalidValue;
+  for (int i = 0; i < nsub; ++i) b->sub[i].tma_in = all_tma ? 1 : 0;
+  k->func = select_kernel(dt, fmt, nsub > 1);
+  if (!k->func) return cudaErrorInvalidValue;
+  k->grid = static_cast<int>(std::min<long long>(b->item_base[nsub], subs[0].grid));
+  k->block = kThreads;
+  k->smem = kSmemBytes;
+  return cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+cudaError_t planar_setup(const XeLaunch* subs, int nsub, cudaStream_t s) {
+  for (int i = 0; i < nsub; ++i) {
+    const XeLaunch& L = subs[i];
+    const int n = L.g.N * L.g.P;
+    cudaError_t e = cudaMemsetAsync(L.counters, 0, 2 * sizeof(unsigned) * L.ring_slots, s);
+    if (e == cudaSuccess && L.in_dtype == 0)
+      e = cudaMemsetAsync(L.amax, 0, sizeof(unsigned) * L.g.F, s);
+    if (e != cudaSuccess) return e;
+    if (L.in_dtype != 0 && L.in_amax) {
+      e = cudaMemsetAsync(L.in_amax, 0, sizeof(unsigned) * L.g.F * static_cast<size_t>(n), s);
+      if (e != cudaSuccess) return e;
+      const dim3 ag((n + 127) / 128, L.g.F, (L.g.T + 127) / 128);
+      if (ag.z > 65535u) return cudaErrorInvalidConfiguration;
+      const float2* gains = static_cast<const float2*>(L.gains);
+      if (L.in_dtype == 1)
+        input_amax_kernel<1><<<ag, 128, 0, s>>>(L.in, gains, L.in_amax, L.g, n);
+      else
+        input_amax_kernel<2><<<ag, 128, 0, s>>>(L.in, gains, L.in_amax, L.g, n);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
   }
+  return cudaSuccess;
+}
+
+cudaError_t planar_launch(PlanarKernel& k, cudaStream_t s) {
+  if (k.grid <= 0) return cudaSuccess;
+  void* args[1] = {k.args};
+  return cudaLaunchKernel(k.func, dim3(k.grid), dim3(k.block), args, static_cast<size_t>(k.smem), s);
+}
+
+cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, cudaStream_t s) {
+  static thread_local PlanarKernel k;
+  const CUtensorMap* maps[1] = {in_map};
+  cudaError_t e = planar_prepare(&L, maps, 1, &k);
+  if (e == cudaSuccess && k.grid > 0) e = planar_setup(&L, 1, s);
+  if (e == cudaSuccess) e = planar_launch(k, s);
+  return e;
 }
 
 }  // namespace xc

@@ -31,6 +31,8 @@ XC_PREC_FP16, XC_PREC_HILO, XC_PREC_FP8 = 0, 1, 2
 (XC_ENGINE_TENSOR, XC_ENGINE_FP32, XC_ENGINE_TENSOR_2PASS, XC_ENGINE_TENSOR_1CTA,
  XC_ENGINE_TENSOR_PAIR) = 0, 1, 2, 3, 4
 XC_CI8_MAX_NTIME = 66572
+XC_BATCH_MAX_SUB = 8
+XC_BATCH_CANDIDATES = 6
 
 # Symbols declared in include/xc.h (checked by the tests against the header).
 EXPORTS = [
@@ -38,6 +40,7 @@ EXPORTS = [
     "xc_last_error_message", "xc_status_string", "xc_set_option", "xc_synchronize",
     "xc_correlate_stream", "xc_input_bytes", "xc_output_bytes", "xc_tri_index", "xc_tri_coords",
     "xc_version", "xc_kernel_times", "xc_correlate_noalloc", "xc_set_gains", "xc_get_grad_gains",
+    "xc_batch_create", "xc_batch_correlate", "xc_batch_tune",
 ]
 
 _lib: Optional[ctypes.CDLL] = None
@@ -72,6 +75,11 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "xc_correlate_noalloc": ([i32, i32, i32, i32, i32, vp, vp, vp, vp], i32),
         "xc_set_gains": ([vp, vp], i32),
         "xc_get_grad_gains": ([vp, vp, vp], i32),
+        "xc_batch_create": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                             i32, i32], vp),
+        "xc_batch_correlate": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i32),
+        "xc_batch_tune": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, i32,
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -342,3 +350,103 @@ def correlate_autograd(engine: "Correlator", x, gains):
             return grad_x, grad_g
 
     return _Correlate.apply(x, gains)
+
+
+# ------------------------------------------------------------ batched form
+
+
+def xc_batch_create(nstation, nfreq, ntime, npol: int, in_dtype: int) -> int:
+    n = len(nstation)
+    arr = ctypes.c_int * n
+    h = load().xc_batch_create(n, arr(*nstation), arr(*nfreq), arr(*ntime), npol, in_dtype)
+    if not h:
+        raise XcError(xc_last_error(), xc_last_error_message())
+    return h
+
+
+def _ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*ptrs)
+
+
+def xc_batch_correlate(h: int, in_ptrs, out_ptrs, stream: int = 0) -> int:
+    return load().xc_batch_correlate(h, _ptr_array(in_ptrs), _ptr_array(out_ptrs), stream)
+
+
+def xc_batch_tune(h: int, in_ptrs, out_ptrs, stream: int = 0, reps: int = 3):
+    ms = (ctypes.c_double * XC_BATCH_CANDIDATES)()
+    best = ctypes.c_int(-1)
+    _check(load().xc_batch_tune(h, _ptr_array(in_ptrs), _ptr_array(out_ptrs), stream, reps, ms,
+                                ctypes.byref(best)))
+    return list(ms), best.value
+
+
+class BatchCorrelator:
+    """Subarrays ``[(nstation, nfreq, ntime), ...]`` (8-bit input, one npol)
+    correlated by one persistent launch replayed from a CUDA graph."""
+
+    def __init__(self, subs, npol: int = 2, timeout_ms: Optional[int] = None):
+        import torch
+        self._torch = torch
+        self.subs = [tuple(int(v) for v in s) for s in subs]
+        self.npol = npol
+        self.h = xc_batch_create([s[0] for s in self.subs], [s[1] for s in self.subs],
+                                 [s[2] for s in self.subs], npol, XC_CI8)
+        if timeout_ms is not None:
+            _check(xc_set_option(self.h, XC_OPT_TIMEOUT_MS, timeout_ms))
+
+    def in_shape(self, i: int):
+        N, F, T = self.subs[i]
+        return (T, F, N, self.npol, 2)
+
+    def out_shape(self, i: int):
+        N, F, _ = self.subs[i]
+        return (F, N * (N + 1) // 2, self.npol * self.npol, 2)
+
+    def new_outputs(self, device=None):
+        dev = device or self._torch.device("cuda")
+        return [self._torch.zeros(self.out_shape(i), dtype=self._torch.int32, device=dev)
+                for i in range(len(self.subs))]
+
+    def _check_bufs(self, xs, outs):
+        assert len(xs) == len(self.subs) and len(outs) == len(self.subs)
+        for i, (x, o) in enumerate(zip(xs, outs)):
+            assert x.is_cuda and x.is_contiguous() and x.dtype == self._torch.int8
+            assert tuple(x.shape) == self.in_shape(i), (i, x.shape)
+            assert o.is_cuda and o.is_contiguous() and o.dtype == self._torch.int32
+            assert tuple(o.shape) == self.out_shape(i), (i, o.shape)
+
+    def set_option(self, key: int, value: int) -> None:
+        _check(xc_set_option(self.h, key, int(value)))
+
+    def correlate(self, xs, outs=None, stream=None, sync: bool = False):
+        if outs is None:
+            outs = self.new_outputs(xs[0].device)
+        self._check_bufs(xs, outs)
+        s = (stream or self._torch.cuda.current_stream()).cuda_stream
+        _check(xc_batch_correlate(self.h, [x.data_ptr() for x in xs], [o.data_ptr() for o in outs], s))
+        if sync:
+            _check(xc_synchronize(self.h, s))
+        return outs
+
+    def tune(self, xs, outs, reps: int = 3, stream=None):
+        self._check_bufs(xs, outs)
+        s = (stream or self._torch.cuda.current_stream()).cuda_stream
+        return xc_batch_tune(self.h, [x.data_ptr() for x in xs], [o.data_ptr() for o in outs], s, reps)
+
+    def synchronize(self, stream=None) -> None:
+        s = (stream or self._torch.cuda.current_stream()).cuda_stream
+        _check(xc_synchronize(self.h, s))
+
+    def kernel_times(self, reset: bool = True):
+        return xc_kernel_times(self.h, reset)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            xc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
