@@ -62,6 +62,9 @@ def parse_args():
                     help="channels per integration (default 1024; smaller only for profiling captures)")
     ap.add_argument("--integrations", type=int, default=N_INTEGRATIONS,
                     help="integrations per step (default 10)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision, batched and differentiable workloads")
+    ap.add_argument("--form-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -228,6 +231,92 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- ours
+
+
+def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks):
+    """Throughput of the other workloads (one line each in the result):
+    precision forms (fp16 input, gains), the batched six-subarray launch and
+    the differentiable workload's forward and adjoint."""
+    res = {}
+    k = args.form_steps
+
+    def executed_planar(w, steps_per_block):
+        nb = (w.npol * w.nstation + 127) // 128
+        return 8 * (nb * (nb + 1) // 2) * 128 * 128 * ((w.ntime + 63) // 64 * 64) * w.nfreq * steps_per_block
+
+    # Precision workload: N=512 x 2 pols, F=480, T=2048, fp16 input, gains.
+    w = synth.PRECISION
+    x, g = synth.precision_input(w, device=dev)
+    x16 = x.to(torch.float16)
+    del x
+    gains = torch.from_numpy(g).float().to(dev)
+    prec = {}
+    for name, form, blk, steps, peak_ratio in (("fp16", xc.XC_PREC_FP16, 0, 1, 1.0),
+                                               ("hilo_fp64_block_64", xc.XC_PREC_HILO, 64, 3, 1.0),
+                                               ("fp8_e4m3", xc.XC_PREC_FP8, 0, 1, 2.0)):
+        eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "float16", precision=form,
+                            fp64_block=blk)
+        eng.set_gains(gains)
+        out = eng.new_output()
+        eng.correlate(x16, out=out, stream=stream)
+        eng.synchronize(stream)
+        eng.set_option(xc.XC_OPT_PROFILE, 1)
+        ms = timed(lambda: eng.correlate(x16, out=out, stream=stream), k) / k
+        eng.synchronize(stream)
+        (_, kms), (_, nk) = eng.kernel_times(reset=True)
+        kms /= max(nk, 1)
+        ex = executed_planar(w, steps)
+        peak = peaks["bf16_tflops"] * peak_ratio
+        prec[name] = {"tops": w.useful_ops / (ms * 1e-3) / 1e12, "ms": ms,
+                      "kernel_ms_incl_scale_pass": kms,
+                      "executed_tflops": ex / (kms * 1e-3) / 1e12,
+                      "frac_of_peak": ex / (kms * 1e-3) / 1e12 / peak,
+                      "peak": "%s x %.0f (bf16 burst x nominal %s/bf16 ratio)"
+                              % (peaks["bf16_tflops"], peak_ratio, name.split("_")[0])}
+        eng.close()
+    del x16
+    res["precision"] = {"workload": w.name, "useful_ops": w.useful_ops, "forms": prec,
+                        "errors": "see tests/test_precision_gpu.py (fp16 3e-5, hi/lo 7e-7, fp8 3.5e-3 Frobenius)"}
+
+    # Batched workload: six subarrays in one persistent launch (graph replay).
+    subs = [(b.nstation, b.nfreq, b.ntime) for b in synth.BATCHED]
+    xs = [synth.int8_sky(b, device=dev) for b in synth.BATCHED]
+    bc = xc.BatchCorrelator(subs, npol=2)
+    outs = bc.new_outputs()
+    cand_ms, best = bc.tune(xs, outs, reps=2, stream=stream)
+    bc.correlate(xs, outs, stream=stream)
+    bc.synchronize(stream)
+    ms = timed(lambda: bc.correlate(xs, outs, stream=stream), k) / k
+    bc.synchronize(stream)
+    useful = sum(b.useful_ops for b in synth.BATCHED)
+    res["batched"] = {"subarrays": [b.name for b in synth.BATCHED], "useful_ops": useful,
+                      "tops": useful / (ms * 1e-3) / 1e12, "ms": ms,
+                      "tuner_candidate_ms": cand_ms, "tuner_best": best, "launches_per_call": 1}
+    bc.close()
+    del xs, outs
+
+    # Differentiable workload: forward with gains, adjoint (grad_x, grad_g).
+    w = synth.DIFF
+    x, g, _, _ = synth.diff_inputs(w, device=dev)
+    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "float32")
+    eng.set_gains(torch.from_numpy(g).float().to(dev))
+    out = eng.new_output()
+    go = torch.randn(out.shape, device=dev)
+    gx = torch.empty_like(x)
+    eng.correlate(x, out=out, stream=stream)
+    eng.correlate_backward(go, x, grad_in=gx, stream=stream)
+    eng.synchronize(stream)
+    fms = timed(lambda: eng.correlate(x, out=out, stream=stream), k) / k
+    bms = timed(lambda: eng.correlate_backward(go, x, grad_in=gx, stream=stream), k) / k
+    eng.synchronize(stream)
+    n = w.npol * w.nstation
+    bwd_ops = 8 * w.nfreq * n * n * w.ntime
+    res["differentiable"] = {"workload": w.name, "forward_tops": w.useful_ops / (fms * 1e-3) / 1e12,
+                             "forward_ms": fms, "backward_tops": bwd_ops / (bms * 1e-3) / 1e12,
+                             "backward_ms": bms, "backward_ops": bwd_ops,
+                             "backward_arithmetic": "fp32 CUDA-core complex GEMM (H_f = G_f + G_f^H) x (g x)"}
+    eng.close()
+    return res
 
 
 def run_xc(args):
@@ -400,6 +489,9 @@ def run_xc(args):
             "h2d_gbs": host_in.numel() * args.e2e_steps / (ems * 1e-3) / 1e9,
         }
         del host_in, host_out
+
+    if not args.no_forms and world == 1:
+        result["workloads"] = measure_forms(args, torch, xc, synth, dev, stream, timed, peaks)
 
     # CPU baseline: the oracle as it stands, bounded sample, rank 0 at N=1.
     if not args.no_cpu_baseline and world == 1 and rank == 0:

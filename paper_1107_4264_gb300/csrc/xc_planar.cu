@@ -301,6 +301,16 @@ __device__ __forceinline__ bool claim_slot_warp(const Params& p, int c, int lane
   return __all_sync(0xffffffffu, ok);
 }
 
+// Would a claim of channel c's slot have to wait for the slot's previous
+// channel?  (Checked before a warp waits while it holds an unpublished unit.)
+__device__ __forceinline__ bool slot_busy(const Params& p, int c, int lane) {
+  const unsigned gen = static_cast<unsigned>(c / p.ring_slots);
+  bool busy = false;
+  if (gen > 0 && lane == 0)
+    busy = ld_acquire(p.done + (c % p.ring_slots)) < gen * static_cast<unsigned>(p.ntiles);
+  return __any_sync(0xffffffffu, busy);
+}
+
 // Publish one converted unit: every writing lane orders its generic stores
 // before later async-proxy (bulk copy) reads, then one release.
 __device__ __forceinline__ void publish_unit(const Params& p, int slot, int lane) {
@@ -467,6 +477,10 @@ __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int
 // rows] int8 = 64 inputs x {re, im}) that always holds its next unit's box
 // in flight while the current one is converted.  A warp claims a slot for
 // itself and publishes each unit on its own: no barrier couples the warps.
+// A unit is published after the next unit's shared-memory reads, so its
+// stores have drained by the time the proxy fence waits for them; a warp
+// that would have to wait for a slot publishes first (a consumer of the
+// slot's previous channel may need that unit).
 template <bool MULTI>
 __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int cw, int lane,
                               volatile int* abort_flag) {
@@ -479,7 +493,10 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
     const Unit x = unit_of(bt.sub[sb_issue], u - bt.unit_base[sb_issue]);
     if (lane == 0) {
       ptx::mbar_arrive_expect_tx(bar, kConvBufBytes);
-      ptx::tma_load_3d(buf, &bt.maps[sb_issue], bar, x.hb * kUnitRows, x.c, x.kb * kUnitT);
+      // The input streams through once: first in line for L2 replacement, so
+      // the operand ring it is converted into stays resident.
+      ptx::tma_load_3d_hint(buf, &bt.maps[sb_issue], bar, x.hb * kUnitRows, x.c, x.kb * kUnitT,
+                            ptx::l2_policy_evict_first());
     }
   };
   const uint32_t* src = reinterpret_cast<const uint32_t*>(__cvta_shared_to_generic(static_cast<size_t>(buf)));
@@ -489,6 +506,8 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
   const int w0 = lane >> 1;
   uint32_t phase = 0;
   int sb = 0, claimed = -1, claimed_sb = -1;
+  const Params* pend = nullptr;  // converted unit not yet published (and its slot)
+  int pend_slot = 0;
   long long u = static_cast<long long>(blockIdx.x) * kNumConvWarps + cw;
   if (u < total) issue(u);
   for (; u < total; u += stride) {
@@ -496,6 +515,10 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
     const Params& p = bt.sub[sb];
     const Unit x = unit_of(p, u - bt.unit_base[sb]);
     if (x.c != claimed || sb != claimed_sb) {
+      if (pend && slot_busy(p, x.c, lane)) {
+        publish_unit(*pend, pend_slot, lane);
+        pend = nullptr;
+      }
       if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
       claimed = x.c;
       claimed_sb = sb;
@@ -513,45 +536,48 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
     __syncwarp();
     ptx::fence_proxy_async_smem();
     if (u + stride < total) issue(u + stride);
-    // max |x| over the unit (zero-filled rows and samples contribute 0).
-    unsigned m = 0;
-#pragma unroll
-    for (int t = 0; t < kUnitT; ++t) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int va = static_cast<int>(static_cast<int8_t>((wa[t] >> (8 * (jre + k))) & 0xffu));
-        const int vb = static_cast<int>(static_cast<int8_t>((wb[t] >> (8 * (jre + k))) & 0xffu));
-        m = max(m, static_cast<unsigned>(max(va < 0 ? -va : va, vb < 0 ? -vb : vb)));
-      }
+    if (pend) {
+      publish_unit(*pend, pend_slot, lane);
+      pend = nullptr;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) atomicMax(p.amax + x.c, m);
     const int ib = x.hb >> 1;
     uint8_t* tre = ring_tile<kFmtF16>(p, x.slot, 0, x.kb, ib);
     uint8_t* tim = ring_tile<kFmtF16>(p, x.slot, 1, x.kb, ib);
     const int row = (x.hb & 1) * 64 + lane;
+    // Ring tiles are read back by every block of the channel: keep them in L2.
+    const uint64_t pol_last = ptx::l2_policy_evict_last();
+    // max |x| over the unit from the converted (exact) fp16 values; zero-filled
+    // rows and samples contribute 0.
+    __half2 mx[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mx[q] = __float2half2_rn(0.f);
+    auto store4 = [&](uint8_t* dst, const uint32_t* W, uint32_t j, __half2& m) {
+      const uint32_t v0 = pair_i8(W[0], W[1], j), v1 = pair_i8(W[2], W[3], j);
+      const uint32_t v2 = pair_i8(W[4], W[5], j), v3 = pair_i8(W[6], W[7], j);
+      m = __hmax2(m, __hmax2(__habs2(*reinterpret_cast<const __half2*>(&v0)),
+                             __habs2(*reinterpret_cast<const __half2*>(&v1))));
+      m = __hmax2(m, __hmax2(__habs2(*reinterpret_cast<const __half2*>(&v2)),
+                             __habs2(*reinterpret_cast<const __half2*>(&v3))));
+      ptx::st_global_v4_hint(dst, v0, v1, v2, v3, pol_last);
+    };
 #pragma unroll
     for (int cc = 0; cc < 8; ++cc) {
       const uint32_t off = cc * kChunkStride + row * 16;
-      const uint32_t* A = wa + 8 * cc;
-      const uint32_t* B = wb + 8 * cc;
-      *reinterpret_cast<uint4*>(tre + off) =
-          make_uint4(pair_i8(A[0], A[1], jre), pair_i8(A[2], A[3], jre), pair_i8(A[4], A[5], jre),
-                     pair_i8(A[6], A[7], jre));
-      *reinterpret_cast<uint4*>(tim + off) =
-          make_uint4(pair_i8(A[0], A[1], jre + 1), pair_i8(A[2], A[3], jre + 1),
-                     pair_i8(A[4], A[5], jre + 1), pair_i8(A[6], A[7], jre + 1));
-      *reinterpret_cast<uint4*>(tre + off + 32 * 16) =
-          make_uint4(pair_i8(B[0], B[1], jre), pair_i8(B[2], B[3], jre), pair_i8(B[4], B[5], jre),
-                     pair_i8(B[6], B[7], jre));
-      *reinterpret_cast<uint4*>(tim + off + 32 * 16) =
-          make_uint4(pair_i8(B[0], B[1], jre + 1), pair_i8(B[2], B[3], jre + 1),
-                     pair_i8(B[4], B[5], jre + 1), pair_i8(B[6], B[7], jre + 1));
+      store4(tre + off, wa + 8 * cc, jre, mx[0]);
+      store4(tim + off, wa + 8 * cc, jre + 1, mx[1]);
+      store4(tre + off + 32 * 16, wb + 8 * cc, jre, mx[2]);
+      store4(tim + off + 32 * 16, wb + 8 * cc, jre + 1, mx[3]);
     }
-    publish_unit(p, x.slot, lane);
+    const __half2 mm = __hmax2(__hmax2(mx[0], mx[1]), __hmax2(mx[2], mx[3]));
+    unsigned m = static_cast<unsigned>(fmaxf(__low2float(mm), __high2float(mm)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) atomicMax(p.amax + x.c, m);
+    pend = &p;
+    pend_slot = x.slot;
     if (*abort_flag) return;
   }
+  if (pend) publish_unit(*pend, pend_slot, lane);
 }
 
 // --------------------------------------------------------------- epilogue
@@ -757,6 +783,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const bool diag = bx == by;
         constexpr int TB = FmtT<FMT>::kTile;
+        const uint64_t pol_last = ptx::l2_policy_evict_last();  // tiles are shared by the channel's blocks
         for (int st = 0; ok && st < p.nkb * FmtT<FMT>::kSteps; ++st) {
           // Step st: K-block kb; HI/LO steps j = 0, 1, 2 take (H, H), (L, H), (H, L).
           const int kb = st / FmtT<FMT>::kSteps, j = st - kb * FmtT<FMT>::kSteps;
@@ -770,11 +797,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t dst = sbase + stage * kStageBytes;
           const uint32_t fb = full_bar(stage);
           ptx::mbar_arrive_expect_tx(fb, same ? 2 * TB : 4 * TB);
-          ptx::bulk_load(dst, ring_tile<FMT>(p, slot, 0, kta, by), TB, fb);
-          ptx::bulk_load(dst + TB, ring_tile<FMT>(p, slot, 1, kta, by), TB, fb);
+          ptx::bulk_load_hint(dst, ring_tile<FMT>(p, slot, 0, kta, by), TB, fb, pol_last);
+          ptx::bulk_load_hint(dst + TB, ring_tile<FMT>(p, slot, 1, kta, by), TB, fb, pol_last);
           if (!same) {
-            ptx::bulk_load(dst + 2 * TB, ring_tile<FMT>(p, slot, 0, ktb, bx), TB, fb);
-            ptx::bulk_load(dst + 3 * TB, ring_tile<FMT>(p, slot, 1, ktb, bx), TB, fb);
+            ptx::bulk_load_hint(dst + 2 * TB, ring_tile<FMT>(p, slot, 0, ktb, bx), TB, fb, pol_last);
+            ptx::bulk_load_hint(dst + 3 * TB, ring_tile<FMT>(p, slot, 1, ktb, bx), TB, fb, pol_last);
           }
           issued_phase[stage] = static_cast<int>(phase);
           if (++stage == kStages) {
