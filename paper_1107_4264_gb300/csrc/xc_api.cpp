@@ -322,7 +322,7 @@ xc_status encode_operand_map(CUtensorMap* map, void* base, int64_t R, int64_t Tp
 }
 
 // 8-bit input [T][F][R] as a 3-D tensor {R, F, T}, loaded in boxes of
-// 128 rows x 1 channel x 64 samples (zero fill past R and T).
+// 128 rows x 1 channel x kPlanarUnitT samples (zero fill past R and T).
 xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g) {
   EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
@@ -330,7 +330,7 @@ xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry&
                               static_cast<cuuint64_t>(g.T)};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(g.R),
                                  static_cast<cuuint64_t>(g.R) * g.F};
-  const cuuint32_t box[3] = {128, 1, 64};
+  const cuuint32_t box[3] = {128, 1, static_cast<cuuint32_t>(xc::kPlanarUnitT)};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(in), dims, strides, box,
                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

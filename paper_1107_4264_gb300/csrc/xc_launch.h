@@ -57,6 +57,9 @@ cudaError_t launch_xengine(const CUtensorMap* tmap, const XeLaunch& p, cudaStrea
 // 128 x 1 x 64 boxes.
 cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& p, cudaStream_t s);
 constexpr int kMaxRingSlots = 256;
+// Samples per converter unit of the planar engine (8-bit input arrives by TMA
+// in 128-row x 1 x kPlanarUnitT boxes).
+constexpr int kPlanarUnitT = 64;
 int planar_ring_slots(const Geometry& g, int grid, int fmt);
 int64_t planar_slot_bytes(const Geometry& g, int fmt);
 

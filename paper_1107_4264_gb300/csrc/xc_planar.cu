@@ -88,8 +88,9 @@ constexpr int kThreads = 32 * (2 + kNumEpiWarps + kNumConvWarps);
 constexpr int kTileBytes = kBlk * kBK * 2;  // 16 KiB: one plane tile
 constexpr int kStageBytes = 4 * kTileBytes;
 constexpr uint32_t kTmemCols = 512;         // 2 sets x (D_re, D_im) x 128
-constexpr int kUnitRows = 128;  // converter unit: 128 real rows (64 inputs) x 64 samples
-constexpr int kUnitT = 64;
+constexpr int kUnitRows = 128;  // converter unit: 128 real rows (64 inputs) x kUnitT samples
+constexpr int kUnitT = kPlanarUnitT;
+static_assert(kUnitT == 32 || kUnitT == 64, "a unit covers a whole or half 64-sample K-block");
 constexpr uint32_t kChunkStride = kBlk * 16;  // bytes between 8-sample chunks of a tile (K)
 constexpr uint32_t kGroupStride = 8 * 16;     // bytes between 8-input groups of a tile (M/N)
 constexpr int kConvBufBytes = kUnitRows * kUnitT;  // int8 staging per converter warp
@@ -271,10 +272,11 @@ __device__ __forceinline__ int scale_exp(unsigned bits) {
 }
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }
 
-// A unit: 64 inputs (half block hb) x 64 samples (K-block kb) of channel c,
-// units numbered channel-major with the K-block fastest.
+// A unit: 64 inputs (half block hb) x kUnitT samples (unit ku along K) of
+// channel c, units numbered channel-major with K fastest; it fills 8-sample
+// chunks cbase .. cbase + kUnitT/8 - 1 of the tiles of K-block kb.
 struct Unit {
-  int c, slot, hb, kb;
+  int c, slot, hb, ku, kb, cbase;
 };
 
 __device__ __forceinline__ Unit unit_of(const Params& p, long long u) {
@@ -282,8 +284,11 @@ __device__ __forceinline__ Unit unit_of(const Params& p, long long u) {
   x.c = static_cast<int>(u / p.units_per_chan);
   const int w = static_cast<int>(u % p.units_per_chan);
   x.slot = x.c % p.ring_slots;
-  x.hb = w / p.nkb;
-  x.kb = w % p.nkb;
+  const int nku = p.nkb * (kBK / kUnitT);
+  x.hb = w / nku;
+  x.ku = w % nku;
+  x.kb = x.ku * kUnitT / kBK;
+  x.cbase = (x.ku * kUnitT % kBK) / 8;
   return x;
 }
 
@@ -313,10 +318,20 @@ __device__ __forceinline__ bool slot_busy(const Params& p, int c, int lane) {
 
 // Publish one converted unit: every writing lane orders its generic stores
 // before later async-proxy (bulk copy) reads, then one release.
-__device__ __forceinline__ void publish_unit(const Params& p, int slot, int lane) {
+__device__ __forceinline__ void publish_unit(const Params& p, int slot, int lane, unsigned n = 1) {
   fence_proxy_async_global();
   __syncwarp();
-  if (lane == 0) red_release_add(p.ready + slot, 1u);
+  if (lane == 0) red_release_add(p.ready + slot, n);
+}
+
+// Converter warps take their units in runs of kUnitRun consecutive units
+// (the same channel except at channel ends): one slot claim and one publish
+// (fence + release of the whole count) per run instead of per unit.  Warp gw
+// of nw takes runs gw, gw + nw, gw + 2 nw, ... of the global unit list.
+constexpr int kUnitRun = 2;
+__device__ __forceinline__ long long first_unit(long long gw) { return gw * kUnitRun; }
+__device__ __forceinline__ long long next_unit(long long u, long long nw) {
+  return (u % kUnitRun != kUnitRun - 1) ? u + 1 : u + 1 + (nw - 1) * kUnitRun;
 }
 
 // Complex sample (re, im) of input a at sample t, channel c, as fp32.
@@ -397,7 +412,7 @@ __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int
       float2 v0[16], v1[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int t = x.kb * kBK + g * 16 + i;
+        const int t = x.ku * kUnitT + g * 16 + i;
         v0[i] = (a0 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a0, t) : make_float2(0.f, 0.f);
         v1[i] = (a1 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a1, t) : make_float2(0.f, 0.f);
       }
@@ -409,7 +424,7 @@ __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int
         }
       }
       if constexpr (FMT == kFmtF8) {
-        const uint32_t off = g * kChunkStride + row0 * 16;
+        const uint32_t off = (x.cbase / 2 + g) * kChunkStride + row0 * 16;
         uint32_t r0[4], i0[4], r1[4], i1[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -427,7 +442,7 @@ __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int
       } else {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const uint32_t off = (2 * g + h) * kChunkStride + row0 * 16;
+          const uint32_t off = (x.cbase + 2 * g + h) * kChunkStride + row0 * 16;
           uint32_t r0[4], i0[4], r1[4], i1[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
@@ -485,7 +500,7 @@ template <bool MULTI>
 __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int cw, int lane,
                               volatile int* abort_flag) {
   const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
-  const long long stride = static_cast<long long>(gridDim.x) * kNumConvWarps;
+  const long long nw = static_cast<long long>(gridDim.x) * kNumConvWarps;
   const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
   int sb_issue = 0;
   auto issue = [&](long long u) {
@@ -495,7 +510,7 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
       ptx::mbar_arrive_expect_tx(bar, kConvBufBytes);
       // The input streams through once: first in line for L2 replacement, so
       // the operand ring it is converted into stays resident.
-      ptx::tma_load_3d_hint(buf, &bt.maps[sb_issue], bar, x.hb * kUnitRows, x.c, x.kb * kUnitT,
+      ptx::tma_load_3d_hint(buf, &bt.maps[sb_issue], bar, x.hb * kUnitRows, x.c, x.ku * kUnitT,
                             ptx::l2_policy_evict_first());
     }
   };
@@ -506,17 +521,19 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
   const int w0 = lane >> 1;
   uint32_t phase = 0;
   int sb = 0, claimed = -1, claimed_sb = -1;
-  const Params* pend = nullptr;  // converted unit not yet published (and its slot)
-  int pend_slot = 0;
-  long long u = static_cast<long long>(blockIdx.x) * kNumConvWarps + cw;
+  // Converted units not yet published: their subarray, slot, channel, count.
+  const Params* pend = nullptr;
+  int pend_slot = 0, pend_c = -1, pend_sb = -1;
+  unsigned pend_n = 0;
+  long long u = first_unit(static_cast<long long>(blockIdx.x) * kNumConvWarps + cw);
   if (u < total) issue(u);
-  for (; u < total; u += stride) {
+  for (; u < total; u = next_unit(u, nw)) {
     sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
     const Params& p = bt.sub[sb];
     const Unit x = unit_of(p, u - bt.unit_base[sb]);
     if (x.c != claimed || sb != claimed_sb) {
       if (pend && slot_busy(p, x.c, lane)) {
-        publish_unit(*pend, pend_slot, lane);
+        publish_unit(*pend, pend_slot, lane, pend_n);
         pend = nullptr;
       }
       if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
@@ -535,9 +552,12 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
     }
     __syncwarp();
     ptx::fence_proxy_async_smem();
-    if (u + stride < total) issue(u + stride);
-    if (pend) {
-      publish_unit(*pend, pend_slot, lane);
+    const long long un = next_unit(u, nw);
+    if (un < total) issue(un);
+    // A finished run (or the units of another channel) is published now: its
+    // stores have drained during this unit's shared-memory reads.
+    if (pend && (pend_n == kUnitRun || pend_c != x.c || pend_sb != sb)) {
+      publish_unit(*pend, pend_slot, lane, pend_n);
       pend = nullptr;
     }
     const int ib = x.hb >> 1;
@@ -561,8 +581,8 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
       ptx::st_global_v4_hint(dst, v0, v1, v2, v3, pol_last);
     };
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc) {
-      const uint32_t off = cc * kChunkStride + row * 16;
+    for (int cc = 0; cc < kUnitT / 8; ++cc) {
+      const uint32_t off = (x.cbase + cc) * kChunkStride + row * 16;
       store4(tre + off, wa + 8 * cc, jre, mx[0]);
       store4(tim + off, wa + 8 * cc, jre + 1, mx[1]);
       store4(tre + off + 32 * 16, wb + 8 * cc, jre, mx[2]);
@@ -573,11 +593,18 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) atomicMax(p.amax + x.c, m);
-    pend = &p;
-    pend_slot = x.slot;
+    if (pend) {
+      ++pend_n;
+    } else {
+      pend = &p;
+      pend_slot = x.slot;
+      pend_c = x.c;
+      pend_sb = sb;
+      pend_n = 1;
+    }
     if (*abort_flag) return;
   }
-  if (pend) publish_unit(*pend, pend_slot, lane);
+  if (pend) publish_unit(*pend, pend_slot, lane, pend_n);
 }
 
 // --------------------------------------------------------------- epilogue
@@ -1081,7 +1108,7 @@ Params sub_params(const XeLaunch& L) {
   p.ready = L.counters;
   p.done = L.counters + L.ring_slots;
   p.row_units = 2 * p.nib;
-  p.units_per_chan = p.row_units * p.nkb;
+  p.units_per_chan = p.row_units * p.nkb * (kBK / kUnitT);
   p.tma_in = 0;
   p.timeout_ns = L.timeout_ns;
   p.status = L.status;
