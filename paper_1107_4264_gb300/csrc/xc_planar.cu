@@ -780,6 +780,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
+  // Hi/lo operands: 22-bit products lose accuracy in a long fp32 TMEM
+  // accumulation, so the MMA restarts its accumulator (buffer 0) every
+  // 64-sample K-block and the epilogue adds each block into a round-to-nearest
+  // fp32 running sum held in TMEM columns 256..511.
+  constexpr bool kTmemSum = FMT == kFmtHiLo;
   const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
   const long long nitems = table_end<MULTI>(bt.item_base, bt.nsub);
 
@@ -876,8 +881,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int ch = 0; ok && ch < nchunks; ++ch) {
           const int kb0 = ch * chunk_kb;
           const int kb1 = min(p.nkb, kb0 + chunk_kb);
-          const uint32_t ab = u & 1u;
-          const uint32_t ap = (u >> 1) & 1u;
+          // Accumulation groups: the whole chunk, or one K-block per group when
+          // the epilogue sums 64-sample fp32 blocks in TMEM (buffer 0 only).
+          const int gstep = kTmemSum ? 1 : (kb1 - kb0);
+          for (int g0 = kb0; ok && g0 < kb1; g0 += gstep) {
+          const int g1 = min(kb1, g0 + gstep);
+          const uint32_t ab = kTmemSum ? 0u : (u & 1u);
+          const uint32_t ap = kTmemSum ? (u & 1u) : ((u >> 1) & 1u);
           if (!ptx::wait_bounded(acce_bar(ab), ap ^ 1u, wc)) {
             ok = false;
             break;
@@ -886,7 +896,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t d_re = tmem + ab * 256;
           const uint32_t d_im = d_re + 128;
           constexpr int TB = FmtT<FMT>::kTile;
-          for (int st = kb0 * FmtT<FMT>::kSteps; st < kb1 * FmtT<FMT>::kSteps; ++st) {
+          for (int st = g0 * FmtT<FMT>::kSteps; st < g1 * FmtT<FMT>::kSteps; ++st) {
             if (!ptx::wait_bounded(full_bar(stage), phase, wc)) {
               ok = false;
               break;
@@ -899,7 +909,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t bi = same ? ai : ar + 3 * TB;
 #pragma unroll
             for (int k = 0; k < FmtT<FMT>::kChunks / 2; ++k) {
-              const uint32_t acc = (st > kb0 * FmtT<FMT>::kSteps || k > 0) ? 1u : 0u;
+              const uint32_t acc = (st > g0 * FmtT<FMT>::kSteps || k > 0) ? 1u : 0u;
               // K-step k covers 16-byte chunks 2k and 2k + 1 (16 fp16 or 32 e4m3 samples).
               const uint32_t ko = k * 2 * kChunkStride;
               const uint64_t dar = ptx::interleave_kmajor_desc(ar + ko, kChunkStride, kGroupStride);
@@ -928,6 +938,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!ok) break;
           ptx::mma_commit(accf_bar(ab));
           ++u;
+          }
         }
         if (ok) red_release_add(p.done + (f % p.ring_slots), 1u);
       }
@@ -964,46 +975,73 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const int chunk_kb = chunk_kblocks(p, f);
       const int nchunks = (p.nkb + chunk_kb - 1) / chunk_kb;
-      for (int ch = 0; ch < nchunks; ++ch) {
-        const uint32_t ab = u & 1u;
-        const uint32_t ap = (u >> 1) & 1u;
-        const bool got = ptx::wait_bounded(accf_bar(ab), ap, wc);
-        if (!__all_sync(0xffffffffu, got)) {
-          ok = false;
-          break;
-        }
-        ptx::tc_fence_after();
+      for (int ch = 0; ok && ch < nchunks; ++ch) {
+        const int kb0 = ch * chunk_kb;
+        const int kb1 = min(p.nkb, kb0 + chunk_kb);
+        const int gstep = kTmemSum ? 1 : (kb1 - kb0);
         const bool add = p.accumulate || ch > 0;
         const bool first = ch == 0, last_chunk = ch == nchunks - 1;
-        if (last < 0) {
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
-        }
-#pragma unroll 1
-        for (int piece = 0; piece <= last; ++piece) {
-          uint32_t vr[32], vi[32];
-          ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + piece * 32, vr);
-          ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + 128 + piece * 32, vi);
-          ptx::tmem_wait_ld();
-          if (piece == last) {
+        for (int g0 = kb0; g0 < kb1; g0 += gstep) {
+          // TMEM running sum: the first group of a chunk starts it, the last
+          // one is stored; groups in between only add into it.
+          const bool gfirst = g0 == kb0, glast = g0 + gstep >= kb1;
+          const uint32_t ab = kTmemSum ? 0u : (u & 1u);
+          const uint32_t ap = kTmemSum ? (u & 1u) : ((u >> 1) & 1u);
+          const bool got = ptx::wait_bounded(accf_bar(ab), ap, wc);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          if (last < 0) {
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
           }
-          const int b0 = bx * kBlk + piece * 32;
-          if constexpr (IS_INT) {
-            store_piece<true>(vr, vi, p, f, a, b0, add);
-          } else {
-            if (p.in_amax) scale_piece<FMT>(vr, vi, p, f, a, b0);
-            if (p.acc64) {
-              store_piece_f64(vr, vi, p, f, a, b0, first, last_chunk);
+#pragma unroll 1
+          for (int piece = 0; piece <= last; ++piece) {
+            uint32_t vr[32], vi[32];
+            ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + piece * 32, vr);
+            ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + 128 + piece * 32, vi);
+            if constexpr (kTmemSum) {
+              if (!gfirst) {
+                uint32_t sr[32], si[32];
+                ptx::tmem_ld_32x32b_x32(t_lanes + 256 + piece * 32, sr);
+                ptx::tmem_ld_32x32b_x32(t_lanes + 384 + piece * 32, si);
+                ptx::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  vr[j] = __float_as_uint(__uint_as_float(vr[j]) + __uint_as_float(sr[j]));
+                  vi[j] = __float_as_uint(__uint_as_float(vi[j]) + __uint_as_float(si[j]));
+                }
+              }
+            }
+            ptx::tmem_wait_ld();
+            if (piece == last) {
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
+            }
+            if (kTmemSum && !glast) {
+              ptx::tmem_st_32x32b_x32(t_lanes + 256 + piece * 32, vr);
+              ptx::tmem_st_32x32b_x32(t_lanes + 384 + piece * 32, vi);
+              continue;
+            }
+            const int b0 = bx * kBlk + piece * 32;
+            if constexpr (IS_INT) {
+              store_piece<true>(vr, vi, p, f, a, b0, add);
             } else {
-              store_piece<false>(vr, vi, p, f, a, b0, add);
+              if (p.in_amax) scale_piece<FMT>(vr, vi, p, f, a, b0);
+              if (p.acc64) {
+                store_piece_f64(vr, vi, p, f, a, b0, first, last_chunk);
+              } else {
+                store_piece<false>(vr, vi, p, f, a, b0, add);
+              }
             }
           }
+          if (kTmemSum && !glast) ptx::tmem_wait_st();
+          ++u;
         }
-        ++u;
       }
     }
   } else {

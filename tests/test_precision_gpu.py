@@ -4,12 +4,12 @@ against the FP64 oracle on the unquantised voltages (gains applied in FP64).
 
 Error metrics (per channel, worst channel reported): Frobenius relative error
 ||dV||_F / ||V||_F and max |dV_ab| / sqrt(V_aa V_bb).  Tolerances: FP16 1e-3
-(both), FP8 3e-2 Frobenius, HI/LO 2e-6 Frobenius with FP64 block sums every
-64 samples.  The hi/lo bound is set by the tensor-core accumulator: with
-exactly representable products, an fp32 TMEM accumulation still loses about
-1e-8 per accumulated sample (relative, growing linearly with the block
-length), so 22-bit operands need short fp32 blocks.  Measured values are
-printed (pytest -s)."""
+(both), FP8 3e-2 Frobenius, HI/LO 2e-6 Frobenius.  The hi/lo bound is set by
+the tensor-core accumulator: with exactly representable products, an fp32
+TMEM accumulation still loses about 1e-8 per accumulated sample (relative,
+growing linearly with the block length), so the hi/lo kernel restarts its
+accumulator every 64 samples and sums the blocks in round-to-nearest fp32.
+Measured values are printed (pytest -s)."""
 import numpy as np
 import pytest
 import torch
@@ -53,8 +53,7 @@ def test_precision_forms_vs_fp64(prec, dtype, dev):
                            dtype=getattr(torch, dtype))
     g = synth.complex_gains(N, P, 71)
     want = oracle.correlate_f64(x.double().numpy(), gains=g)
-    kw = {"fp64_block": HILO_BLOCK} if prec == "hilo" else {}
-    got = run(x.to(dev), N, P, F, T, dtype, gains=g, precision=PRECS[prec], **kw)
+    got = run(x.to(dev), N, P, F, T, dtype, gains=g, precision=PRECS[prec])
     frob, mx = frob_and_maxnorm(got, want, N, P)
     print(f"\n{prec} {dtype}: frobenius {frob:.3e} max-norm {mx:.3e}")
     assert frob <= FROB_TOL[prec], frob
@@ -71,8 +70,7 @@ def test_scales_cover_fp32_range(prec, dev):
     mag = torch.tensor([1e9, 1e-9, 3e4, 1.0, 7e-3, 2e6, 1e-5, 5e2], dtype=torch.float32)
     x = (x * mag[None, None, :, None, None]).contiguous()
     want = oracle.correlate_f64(x.double().numpy())
-    kw = {"fp64_block": HILO_BLOCK} if prec == "hilo" else {}
-    got = run(x.to(dev), N, P, F, T, "float32", precision=PRECS[prec], **kw)
+    got = run(x.to(dev), N, P, F, T, "float32", precision=PRECS[prec])
     frob, mx = frob_and_maxnorm(got, want, N, P)
     print(f"\n{prec} wide range: frobenius {frob:.3e} max-norm {mx:.3e}")
     assert np.isfinite(got).all()
@@ -90,7 +88,7 @@ def test_hilo_beats_fp16(dev):
     ehb, _ = frob_and_maxnorm(run(xd, N, P, F, T, "float32", precision=xc.XC_PREC_HILO,
                                   fp64_block=HILO_BLOCK), want, N, P)
     print(f"\nfp16 {e16:.3e} hilo {ehl:.3e} hilo+fp64/{HILO_BLOCK} {ehb:.3e}")
-    assert ehl < e16 / 4
+    assert ehl < e16 / 30
     assert ehb < e16 / 30
 
 
@@ -164,9 +162,7 @@ def test_precision_workload_sampled(prec, dev):
     x, g = synth.precision_input(w, device=dev)
     x16 = x.to(torch.float16)
     del x
-    kw = {"fp64_block": HILO_BLOCK} if prec == "hilo" else {}
-    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "float16", precision=PRECS[prec],
-                        **kw)
+    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "float16", precision=PRECS[prec])
     try:
         eng.set_gains(torch.from_numpy(g).float().to(dev))
         out = eng.correlate(x16, sync=True)
