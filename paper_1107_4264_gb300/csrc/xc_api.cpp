@@ -151,7 +151,9 @@ struct xc_handle {
 namespace {
 
 xc_status encode_operand_map(CUtensorMap* map, void* base, int64_t R, int64_t Tp, int64_t n);
-xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g);
+xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g,
+                           xc_dtype dtype = XC_CI8);
+bool input_map_possible(xc_dtype dtype, const xc::Geometry& g);
 
 void release(xc_handle* h) {
   if (!h) return;
@@ -251,11 +253,11 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     X.grid = h->num_sms;
     X.timeout_ns = h->timeout_ns;
     X.status = h->d_status;
-    // 8-bit input in 128-row x 64-sample TMA boxes when rows are 16-byte strided.
+    // Input in TMA boxes when its rows are 16-byte strided.
     CUtensorMap in_map;
     const CUtensorMap* im = nullptr;
-    if (h->dtype == XC_CI8 && h->g.R % 16 == 0) {
-      if (encode_input_map(&in_map, in, h->g) != XC_OK) return t_status;
+    if (input_map_possible(h->dtype, h->g)) {
+      if (encode_input_map(&in_map, in, h->g, h->dtype) != XC_OK) return t_status;
       im = &in_map;
     }
     if (tm) tm->nkern = 1;
@@ -321,19 +323,52 @@ xc_status encode_operand_map(CUtensorMap* map, void* base, int64_t R, int64_t Tp
   return XC_OK;
 }
 
-// 8-bit input [T][F][R] as a 3-D tensor {R, F, T}, loaded in boxes of
-// 128 rows x 1 channel x kPlanarUnitT samples (zero fill past R and T).
-xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g) {
+// Input [T][F][n] (complex) as a 3-D tensor {row elements, F, T} for the
+// planar converters' TMA boxes of 8 KiB (zero fill past the row and T):
+//   8-bit: {R = 2n bytes}, boxes of 128 x 1 x kPlanarUnitT;
+//   fp16:  {n} 32-bit complex elements, boxes of 64 x 1 x 32;
+//   fp32:  {2n} fp32 components, boxes of 128 x 1 x 16.
+// A row must be a multiple of 16 bytes (TMA global strides).
+bool input_map_possible(xc_dtype dtype, const xc::Geometry& g) {
+  const int64_t n = static_cast<int64_t>(g.N) * g.P;
+  switch (dtype) {
+    case XC_CI8: return g.R % 16 == 0;
+    case XC_CF16: return n % 4 == 0;
+    case XC_CF32: return n % 2 == 0;
+  }
+  return false;
+}
+
+xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g, xc_dtype dtype) {
   EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
-  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(g.R), static_cast<cuuint64_t>(g.F),
-                              static_cast<cuuint64_t>(g.T)};
-  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(g.R),
-                                 static_cast<cuuint64_t>(g.R) * g.F};
-  const cuuint32_t box[3] = {128, 1, static_cast<cuuint32_t>(xc::kPlanarUnitT)};
+  const cuuint64_t n = static_cast<cuuint64_t>(g.N) * g.P;
+  cuuint64_t row = 0, esize = 1;
+  cuuint32_t box_x = 0, box_t = 0;
+  CUtensorMapDataType type = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  if (dtype == XC_CI8) {
+    row = static_cast<cuuint64_t>(g.R);
+    box_x = 128;
+    box_t = static_cast<cuuint32_t>(xc::kPlanarUnitT);
+  } else if (dtype == XC_CF16) {
+    type = CU_TENSOR_MAP_DATA_TYPE_UINT32;
+    esize = 4;
+    row = n;
+    box_x = 64;
+    box_t = 32;
+  } else {
+    type = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    esize = 4;
+    row = 2 * n;
+    box_x = 128;
+    box_t = 16;
+  }
+  const cuuint64_t dims[3] = {row, static_cast<cuuint64_t>(g.F), static_cast<cuuint64_t>(g.T)};
+  const cuuint64_t strides[2] = {row * esize, row * esize * static_cast<cuuint64_t>(g.F)};
+  const cuuint32_t box[3] = {box_x, 1, box_t};
   const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(in), dims, strides, box,
-                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  CUresult cr = enc(map, type, 3, const_cast<void*>(in), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS)
     return fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled (input) failed (%d)", static_cast<int>(cr));

@@ -607,6 +607,199 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
   if (pend) publish_unit(*pend, pend_slot, lane, pend_n);
 }
 
+// Convert 16 samples of two inputs (v0: input a0, v1: input a1 = a0 + 32;
+// gains and scale already applied) into the tiles of one K-block: fp16 (two
+// 8-sample chunks from chunk8), hi/lo (the same in the H tiles plus the
+// residuals in the L tiles) or e4m3 (one 16-sample chunk).
+template <int FMT>
+__device__ __forceinline__ void store_group16(const Params& p, uint8_t* tre, uint8_t* tim, int row0,
+                                              int chunk8, const float2 (&v0)[16],
+                                              const float2 (&v1)[16], uint64_t pol) {
+  auto st = [&](uint8_t* dst, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    ptx::st_global_v4_hint(dst, a, b, c, d, pol);
+  };
+  if constexpr (FMT == kFmtF8) {
+    const uint32_t off = (chunk8 / 2) * kChunkStride + row0 * 16;
+    uint32_t r0[4], i0[4], r1[4], i1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2* A = v0 + 4 * k;
+      const float2* B = v1 + 4 * k;
+      r0[k] = e4m3x4(A[0].x, A[1].x, A[2].x, A[3].x);
+      i0[k] = e4m3x4(A[0].y, A[1].y, A[2].y, A[3].y);
+      r1[k] = e4m3x4(B[0].x, B[1].x, B[2].x, B[3].x);
+      i1[k] = e4m3x4(B[0].y, B[1].y, B[2].y, B[3].y);
+    }
+    st(tre + off, r0[0], r0[1], r0[2], r0[3]);
+    st(tim + off, i0[0], i0[1], i0[2], i0[3]);
+    st(tre + off + 32 * 16, r1[0], r1[1], r1[2], r1[3]);
+    st(tim + off + 32 * 16, i1[0], i1[1], i1[2], i1[3]);
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t off = (chunk8 + h) * kChunkStride + row0 * 16;
+      uint32_t r0[4], i0[4], r1[4], i1[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 a = v0[8 * h + 2 * k], b = v0[8 * h + 2 * k + 1];
+        const float2 c = v1[8 * h + 2 * k], d = v1[8 * h + 2 * k + 1];
+        r0[k] = h2bits(a.x, b.x);
+        i0[k] = h2bits(a.y, b.y);
+        r1[k] = h2bits(c.x, d.x);
+        i1[k] = h2bits(c.y, d.y);
+      }
+      st(tre + off, r0[0], r0[1], r0[2], r0[3]);
+      st(tim + off, i0[0], i0[1], i0[2], i0[3]);
+      st(tre + off + 32 * 16, r1[0], r1[1], r1[2], r1[3]);
+      st(tim + off + 32 * 16, i1[0], i1[1], i1[2], i1[3]);
+      if constexpr (FMT == kFmtHiLo) {
+        // Residual tile of the same K-block: K-tile nkb + kb.
+        const int64_t lo_off = static_cast<int64_t>(p.nkb) * p.nib << FmtT<FMT>::kTileShift;
+        uint32_t l0[4], m0[4], l1[4], m1[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 a = v0[8 * h + 2 * k], b = v0[8 * h + 2 * k + 1];
+          const float2 c = v1[8 * h + 2 * k], d = v1[8 * h + 2 * k + 1];
+          l0[k] = lo2bits(a.x, b.x, r0[k]);
+          m0[k] = lo2bits(a.y, b.y, i0[k]);
+          l1[k] = lo2bits(c.x, d.x, r1[k]);
+          m1[k] = lo2bits(c.y, d.y, i1[k]);
+        }
+        st(tre + lo_off + off, l0[0], l0[1], l0[2], l0[3]);
+        st(tim + lo_off + off, m0[0], m0[1], m0[2], m0[3]);
+        st(tre + lo_off + off + 32 * 16, l1[0], l1[1], l1[2], l1[3]);
+        st(tim + lo_off + off + 32 * 16, m1[0], m1[1], m1[2], m1[3]);
+      }
+    }
+  }
+}
+
+// Float converter with TMA-staged input: boxes of 64 inputs x kFBox samples
+// (8 KiB: complex fp16, 32 samples, or complex fp32, 16 samples) pass
+// through the warp's one staging buffer, kUnitT / kFBox boxes per unit;
+// while one box is converted the next (of this unit or of the next) is in
+// flight.  Units are taken in runs and published as in converter_tma.
+template <int DT, int FMT, bool MULTI>
+__device__ void converter_tma_float(const Batch& bt, uint32_t buf, uint32_t bar, int cw, int lane,
+                                    volatile int* abort_flag) {
+  constexpr int kCx = DT == 1 ? 4 : 8;  // bytes per complex sample
+  constexpr int kFBox = kConvBufBytes / (64 * kCx);
+  constexpr int kBoxes = kUnitT / kFBox;
+  static_assert(kFBox % 16 == 0 && kUnitT % kFBox == 0, "boxes hold whole 16-sample groups");
+  const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
+  const long long nw = static_cast<long long>(gridDim.x) * kNumConvWarps;
+  const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
+  int sb_issue = 0;
+  auto issue = [&](long long u, int j) {
+    sb_issue = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb_issue);
+    const Unit x = unit_of(bt.sub[sb_issue], u - bt.unit_base[sb_issue]);
+    if (lane == 0) {
+      ptx::mbar_arrive_expect_tx(bar, kConvBufBytes);
+      // Map elements: one complex fp16 (32-bit) or one fp32 component.
+      const int ex = DT == 1 ? x.hb * 64 : x.hb * 128;
+      ptx::tma_load_3d_hint(buf, &bt.maps[sb_issue], bar, ex, x.c, x.ku * kUnitT + j * kFBox,
+                            ptx::l2_policy_evict_first());
+    }
+  };
+  const uint8_t* src = reinterpret_cast<const uint8_t*>(__cvta_shared_to_generic(static_cast<size_t>(buf)));
+  const uint64_t pol_last = ptx::l2_policy_evict_last();
+  uint32_t phase = 0;
+  int sb = 0, claimed = -1, claimed_sb = -1;
+  const Params* pend = nullptr;
+  int pend_slot = 0, pend_c = -1, pend_sb = -1;
+  unsigned pend_n = 0;
+  long long u = first_unit(static_cast<long long>(blockIdx.x) * kNumConvWarps + cw);
+  if (u < total) issue(u, 0);
+  for (; u < total; u = next_unit(u, nw)) {
+    sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
+    const Params& p = bt.sub[sb];
+    const Unit x = unit_of(p, u - bt.unit_base[sb]);
+    if (x.c != claimed || sb != claimed_sb) {
+      if (pend && slot_busy(p, x.c, lane)) {
+        publish_unit(*pend, pend_slot, lane, pend_n);
+        pend = nullptr;
+      }
+      if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
+      claimed = x.c;
+      claimed_sb = sb;
+    }
+    const int ib = x.hb >> 1;
+    uint8_t* tre = ring_tile<FMT>(p, x.slot, 0, x.kb, ib);
+    uint8_t* tim = ring_tile<FMT>(p, x.slot, 1, x.kb, ib);
+    const int a0 = x.hb * 64 + lane, a1 = a0 + 32;
+    const int row0 = (x.hb & 1) * 64 + lane;
+    // y = g x 2^-e.
+    float2 g0 = make_float2(1.f, 0.f), g1 = make_float2(1.f, 0.f);
+    if (p.gains) {
+      g0 = a0 < p.n ? p.gains[a0] : make_float2(0.f, 0.f);
+      g1 = a1 < p.n ? p.gains[a1] : make_float2(0.f, 0.f);
+    }
+    if (p.in_amax) {
+      const unsigned* am = p.in_amax + static_cast<int64_t>(x.c) * p.n;
+      const float s0 = a0 < p.n ? exp2i(-scale_exp<FMT>(am[a0])) : 0.f;
+      const float s1 = a1 < p.n ? exp2i(-scale_exp<FMT>(am[a1])) : 0.f;
+      g0 = make_float2(g0.x * s0, g0.y * s0);  // exact: s is a power of two
+      g1 = make_float2(g1.x * s1, g1.y * s1);
+    }
+#pragma unroll 1
+    for (int j = 0; j < kBoxes; ++j) {
+      const bool got = ptx::wait_bounded(bar, phase, wc);
+      if (!__all_sync(0xffffffffu, got)) return;
+      phase ^= 1u;
+      // Lane l: inputs l and l + 32 of the box's 64, every sample.
+      using Raw = typename std::conditional<DT == 1, uint32_t, float2>::type;
+      const Raw* box = reinterpret_cast<const Raw*>(src);
+      Raw w0[kFBox], w1[kFBox];
+#pragma unroll
+      for (int t = 0; t < kFBox; ++t) {
+        w0[t] = box[t * 64 + lane];
+        w1[t] = box[t * 64 + 32 + lane];
+      }
+      __syncwarp();
+      ptx::fence_proxy_async_smem();
+      if (j + 1 < kBoxes) {
+        issue(u, j + 1);
+      } else {
+        const long long un = next_unit(u, nw);
+        if (un < total) issue(un, 0);
+      }
+      if (j == 0 && pend && (pend_n == kUnitRun || pend_c != x.c || pend_sb != sb)) {
+        publish_unit(*pend, pend_slot, lane, pend_n);
+        pend = nullptr;
+      }
+#pragma unroll
+      for (int g16 = 0; g16 < kFBox / 16; ++g16) {
+        float2 v0[16], v1[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float2 c0, c1;
+          if constexpr (DT == 1) {
+            c0 = __half22float2(*reinterpret_cast<const __half2*>(&w0[16 * g16 + i]));
+            c1 = __half22float2(*reinterpret_cast<const __half2*>(&w1[16 * g16 + i]));
+          } else {
+            c0 = w0[16 * g16 + i];
+            c1 = w1[16 * g16 + i];
+          }
+          v0[i] = make_float2(g0.x * c0.x - g0.y * c0.y, g0.x * c0.y + g0.y * c0.x);
+          v1[i] = make_float2(g1.x * c1.x - g1.y * c1.y, g1.x * c1.y + g1.y * c1.x);
+        }
+        store_group16<FMT>(p, tre, tim, row0, x.cbase + (j * kFBox + 16 * g16) / 8, v0, v1, pol_last);
+      }
+    }
+    if (pend) {
+      ++pend_n;
+    } else {
+      pend = &p;
+      pend_slot = x.slot;
+      pend_c = x.c;
+      pend_sb = sb;
+      pend_n = 1;
+    }
+    if (*abort_flag) return;
+  }
+  if (pend) publish_unit(*pend, pend_slot, lane, pend_n);
+}
+
 // --------------------------------------------------------------- epilogue
 
 // Store one 32-column piece: values v_re[j], v_im[j] of V(a, b0 + j).
@@ -1054,7 +1247,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         converter_direct<DT, FMT, MULTI>(bt, cw, lane, abort_flag);
       }
     } else {
-      converter_direct<DT, FMT, MULTI>(bt, cw, lane, abort_flag);
+      if (bt.sub[0].tma_in) {
+        converter_tma_float<DT, FMT, MULTI>(bt, sbase + kConvOff + cw * kConvBufBytes, conv_bar(cw),
+                                            cw, lane, abort_flag);
+      } else {
+        converter_direct<DT, FMT, MULTI>(bt, cw, lane, abort_flag);
+      }
     }
   }
 
@@ -1181,7 +1379,7 @@ cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps,
   Batch* b = reinterpret_cast<Batch*>(k->args);
   memset(b, 0, sizeof(Batch));
   b->nsub = nsub;
-  bool all_tma = dt == 0;
+  bool all_tma = true;
   for (int i = 0; i < nsub; ++i) {
     if (subs[i].in_dtype != dt || (dt != 0 && subs[i].fmt != fmt)) return cudaErrorInvalidValue;
     if (subs[i].ring_slots < 1 || subs[i].ring_slots > kMaxRingSlots) return cudaErrorInvalidValue;
