@@ -487,8 +487,29 @@ def run_xc(args):
             "h2d_bytes_per_step": host_in.numel(), "d2h_bytes_per_step": host_out.numel() * 4,
             "ms_per_step": ems / args.e2e_steps,
             "h2d_gbs": host_in.numel() * args.e2e_steps / (ems * 1e-3) / 1e9,
+            "mode": "every integration's visibilities copied back (dump)",
         }
-        del host_in, host_out
+        # The paper's own pipeline (Algorithm 1): the integrations of a step
+        # accumulate into one matrix, copied back once.
+        host_acc = torch.empty(w.out_shape, dtype=torch.int32, pin_memory=True)
+        eng.set_option(xc.XC_OPT_ACCUMULATE, 1)
+
+        def alg1_step():
+            eng.correlate_stream(host_in, nint, outs[0], host_out=host_acc, stream=stream)
+
+        alg1_step()
+        eng.synchronize(stream)
+        ams = timed(alg1_step, args.e2e_steps)
+        eng.synchronize(stream)
+        eng.kernel_times(reset=True)
+        eng.set_option(xc.XC_OPT_ACCUMULATE, 0)
+        result["e2e_algorithm1"] = {
+            "value": world * args.e2e_steps * nint * ops_int / (ams * 1e-3) / 1e12, "unit": UNIT,
+            "h2d_bytes_per_step": host_in.numel(), "d2h_bytes_per_step": host_acc.numel() * 4,
+            "ms_per_step": ams / args.e2e_steps,
+            "mode": "ACCUMULATE: 10 integrations summed into one matrix, copied back once per step",
+        }
+        del host_in, host_out, host_acc
 
     if not args.no_forms and world == 1:
         result["workloads"] = measure_forms(args, torch, xc, synth, dev, stream, timed, peaks)

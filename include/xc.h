@@ -222,7 +222,11 @@ xc_status xc_synchronize(xc_handle* h, void* stream);
  *   host_out: optional pinned host memory of the same size as `out`; when
  *             not NULL each integration's output is also copied back on a
  *             second side stream once computed.
- * Stream-ordered on `stream`: returns once all work is queued.
+ * Returns once all work is queued.  The correlations and the copies out are
+ * ordered after work queued earlier on `stream`, and later work on `stream`
+ * after this call's copies out.  The copies in wait only for their staging
+ * buffer (so they overlap an earlier call's last copies out): `host_in` must
+ * already hold its data when the call is made.
  */
 xc_status xc_correlate_stream(xc_handle* h, const void* host_in, int n_integrations, void* out,
                               void* host_out, void* stream);

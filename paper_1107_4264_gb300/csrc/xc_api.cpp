@@ -135,6 +135,7 @@ struct xc_handle {
   cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
   cudaEvent_t ev_ready[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  bool free_recorded[2] = {false, false};  // ev_free[b] marks the last read of stage[b]
   cudaEvent_t ev_start = nullptr, ev_computed = nullptr, ev_d2h = nullptr;
   // Kernel timing (XC_OPT_PROFILE): events bracketing each launch.
   int profile = 0;
@@ -755,14 +756,16 @@ xc_status xc_correlate_stream(xc_handle* h, const void* host_in, int n_integrati
   const char* src = static_cast<const char*>(host_in);
   char* dst = static_cast<char*>(out);
   char* hdst = static_cast<char*>(host_out);
-  // The staging buffers may still be read by work queued earlier on `stream`.
+  // Copies out follow the work queued earlier on `stream`.  Copies in wait
+  // only until their staging buffer has been read (by this call's
+  // correlation of integration i-2, or the last use in an earlier call), so
+  // they overlap an earlier call's final copies out.
   e = cudaEventRecord(h->ev_start, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->ev_start, 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h_stream, h->ev_start, 0);
   for (int i = 0; i < n_integrations && e == cudaSuccess; ++i) {
     const int b = i & 1;
-    // H2D of integration i into buffer b once the correlation of i-2 has read it.
-    if (i >= 2) e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0);
+    // H2D of integration i into buffer b once the buffer's previous correlation has read it.
+    if (i >= 2 || h->free_recorded[b]) e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h->stage[b], src + static_cast<size_t>(i) * h->in_bytes, h->in_bytes,
                           cudaMemcpyHostToDevice, h->copy_stream);
@@ -773,6 +776,7 @@ xc_status xc_correlate_stream(xc_handle* h, const void* host_in, int n_integrati
     xc_status st = launch_one(h, h->stage[b], o, s);
     if (st != XC_OK) return st;
     e = cudaEventRecord(h->ev_free[b], s);
+    h->free_recorded[b] = true;
     if (e == cudaSuccess && hdst && (!h->accumulate || i == n_integrations - 1)) {
       e = cudaEventRecord(h->ev_computed, s);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(h->d2h_stream, h->ev_computed, 0);
