@@ -65,6 +65,9 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision, batched and differentiable workloads")
     ap.add_argument("--form-steps", type=int, default=5)
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the bench line: kernel TOPS over N (fixed work) and over T at "
+                         "fixed F*T (output traffic), one JSON object")
     return ap.parse_args()
 
 
@@ -319,6 +322,57 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks):
     return res
 
 
+def run_sweep(args):
+    """Kernel throughput of the 8-bit tensor-core engine over the station count
+    N (F chosen for ~1.1e12 useful ops per integration, T = 1000; Sec. 6's
+    dependence on N) and over the integration length T at fixed F*T = 1024000
+    with N = 256 (the output is written once per integration, so short
+    integrations are bound by output traffic)."""
+    import torch
+
+    from paper_1107_4264_gb300 import build as engine_build
+    from paper_1107_4264_gb300 import synth, xc
+
+    engine_build.build()
+    xc.load()
+    dev = torch.device("cuda")
+
+    def measure(N, F, T, reps=10):
+        x = synth.sky_voltages(T, F, N, 2, noise_sigma=3.0, nsrc=3, src_amp=1.5, seed=4242 + N + T,
+                               device=dev, quantise_int8=True)
+        eng = xc.Correlator(N, 2, F, T, "int8")
+        out = eng.new_output()
+        for _ in range(2):
+            eng.correlate(x, out=out)
+        eng.synchronize()
+        eng.set_option(xc.XC_OPT_PROFILE, 1)
+        eng.kernel_times(reset=True)
+        for _ in range(reps):
+            eng.correlate(x, out=out)
+        eng.synchronize()
+        (_, kms), (_, nk) = eng.kernel_times(reset=True)
+        eng.close()
+        ms = kms / max(nk, 1)
+        useful = 8 * F * T * 4 * N * (N + 1) // 2
+        nb = (2 * N + 127) // 128
+        executed = 8 * (nb * (nb + 1) // 2) * 128 * 128 * ((T + 63) // 64 * 64) * F
+        in_b, out_b = T * F * N * 4, F * N * (N + 1) // 2 * 4 * 8
+        return {"N": N, "F": F, "T": T, "kernel_ms": ms, "tops": useful / ms / 1e9,
+                "executed_tflops": executed / ms / 1e9, "useful_fraction": useful / executed,
+                "hbm_gbs_algorithmic": (in_b + out_b) / ms / 1e6}
+
+    by_n = []
+    for N in (16, 32, 64, 128, 256, 512, 1024):
+        F = max(1, min(65535, int(round(1.1e12 / (8 * 1000 * 4 * N * (N + 1) / 2)))))
+        by_n.append(measure(N, F, 1000))
+    by_t = []
+    for T in (125, 250, 500, 1000, 2000, 4000, 8000):
+        by_t.append(measure(256, 1024000 // T, T))
+    print(json.dumps({"sweep": "planar_kernel<int8>, GB300, 1 GPU", "by_nstation": by_n,
+                      "by_ntime_fixed_FT": by_t}))
+    return 0
+
+
 def run_xc(args):
     import torch
 
@@ -540,6 +594,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_xc(args)
 
 
