@@ -515,10 +515,10 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
     }
   };
   const uint32_t* src = reinterpret_cast<const uint32_t*>(__cvta_shared_to_generic(static_cast<size_t>(buf)));
-  // Lane l converts inputs l and l + 32: words l/2 and 16 + l/2 of each
-  // sample row, bytes 2 (l & 1) (re) and 2 (l & 1) + 1 (im).
-  const uint32_t jre = 2u * (lane & 1);
-  const int w0 = lane >> 1;
+  // Lane l converts inputs 2l and 2l + 1 of the half block: word l of each
+  // 128-byte sample row holds (re, im) of both.  Per 8-sample chunk and plane
+  // the lane writes tile rows 2l and 2l + 1 (32 contiguous bytes), so a warp
+  // store covers 1 KiB.
   uint32_t phase = 0;
   int sb = 0, claimed = -1, claimed_sb = -1;
   // Converted units not yet published: their subarray, slot, channel, count.
@@ -543,13 +543,10 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
     const bool got = ptx::wait_bounded(bar, phase, wc);
     if (!__all_sync(0xffffffffu, got)) return;
     phase ^= 1u;
-    // Both inputs' 64 samples into registers, then refill the buffer.
-    uint32_t wa[kUnitT], wb[kUnitT];
+    // Both inputs' kUnitT samples into registers, then refill the buffer.
+    uint32_t w[kUnitT];
 #pragma unroll
-    for (int t = 0; t < kUnitT; ++t) {
-      wa[t] = src[t * (kUnitRows / 4) + w0];
-      wb[t] = src[t * (kUnitRows / 4) + 16 + w0];
-    }
+    for (int t = 0; t < kUnitT; ++t) w[t] = src[t * (kUnitRows / 4) + lane];
     __syncwarp();
     ptx::fence_proxy_async_smem();
     const long long un = next_unit(u, nw);
@@ -563,32 +560,35 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
     const int ib = x.hb >> 1;
     uint8_t* tre = ring_tile<kFmtF16>(p, x.slot, 0, x.kb, ib);
     uint8_t* tim = ring_tile<kFmtF16>(p, x.slot, 1, x.kb, ib);
-    const int row = (x.hb & 1) * 64 + lane;
+    const int row = (x.hb & 1) * 64 + 2 * lane;  // tile rows 2l and 2l + 1
     // Ring tiles are read back by every block of the channel: keep them in L2.
     const uint64_t pol_last = ptx::l2_policy_evict_last();
     // max |x| over the unit from the converted (exact) fp16 values; zero-filled
     // rows and samples contribute 0.
-    __half2 mx[4];
+    __half2 mx[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) mx[q] = __float2half2_rn(0.f);
-    auto store4 = [&](uint8_t* dst, const uint32_t* W, uint32_t j, __half2& m) {
-      const uint32_t v0 = pair_i8(W[0], W[1], j), v1 = pair_i8(W[2], W[3], j);
-      const uint32_t v2 = pair_i8(W[4], W[5], j), v3 = pair_i8(W[6], W[7], j);
-      m = __hmax2(m, __hmax2(__habs2(*reinterpret_cast<const __half2*>(&v0)),
-                             __habs2(*reinterpret_cast<const __half2*>(&v1))));
-      m = __hmax2(m, __hmax2(__habs2(*reinterpret_cast<const __half2*>(&v2)),
-                             __habs2(*reinterpret_cast<const __half2*>(&v3))));
-      ptx::st_global_v4_hint(dst, v0, v1, v2, v3, pol_last);
+    for (int q = 0; q < 2; ++q) mx[q] = __float2half2_rn(0.f);
+    // Rows 2l and 2l + 1 of one plane: bytes j and j + 2 of the words.
+    auto store8 = [&](uint8_t* dst, const uint32_t* W, uint32_t j, __half2& m) {
+      uint32_t v[8];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[k] = pair_i8(W[2 * k], W[2 * k + 1], j);
+        v[4 + k] = pair_i8(W[2 * k], W[2 * k + 1], j + 2);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; k += 2)
+        m = __hmax2(m, __hmax2(__habs2(*reinterpret_cast<const __half2*>(&v[k])),
+                               __habs2(*reinterpret_cast<const __half2*>(&v[k + 1]))));
+      ptx::st_global_v8_hint(dst, v, pol_last);
     };
 #pragma unroll
     for (int cc = 0; cc < kUnitT / 8; ++cc) {
       const uint32_t off = (x.cbase + cc) * kChunkStride + row * 16;
-      store4(tre + off, wa + 8 * cc, jre, mx[0]);
-      store4(tim + off, wa + 8 * cc, jre + 1, mx[1]);
-      store4(tre + off + 32 * 16, wb + 8 * cc, jre, mx[2]);
-      store4(tim + off + 32 * 16, wb + 8 * cc, jre + 1, mx[3]);
+      store8(tre + off, w + 8 * cc, 0u, mx[0]);
+      store8(tim + off, w + 8 * cc, 1u, mx[1]);
     }
-    const __half2 mm = __hmax2(__hmax2(mx[0], mx[1]), __hmax2(mx[2], mx[3]));
+    const __half2 mm = __hmax2(mx[0], mx[1]);
     unsigned m = static_cast<unsigned>(fmaxf(__low2float(mm), __high2float(mm)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
