@@ -317,7 +317,7 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks):
     res["differentiable"] = {"workload": w.name, "forward_tops": w.useful_ops / (fms * 1e-3) / 1e12,
                              "forward_ms": fms, "backward_tops": bwd_ops / (bms * 1e-3) / 1e12,
                              "backward_ms": bms, "backward_ops": bwd_ops,
-                             "backward_arithmetic": "fp32 CUDA-core complex GEMM (H_f = G_f + G_f^H) x (g x)"}
+                             "backward_arithmetic": "tcgen05 complex GEMM (H_f diag(g)) x, fp16 hi/lo operands, fp32 accumulation"}
     eng.close()
     return res
 

@@ -151,15 +151,22 @@ __global__ void __launch_bounds__(256) adjoint_gemm_kernel(const float2* __restr
 
 }  // namespace
 
+cudaError_t launch_build_h(const void* grad_out, void* h_ws, const Geometry& g, cudaStream_t s) {
+  const int n = g.N * g.P;
+  if (n == 0 || g.F == 0) return cudaSuccess;
+  dim3 hb(32, 8);
+  dim3 hg((n + 31) / 32, (n + 7) / 8, g.F);
+  if (hg.y > 65535u || hg.z > 65535u) return cudaErrorInvalidConfiguration;
+  build_h_kernel<<<hg, hb, 0, s>>>(static_cast<const float2*>(grad_out), static_cast<float2*>(h_ws), g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint(const void* grad_out, const void* in, const void* gains, void* grad_in,
                            float* grad_g, void* h_ws, const Geometry& g, cudaStream_t s) {
   const int n = g.N * g.P;
   if (n == 0 || g.F == 0) return cudaSuccess;
   float2* H = static_cast<float2*>(h_ws);
-  dim3 hb(32, 8);
-  dim3 hg((n + 31) / 32, (n + 7) / 8, g.F);
-  build_h_kernel<<<hg, hb, 0, s>>>(static_cast<const float2*>(grad_out), H, g);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_build_h(grad_out, h_ws, g, s);
   if (e != cudaSuccess) return e;
   if (grad_g) {
     e = cudaMemsetAsync(grad_g, 0, sizeof(float) * 2 * n, s);

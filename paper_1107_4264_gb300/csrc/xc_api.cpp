@@ -125,6 +125,7 @@ struct xc_handle {
   void* gains = nullptr;     // cf32 [n]
   int gains_set = 0;
   void* adj_ws = nullptr;    // cf32 [F][n][n]: H_f = G_f + G_f^H
+  void* adj_tc_ws = nullptr; // tensor-core adjoint: fp16 hi/lo operand tiles
   float* grad_g = nullptr;   // cf32 [n]
   // Two-pass engine (allocated when selected): fp16 operands [F][R][Tp].
   void* ws = nullptr;
@@ -183,6 +184,7 @@ void release(xc_handle* h) {
   if (h->ws) cudaFree(h->ws);
   if (h->gains) cudaFree(h->gains);
   if (h->adj_ws) cudaFree(h->adj_ws);
+  if (h->adj_tc_ws) cudaFree(h->adj_tc_ws);
   if (h->grad_g) cudaFree(h->grad_g);
   if (h->ring) cudaFree(h->ring);
   if (h->counters) cudaFree(h->counters);
@@ -650,8 +652,22 @@ xc_status xc_correlate_backward(xc_handle* h, const void* grad_out, const void* 
   if (!h->adj_ws) e = cudaMalloc(&h->adj_ws, static_cast<size_t>(h->g.F) * n * n * 8);
   if (e == cudaSuccess && !h->grad_g) e = cudaMalloc(reinterpret_cast<void**>(&h->grad_g), 8 * n);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint workspace");
-  e = xc::launch_adjoint(grad_out, in, h->gains_set ? h->gains : nullptr, grad_in, h->grad_g,
-                         h->adj_ws, h->g, static_cast<cudaStream_t>(stream));
+  const void* gains = h->gains_set ? h->gains : nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->engine == XC_ENGINE_FP32) {
+    // The FP32 engine's adjoint: complex GEMM on the CUDA cores.
+    e = xc::launch_adjoint(grad_out, in, gains, grad_in, h->grad_g, h->adj_ws, h->g, s);
+  } else {
+    if (!h->adj_tc_ws) {
+      e = cudaMalloc(&h->adj_tc_ws, xc::adjoint_tc_workspace_bytes(h->g));
+      if (e != cudaSuccess) {
+        h->adj_tc_ws = nullptr;
+        return cuda_fail(e, "adjoint workspace");
+      }
+    }
+    e = xc::launch_adjoint_tc(grad_out, in, gains, grad_in, h->grad_g, h->adj_ws, h->adj_tc_ws, h->g,
+                              h->timeout_ns, h->d_status, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   return succeed();
 }

@@ -95,6 +95,15 @@ cudaError_t launch_fp32_xengine(const void* in, int in_dtype, void* out, const G
 // grad_g = sum conj(x) H_f (g x) (cf32 [n], may be NULL).
 cudaError_t launch_adjoint(const void* grad_out, const void* in, const void* gains, void* grad_in,
                            float* grad_g, void* h_ws, const Geometry& g, cudaStream_t s);
+// H_f = G_f + G_f^H from grad_out (the first step of both adjoints).
+cudaError_t launch_build_h(const void* grad_out, void* h_ws, const Geometry& g, cudaStream_t s);
+// Tensor-core adjoint: the same result with H'_f = H_f diag(g) and x split
+// into fp16 hi/lo MMA tiles in `tc_ws` (adjoint_tc_workspace_bytes) and a
+// tcgen05 GEMM; bounded waits report through `status`.
+size_t adjoint_tc_workspace_bytes(const Geometry& g);
+cudaError_t launch_adjoint_tc(const void* grad_out, const void* in, const void* gains, void* grad_in,
+                              float* grad_g, void* h_ws, void* tc_ws, const Geometry& g,
+                              unsigned long long timeout_ns, int* status, cudaStream_t s);
 
 // Record `s` and a printf-style message as this thread's last error
 // (xc_last_error / xc_last_error_message); returns s.

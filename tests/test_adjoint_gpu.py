@@ -55,14 +55,15 @@ def test_gains_rejected_for_8bit_input(dev):
         eng.close()
 
 
-@pytest.mark.parametrize("N,P,F,T", [(12, 2, 3, 70), (7, 1, 2, 33), (70, 2, 2, 130)])
-def test_backward_matches_fp64_adjoint(N, P, F, T, dev):
+@pytest.mark.parametrize("engine", [xc.XC_ENGINE_TENSOR, xc.XC_ENGINE_FP32], ids=["tensor", "fp32"])
+@pytest.mark.parametrize("N,P,F,T", [(12, 2, 3, 70), (7, 1, 2, 33), (70, 2, 2, 130), (130, 2, 2, 300)])
+def test_backward_matches_fp64_adjoint(N, P, F, T, engine, dev):
     rng = np.random.default_rng(N * 1000 + T)
     x = rng.standard_normal((T, F, N, P, 2))
     g = synth.complex_gains(N, P, N + T)
     go = rng.standard_normal((F, N * (N + 1) // 2, P * P, 2))
     gx_want, gg_want = oracle.backward_f64(x, go, gains=g)
-    eng = xc.Correlator(N, P, F, T, "float32")
+    eng = xc.Correlator(N, P, F, T, "float32", engine=engine)
     try:
         eng.set_gains(torch.from_numpy(g).float().to(dev))
         gx = eng.correlate_backward(torch.from_numpy(go).float().to(dev),
