@@ -17,7 +17,7 @@
 //
 // Kernels: amax of H' and of x per channel; operand formation into 16 KiB
 // MMA-ready tiles ([8-column chunk][128 rows][8 fp16], the no-swizzle K-major
-// layout); the GEMM, one CTA per 128 x 128 (a, t) tile of a channel, with a
+// layout); the GEMM, a persistent kernel over 128 x 128 (a, t) tiles with a
 // bulk-copy producer warp, an MMA warp and four epilogue warps that re-read
 // x (nothing from the forward is stored).
 #include <cuda.h>
@@ -40,9 +40,9 @@ constexpr int kStages = 3;
 constexpr int kStageBytes = 4 * kTile;
 constexpr int kThreads = 192;  // producer, MMA, 4 epilogue warps
 constexpr int kBarOff = kStages * kStageBytes;
-constexpr int kNumBars = 2 * kStages + 2;
+constexpr int kNumBars = 2 * kStages + 5;
 constexpr int kSmemBytes = kBarOff + kNumBars * 8 + 16 + 1024;
-constexpr uint32_t kTmemCols = 256;  // D_re, D_im
+constexpr uint32_t kTmemCols = 512;  // 2 sets x (D_re, D_im)
 constexpr uint32_t kIdesc = ptx::idesc_f16_f32(kBlk, kBlk);
 constexpr uint32_t kIdescNegB = kIdesc | (1u << 14);
 
@@ -74,34 +74,36 @@ __device__ __forceinline__ size_t tile_off(int f, int plane, int hl, int rb, int
          static_cast<size_t>(kTile);
 }
 
-// amax[f] = max |component| of H'_f = H_f diag(g).
+// amax[f] = max |component| of H'_f = H_f diag(g).  Block: 8 rows a of one
+// channel, threads along b.
 __global__ void adj_amax_h(const float2* __restrict__ H, const float2* __restrict__ gains,
                            unsigned* __restrict__ amax, int n) {
   const int f = blockIdx.y;
-  const float2* Hf = H + static_cast<size_t>(f) * n * n;
-  const size_t total = static_cast<size_t>(n) * n;
   float m = 0.f;
-  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
-       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    float2 v = Hf[i];
-    if (gains) v = cmul(v, gains[i % n]);
-    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  for (int a = blockIdx.x * 8; a < min(n, blockIdx.x * 8 + 8); ++a) {
+    const float2* row = H + (static_cast<size_t>(f) * n + a) * n;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+      float2 v = row[b];
+      if (gains) v = cmul(v, gains[b]);
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(amax + f, __float_as_uint(m));
 }
 
-// amax[F + f] = max |component| of x over channel f.
+// amax[F + f] = max |component| of x over channel f.  Block: 32 samples t of
+// one channel, threads along b.
 __global__ void adj_amax_x(const float2* __restrict__ x, unsigned* __restrict__ amax, Geometry g,
                            int n) {
   const int f = blockIdx.y;
-  const size_t total = static_cast<size_t>(g.T) * n;
   float m = 0.f;
-  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
-       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const size_t t = i / n, b = i - t * n;
-    const float2 v = x[(t * g.F + f) * n + b];
-    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  for (int t = blockIdx.x * 32; t < min(g.T, blockIdx.x * 32 + 32); ++t) {
+    const float2* row = x + (static_cast<size_t>(t) * g.F + f) * n;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+      const float2 v = row[b];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(amax + g.F + f, __float_as_uint(m));
@@ -192,8 +194,11 @@ struct AdjParams {
   int* status;
 };
 
-// grad_y for one (t block, a block, channel) tile; epilogue writes grad_x and
-// adds this tile's part of grad_g.
+// Persistent GEMM: CTA i takes tiles i, i + grid, ... in (channel, t block,
+// a block) order with the a block fastest, so the CTAs working at one time
+// share their x tiles (and a channel's H' tiles) through L2.  The stage ring
+// runs on across tiles and the accumulator is double-buffered in TMEM: the
+// epilogue of one tile overlaps the MMAs of the next.
 __global__ void __launch_bounds__(kThreads, 1) adj_gemm_tc(const AdjParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -202,20 +207,30 @@ __global__ void __launch_bounds__(kThreads, 1) adj_gemm_tc(const AdjParams P) {
   const uint32_t bar0 = sbase + kBarOff;
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
-  const uint32_t accf_bar = bar0 + 8u * (2 * kStages);
-  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 1);
+  auto accf_bar = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
+  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * kStages + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + kBarOff + kNumBars * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const AdjGeom& G = P.G;
-  const int tb = blockIdx.x, ab = blockIdx.y, f = blockIdx.z;
+  const long long ntiles = static_cast<long long>(G.g.F) * G.nt * G.na;
+  auto tile_of = [&](long long it, int* f, int* tb, int* ab) {
+    *ab = static_cast<int>(it % G.na);
+    const long long r = it / G.na;
+    *tb = static_cast<int>(r % G.nt);
+    *f = static_cast<int>(r / G.nt);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       ptx::mbar_init(full_bar(s), 1);
       ptx::mbar_init(empty_bar(s), 1);
     }
-    ptx::mbar_init(accf_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(accf_bar(b), 1);
+      ptx::mbar_init(acce_bar(b), 4);
+    }
     ptx::mbar_init(drain_bar, 1);
     *abort_flag = 0;
     ptx::fence_mbar_init();
@@ -237,23 +252,28 @@ __global__ void __launch_bounds__(kThreads, 1) adj_gemm_tc(const AdjParams P) {
       int issued_phase[kStages];
       for (int s = 0; s < kStages; ++s) issued_phase[s] = -1;
       bool ok = true;
-      for (int st = 0; st < steps; ++st) {
-        const int stage = st % kStages;
-        const uint32_t phase = (st / kStages) & 1u;
-        if (!ptx::wait_bounded(empty_bar(stage), phase ^ 1u, wc)) {
-          ok = false;
-          break;
+      long long gst = 0;  // stage-ring position across tiles
+      for (long long it = blockIdx.x; ok && it < ntiles; it += gridDim.x) {
+        int f, tb, ab;
+        tile_of(it, &f, &tb, &ab);
+        for (int st = 0; st < steps; ++st, ++gst) {
+          const int stage = static_cast<int>(gst % kStages);
+          const uint32_t phase = static_cast<uint32_t>(gst / kStages) & 1u;
+          if (!ptx::wait_bounded(empty_bar(stage), phase ^ 1u, wc)) {
+            ok = false;
+            break;
+          }
+          const int kb = st / 3, j = st % 3;
+          const int hla = j == 1 ? 1 : 0, hlb = j == 2 ? 1 : 0;
+          const uint32_t dst = sbase + stage * kStageBytes;
+          const uint32_t fb = full_bar(stage);
+          ptx::mbar_arrive_expect_tx(fb, kStageBytes);
+          ptx::bulk_load(dst, P.At + tile_off(f, 0, hla, ab, kb, G.na, G.nk), kTile, fb);
+          ptx::bulk_load(dst + kTile, P.At + tile_off(f, 1, hla, ab, kb, G.na, G.nk), kTile, fb);
+          ptx::bulk_load(dst + 2 * kTile, P.Bt + tile_off(f, 0, hlb, tb, kb, G.nt, G.nk), kTile, fb);
+          ptx::bulk_load(dst + 3 * kTile, P.Bt + tile_off(f, 1, hlb, tb, kb, G.nt, G.nk), kTile, fb);
+          issued_phase[stage] = static_cast<int>(phase);
         }
-        const int kb = st / 3, j = st % 3;
-        const int hla = j == 1 ? 1 : 0, hlb = j == 2 ? 1 : 0;
-        const uint32_t dst = sbase + stage * kStageBytes;
-        const uint32_t fb = full_bar(stage);
-        ptx::mbar_arrive_expect_tx(fb, kStageBytes);
-        ptx::bulk_load(dst, P.At + tile_off(f, 0, hla, ab, kb, G.na, G.nk), kTile, fb);
-        ptx::bulk_load(dst + kTile, P.At + tile_off(f, 1, hla, ab, kb, G.na, G.nk), kTile, fb);
-        ptx::bulk_load(dst + 2 * kTile, P.Bt + tile_off(f, 0, hlb, tb, kb, G.nt, G.nk), kTile, fb);
-        ptx::bulk_load(dst + 3 * kTile, P.Bt + tile_off(f, 1, hlb, tb, kb, G.nt, G.nk), kTile, fb);
-        issued_phase[stage] = static_cast<int>(phase);
       }
       if (!ok) {
         for (int s = 0; s < kStages; ++s) {
@@ -268,36 +288,46 @@ __global__ void __launch_bounds__(kThreads, 1) adj_gemm_tc(const AdjParams P) {
   } else if (warp == 1) {
     if (lane == 0) {
       bool ok = true, issued_any = false;
-      const uint32_t d_re = tmem, d_im = tmem + 128;
-      for (int st = 0; st < steps; ++st) {
-        const int stage = st % kStages;
-        const uint32_t phase = (st / kStages) & 1u;
-        if (!ptx::wait_bounded(full_bar(stage), phase, wc)) {
+      long long gst = 0;
+      uint32_t u = 0;  // tiles done by this CTA
+      for (long long it = blockIdx.x; ok && it < ntiles; it += gridDim.x, ++u) {
+        const uint32_t ab = u & 1u, ap = (u >> 1) & 1u;
+        if (!ptx::wait_bounded(acce_bar(ab), ap ^ 1u, wc)) {
           ok = false;
           break;
         }
         ptx::tc_fence_after();
-        const uint32_t ar = sbase + stage * kStageBytes, ai = ar + kTile;
-        const uint32_t br = ar + 2 * kTile, bi = ar + 3 * kTile;
+        const uint32_t d_re = tmem + ab * 256, d_im = d_re + 128;
+        for (int st = 0; st < steps; ++st, ++gst) {
+          const int stage = static_cast<int>(gst % kStages);
+          const uint32_t phase = static_cast<uint32_t>(gst / kStages) & 1u;
+          if (!ptx::wait_bounded(full_bar(stage), phase, wc)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t ar = sbase + stage * kStageBytes, ai = ar + kTile;
+          const uint32_t br = ar + 2 * kTile, bi = ar + 3 * kTile;
 #pragma unroll
-        for (int k = 0; k < kBK / 16; ++k) {
-          const uint32_t acc = (st > 0 || k > 0) ? 1u : 0u;
-          const uint32_t ko = k * 2 * kChunkStride;
-          const uint64_t dar = ptx::interleave_kmajor_desc(ar + ko, kChunkStride, kGroupStride);
-          const uint64_t dai = ptx::interleave_kmajor_desc(ai + ko, kChunkStride, kGroupStride);
-          const uint64_t dbr = ptx::interleave_kmajor_desc(br + ko, kChunkStride, kGroupStride);
-          const uint64_t dbi = ptx::interleave_kmajor_desc(bi + ko, kChunkStride, kGroupStride);
-          ptx::mma_f16_ss(d_re, dar, dbr, kIdesc, acc);      // Re += Hr Xr^T
-          ptx::mma_f16_ss(d_re, dai, dbi, kIdescNegB, 1u);   // Re -= Hi Xi^T
-          ptx::mma_f16_ss(d_im, dar, dbi, kIdesc, acc);      // Im += Hr Xi^T
-          ptx::mma_f16_ss(d_im, dai, dbr, kIdesc, 1u);       // Im += Hi Xr^T
+          for (int k = 0; k < kBK / 16; ++k) {
+            const uint32_t acc = (st > 0 || k > 0) ? 1u : 0u;
+            const uint32_t ko = k * 2 * kChunkStride;
+            const uint64_t dar = ptx::interleave_kmajor_desc(ar + ko, kChunkStride, kGroupStride);
+            const uint64_t dai = ptx::interleave_kmajor_desc(ai + ko, kChunkStride, kGroupStride);
+            const uint64_t dbr = ptx::interleave_kmajor_desc(br + ko, kChunkStride, kGroupStride);
+            const uint64_t dbi = ptx::interleave_kmajor_desc(bi + ko, kChunkStride, kGroupStride);
+            ptx::mma_f16_ss(d_re, dar, dbr, kIdesc, acc);      // Re += Hr Xr^T
+            ptx::mma_f16_ss(d_re, dai, dbi, kIdescNegB, 1u);   // Re -= Hi Xi^T
+            ptx::mma_f16_ss(d_im, dar, dbi, kIdesc, acc);      // Im += Hr Xi^T
+            ptx::mma_f16_ss(d_im, dai, dbr, kIdesc, 1u);       // Im += Hi Xr^T
+          }
+          issued_any = true;
+          ptx::mma_commit(empty_bar(stage));
         }
-        issued_any = true;
-        ptx::mma_commit(empty_bar(stage));
+        if (!ok) break;
+        ptx::mma_commit(accf_bar(ab));
       }
-      if (ok) {
-        ptx::mma_commit(accf_bar);
-      } else if (issued_any) {
+      if (!ok && issued_any) {
         ptx::mma_commit(drain_bar);
         const uint64_t t0 = ptx::globaltimer();
         while (!ptx::mbar_try_wait(drain_bar, 0) && ptx::globaltimer() - t0 < P.timeout_ns) {
@@ -307,11 +337,16 @@ __global__ void __launch_bounds__(kThreads, 1) adj_gemm_tc(const AdjParams P) {
   } else {
     // Epilogue: warp q owns TMEM lanes 32q..32q+31 = rows a of the tile.
     const int q = warp & 3;
-    const int a = ab * kBlk + q * 32 + lane;
     const uint32_t t_lanes = tmem + (static_cast<uint32_t>(q * 32) << 16);
-    const bool got = ptx::wait_bounded(accf_bar, 0, wc);
-    if (__all_sync(0xffffffffu, got)) {
+    uint32_t u = 0;
+    for (long long it = blockIdx.x; it < ntiles; it += gridDim.x, ++u) {
+      int f, tb, abk;
+      tile_of(it, &f, &tb, &abk);
+      const uint32_t ab = u & 1u, ap = (u >> 1) & 1u;
+      const bool got = ptx::wait_bounded(accf_bar(ab), ap, wc);
+      if (!__all_sync(0xffffffffu, got)) break;
       ptx::tc_fence_after();
+      const int a = abk * kBlk + q * 32 + lane;
       const float sc = adj_exp2i(adj_scale_exp(P.amax[f]) + adj_scale_exp(P.amax[G.g.F + f]));
       const bool row_ok = a < G.n;
       const float2 ga = (P.gains && row_ok) ? P.gains[a] : make_float2(1.f, 0.f);
@@ -320,20 +355,31 @@ __global__ void __launch_bounds__(kThreads, 1) adj_gemm_tc(const AdjParams P) {
 #pragma unroll 1
       for (int piece = 0; piece < kBlk / 32; ++piece) {
         uint32_t vr[32], vi[32];
-        ptx::tmem_ld_32x32b_x32(t_lanes + piece * 32, vr);
-        ptx::tmem_ld_32x32b_x32(t_lanes + 128 + piece * 32, vi);
+        ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + piece * 32, vr);
+        ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + 128 + piece * 32, vi);
         ptx::tmem_wait_ld();
+        if (piece == kBlk / 32 - 1) {
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
+        }
         if (!row_ok) continue;
+        // All 32 samples of x first (the compiler may not move these loads
+        // above the grad_x stores), then grad_x and the grad_g terms.
+        const int t0 = tb * kBlk + piece * 32;
+        const size_t step = static_cast<size_t>(G.g.F) * G.n;
+        const size_t idx0 = (static_cast<size_t>(t0) * G.g.F + f) * G.n + a;
+        float2 xv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          xv[j] = t0 + j < G.g.T ? __ldcs(P.x + idx0 + j * step) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int t = tb * kBlk + piece * 32 + j;
-          if (t >= G.g.T) continue;
+          if (t0 + j >= G.g.T) continue;
           const float2 gy = make_float2(__uint_as_float(vr[j]) * sc, __uint_as_float(vi[j]) * sc);
-          const size_t idx = (static_cast<size_t>(t) * G.g.F + f) * G.n + a;
-          P.grad_x[idx] = cmul(cga, gy);
-          const float2 xv = P.x[idx];
-          gg.x += xv.x * gy.x + xv.y * gy.y;  // conj(x) gy
-          gg.y += xv.x * gy.y - xv.y * gy.x;
+          __stcs(P.grad_x + idx0 + j * step, cmul(cga, gy));
+          gg.x += xv[j].x * gy.x + xv[j].y * gy.y;  // conj(x) gy
+          gg.y += xv[j].x * gy.y - xv[j].y * gy.x;
         }
       }
       if (row_ok && P.grad_g) {
@@ -373,7 +419,6 @@ cudaError_t launch_adjoint_tc(const void* grad_out, const void* in, const void* 
                               unsigned long long timeout_ns, int* status, cudaStream_t s) {
   const AdjGeom G = adj_geom(g);
   if (G.n == 0 || g.F == 0 || g.T == 0) return cudaSuccess;
-  if (G.nt > 65535 || G.na > 65535 || g.F > 65535) return cudaErrorInvalidConfiguration;
   cudaError_t e = launch_build_h(grad_out, h_ws, g, s);
   if (e != cudaSuccess) return e;
   uint8_t* At = static_cast<uint8_t*>(tc_ws);
@@ -386,8 +431,8 @@ cudaError_t launch_adjoint_tc(const void* grad_out, const void* in, const void* 
   e = cudaMemsetAsync(amax, 0, sizeof(unsigned) * 2 * g.F, s);
   if (e == cudaSuccess && grad_g) e = cudaMemsetAsync(grad_g, 0, sizeof(float) * 2 * G.n, s);
   if (e != cudaSuccess) return e;
-  adj_amax_h<<<dim3(64, g.F), 256, 0, s>>>(H, gn, amax, G.n);
-  adj_amax_x<<<dim3(128, g.F), 256, 0, s>>>(x, amax, g, G.n);
+  adj_amax_h<<<dim3((G.n + 7) / 8, g.F), 256, 0, s>>>(H, gn, amax, G.n);
+  adj_amax_x<<<dim3((g.T + 31) / 32, g.F), 256, 0, s>>>(x, amax, g, G.n);
   const int rows_a = G.na * kBlk * G.nk * (kBK / 8);
   adj_form_h<<<dim3((rows_a + 255) / 256, g.F), 256, 0, s>>>(H, gn, amax, At, G);
   const int64_t rows_t = static_cast<int64_t>(G.nt) * kBlk * G.nk * (kBK / 8);
@@ -408,7 +453,12 @@ cudaError_t launch_adjoint_tc(const void* grad_out, const void* in, const void* 
   P.grad_g = grad_g;
   P.timeout_ns = timeout_ns;
   P.status = status;
-  adj_gemm_tc<<<dim3(G.nt, G.na, g.F), kThreads, kSmemBytes, s>>>(P);
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = static_cast<long long>(g.F) * G.nt * G.na;
+  adj_gemm_tc<<<static_cast<unsigned>(std::min<long long>(ntiles, sms)), kThreads, kSmemBytes, s>>>(P);
   return cudaGetLastError();
 }
 
