@@ -62,6 +62,22 @@ def test_precision_forms_vs_fp64(prec, dtype, dev):
 
 
 @pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("dtype", ["float32", "float16"])
+def test_precision_forms_direct_load_converter(prec, dtype, dev):
+    """n = 37 (P = 1): rows are not 16-byte strided, so the converter loads
+    the input directly instead of through TMA boxes."""
+    T, F, N, P = 300, 2, 37, 1
+    x = synth.sky_voltages(T, F, N, P, noise_sigma=0.7, nsrc=2, src_amp=1.0, seed=72,
+                           dtype=getattr(torch, dtype))
+    g = synth.complex_gains(N, P, 72)
+    want = oracle.correlate_f64(x.double().numpy(), gains=g)
+    got = run(x.to(dev), N, P, F, T, dtype, gains=g, precision=PRECS[prec])
+    frob, mx = frob_and_maxnorm(got, want, N, P)
+    print(f"\n{prec} {dtype} direct: frobenius {frob:.3e} max-norm {mx:.3e}")
+    assert frob <= FROB_TOL[prec], frob
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
 def test_scales_cover_fp32_range(prec, dev):
     """Inputs far outside the fp16 / e4m3 range (and far below it) keep the
     same relative error: the power-of-two scales follow each input."""
