@@ -256,7 +256,8 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks):
     prec = {}
     for name, form, blk, steps, peak_ratio in (("fp16", xc.XC_PREC_FP16, 0, 1, 1.0),
                                                ("hilo", xc.XC_PREC_HILO, 0, 3, 1.0),
-                                               ("fp8_e4m3", xc.XC_PREC_FP8, 0, 1, 2.0)):
+                                               ("fp8_e4m3", xc.XC_PREC_FP8, 0, 1, 2.0),
+                                               ("fp16_fp64_blocks_1024", xc.XC_PREC_FP16, 1024, 1, 1.0)):
         eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "float16", precision=form,
                             fp64_block=blk)
         eng.set_gains(gains)
@@ -271,11 +272,15 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks):
         ex = executed_planar(w, steps)
         peak = peaks["bf16_tflops"] * peak_ratio
         prec[name] = {"tops": w.useful_ops / (ms * 1e-3) / 1e12, "ms": ms,
+                      "fp64_block": blk,
                       "kernel_ms_incl_scale_pass": kms,
                       "executed_tflops": ex / (kms * 1e-3) / 1e12,
                       "frac_of_peak": ex / (kms * 1e-3) / 1e12 / peak,
                       "peak": "%s x %.0f (bf16 burst x nominal %s/bf16 ratio)"
                               % (peaks["bf16_tflops"], peak_ratio, name.split("_")[0])}
+        if blk:
+            prec[name]["note"] = ("fp32 blocks of %d samples summed in float64 in device memory "
+                                  "(long-integration mode; 2 drains per 2048-sample integration)" % blk)
         eng.close()
     del x16
     res["precision"] = {"workload": w.name, "useful_ops": w.useful_ops, "forms": prec,
