@@ -157,7 +157,14 @@ enum {
   XC_OPT_TIMEOUT_MS = 3, /* bound on any in-kernel wait, milliseconds (default 2000) */
   XC_OPT_PROFILE = 4,    /* 1: time every kernel with CUDA events (see xc_kernel_times) */
   XC_OPT_PRECISION = 5,  /* float input, XC_ENGINE_TENSOR: XC_PREC_* (default FP16) */
-  XC_OPT_FP64_BLOCK = 6  /* float input, XC_ENGINE_TENSOR: T_blk > 0 enables FP64 block sums */
+  XC_OPT_FP64_BLOCK = 6, /* float input, XC_ENGINE_TENSOR: T_blk > 0 enables FP64 block sums */
+  /* Test hook for the failure-detection path (XC_ENGINE_TENSOR): 1 makes the
+   * operand converters skip publishing converted units, so every wait of the
+   * kernel's consumers runs out after XC_OPT_TIMEOUT_MS; the kernel then
+   * finishes its in-flight copies and MMAs, frees its tensor memory and
+   * returns, and xc_synchronize reports XC_ERR_TIMEOUT.  Never set it outside
+   * tests: the output is not computed. */
+  XC_OPT_TEST_NO_PUBLISH = 100
 };
 /* Operand precision of float input on XC_ENGINE_TENSOR (Sec. 5 leaves the
  * precision of float voltages open; 8-bit input is always exact).  Every

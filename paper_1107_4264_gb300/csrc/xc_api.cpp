@@ -119,6 +119,7 @@ struct xc_handle {
   // buffer [F][n] and the FP64 block sums (allocated on use).
   int precision = XC_PREC_FP16;
   int fp64_block = 0;
+  int test_no_publish = 0;
   unsigned* in_amax = nullptr;
   double* acc64 = nullptr;
   // Complex gains (float input) and the adjoint's buffers, allocated on use.
@@ -253,6 +254,7 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     X.in_amax = h->in_amax;
     X.acc64 = h->fp64_block ? h->acc64 : nullptr;
     X.f64_block = h->fp64_block;
+    X.test_no_publish = h->test_no_publish;
     X.grid = h->num_sms;
     X.timeout_ns = h->timeout_ns;
     X.status = h->d_status;
@@ -608,6 +610,10 @@ xc_status xc_set_option(xc_handle* h, int key, long long value) {
       h->planar_slots = slots;
       return succeed();
     }
+    case XC_OPT_TEST_NO_PUBLISH:
+      if (value != 0 && value != 1) return fail(XC_ERR_INVALID_ARG, "TEST_NO_PUBLISH must be 0 or 1");
+      h->test_no_publish = static_cast<int>(value);
+      return succeed();
     case XC_OPT_FP64_BLOCK: {
       if (value < 0 || value % 64 != 0 || value > (1LL << 30))
         return fail(XC_ERR_INVALID_ARG, "FP64_BLOCK must be 0 or a positive multiple of 64");

@@ -46,6 +46,7 @@ struct XeLaunch {
   unsigned* in_amax = nullptr;  // [F][N*P] scale pre-pass buffer (NULL: unscaled)
   double* acc64 = nullptr;  // FP64 block sums in the output layout (NULL: off)
   int f64_block = 0;        // samples per fp32 block when acc64 is set (multiple of 64)
+  int test_no_publish = 0;  // test hook (XC_OPT_TEST_NO_PUBLISH)
   int grid;
   unsigned long long timeout_ns;
   int* status;

@@ -138,6 +138,7 @@ struct Params {
   int tma_in;          // 8-bit input staged by TMA (else direct loads)
   unsigned long long timeout_ns;
   int* status;
+  int test_no_publish;  // test hook: converted units are never published
 };
 
 // One launch over up to kMaxSub subarrays (Sec. 4.2's channel-major raster
@@ -319,6 +320,10 @@ __device__ __forceinline__ bool slot_busy(const Params& p, int c, int lane) {
 // Publish one converted unit: every writing lane orders its generic stores
 // before later async-proxy (bulk copy) reads, then one release.
 __device__ __forceinline__ void publish_unit(const Params& p, int slot, int lane, unsigned n = 1) {
+  if (p.test_no_publish) {  // failure-detection test: every consumer wait runs out
+    __syncwarp();
+    return;
+  }
   fence_proxy_async_global();
   __syncwarp();
   if (lane == 0) red_release_add(p.ready + slot, n);
@@ -486,6 +491,19 @@ __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int
   }
 }
 
+// Bounded wait for the warp's TMA box still in flight (completing phase
+// `phase` of `bar`): a converter that gives up never leaves a copy landing in
+// shared memory after it has returned.
+__device__ __forceinline__ void drain_tma(uint32_t bar, uint32_t phase, bool pending,
+                                          unsigned long long timeout_ns) {
+  if (pending) {
+    const uint64_t t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(bar, phase) && ptx::globaltimer() - t0 < timeout_ns) {
+    }
+  }
+  __syncwarp();
+}
+
 // 8-bit converter with TMA-staged input.  Each converter warp is an
 // independent worker on its own stream of units (u = global warp id + k *
 // warps, channel-major), with an 8 KiB staging buffer ([64 samples][128
@@ -503,7 +521,9 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
   const long long nw = static_cast<long long>(gridDim.x) * kNumConvWarps;
   const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
   int sb_issue = 0;
+  bool tma_pending = false;  // a box issued and not yet waited for
   auto issue = [&](long long u) {
+    tma_pending = true;
     sb_issue = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb_issue);
     const Unit x = unit_of(bt.sub[sb_issue], u - bt.unit_base[sb_issue]);
     if (lane == 0) {
@@ -536,12 +556,19 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
         publish_unit(*pend, pend_slot, lane, pend_n);
         pend = nullptr;
       }
-      if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
+      if (!claim_slot_warp(p, x.c, lane, abort_flag)) {
+        drain_tma(bar, phase, tma_pending, wc.timeout_ns);
+        return;
+      }
       claimed = x.c;
       claimed_sb = sb;
     }
     const bool got = ptx::wait_bounded(bar, phase, wc);
-    if (!__all_sync(0xffffffffu, got)) return;
+    if (!__all_sync(0xffffffffu, got)) {
+      drain_tma(bar, phase, tma_pending, wc.timeout_ns);
+      return;
+    }
+    tma_pending = false;
     phase ^= 1u;
     // Both inputs' kUnitT samples into registers, then refill the buffer.
     uint32_t w[kUnitT];
@@ -602,7 +629,10 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
       pend_sb = sb;
       pend_n = 1;
     }
-    if (*abort_flag) return;
+    if (*abort_flag) {
+      drain_tma(bar, phase, tma_pending, wc.timeout_ns);
+      return;
+    }
   }
   if (pend) publish_unit(*pend, pend_slot, lane, pend_n);
 }
@@ -690,7 +720,9 @@ __device__ void converter_tma_float(const Batch& bt, uint32_t buf, uint32_t bar,
   const long long nw = static_cast<long long>(gridDim.x) * kNumConvWarps;
   const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
   int sb_issue = 0;
+  bool tma_pending = false;  // a box issued and not yet waited for
   auto issue = [&](long long u, int j) {
+    tma_pending = true;
     sb_issue = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb_issue);
     const Unit x = unit_of(bt.sub[sb_issue], u - bt.unit_base[sb_issue]);
     if (lane == 0) {
@@ -719,7 +751,10 @@ __device__ void converter_tma_float(const Batch& bt, uint32_t buf, uint32_t bar,
         publish_unit(*pend, pend_slot, lane, pend_n);
         pend = nullptr;
       }
-      if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
+      if (!claim_slot_warp(p, x.c, lane, abort_flag)) {
+        drain_tma(bar, phase, tma_pending, wc.timeout_ns);
+        return;
+      }
       claimed = x.c;
       claimed_sb = sb;
     }
@@ -744,7 +779,11 @@ __device__ void converter_tma_float(const Batch& bt, uint32_t buf, uint32_t bar,
 #pragma unroll 1
     for (int j = 0; j < kBoxes; ++j) {
       const bool got = ptx::wait_bounded(bar, phase, wc);
-      if (!__all_sync(0xffffffffu, got)) return;
+      if (!__all_sync(0xffffffffu, got)) {
+        drain_tma(bar, phase, tma_pending, wc.timeout_ns);
+        return;
+      }
+      tma_pending = false;
       phase ^= 1u;
       // Lane l: inputs l and l + 32 of the box's 64, every sample.
       using Raw = typename std::conditional<DT == 1, uint32_t, float2>::type;
@@ -795,7 +834,10 @@ __device__ void converter_tma_float(const Batch& bt, uint32_t buf, uint32_t bar,
       pend_sb = sb;
       pend_n = 1;
     }
-    if (*abort_flag) return;
+    if (*abort_flag) {
+      drain_tma(bar, phase, tma_pending, wc.timeout_ns);
+      return;
+    }
   }
   if (pend) publish_unit(*pend, pend_slot, lane, pend_n);
 }
@@ -1348,6 +1390,7 @@ Params sub_params(const XeLaunch& L) {
   p.tma_in = 0;
   p.timeout_ns = L.timeout_ns;
   p.status = L.status;
+  p.test_no_publish = L.test_no_publish;
   return p;
 }
 

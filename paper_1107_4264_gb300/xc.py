@@ -27,6 +27,7 @@ XC_ERR_OOM = 7
 XC_ERR_NO_DEVICE = 8
 XC_OPT_ENGINE, XC_OPT_ACCUMULATE, XC_OPT_TIMEOUT_MS, XC_OPT_PROFILE = 1, 2, 3, 4
 XC_OPT_PRECISION, XC_OPT_FP64_BLOCK = 5, 6
+XC_OPT_TEST_NO_PUBLISH = 100
 XC_PREC_FP16, XC_PREC_HILO, XC_PREC_FP8 = 0, 1, 2
 (XC_ENGINE_TENSOR, XC_ENGINE_FP32, XC_ENGINE_TENSOR_2PASS, XC_ENGINE_TENSOR_1CTA,
  XC_ENGINE_TENSOR_PAIR) = 0, 1, 2, 3, 4
