@@ -106,6 +106,32 @@ def traffic_for(kernel: str):
     return e.get("bytes_per_launch")
 
 
+# ------------------------------------------------------------- multi-rank
+# One process per GPU (torchrun): every rank correlates its own integrations
+# (channels and integrations are independent; no data-path collective), the
+# timed region is bracketed by barriers and the slowest rank's time counts.
+
+
+def rank_integrations(rank: int, per_rank: int):
+    """Integration indices (generator seeds) of one rank: disjoint across ranks."""
+    return [rank * per_rank + i for i in range(per_rank)]
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (identity without a process group)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_tops(world: int, steps: int, per_rank: int, ops_per_unit: float, ms: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return world * steps * per_rank * ops_per_unit / (ms * 1e-3) / 1e12
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -408,8 +434,8 @@ def run_xc(args):
 
     # Inputs resident in HBM: this rank's 10 integrations (1.05 GB each).
     xs = torch.empty((nint,) + w.shape, dtype=torch.int8, device=dev)
-    for i in range(nint):
-        synth.large_n_input(w, integration=rank * nint + i, device=dev, out=xs[i])
+    for i, seed_index in enumerate(rank_integrations(rank, nint)):
+        synth.large_n_input(w, integration=seed_index, device=dev, out=xs[i])
     outs = torch.empty((nint,) + w.out_shape, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -433,12 +459,7 @@ def run_xc(args):
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), dist, dev)
 
     for _ in range(args.warmup):
         step()
@@ -453,8 +474,7 @@ def run_xc(args):
     (form_ms, main_ms), (n_form, n_main) = eng.kernel_times(reset=True)
 
     ops_int = w.useful_ops  # per integration
-    total_units = world * args.steps * nint
-    value = total_units * ops_int / (ms * 1e-3) / 1e12
+    value = aggregate_tops(world, args.steps, nint, ops_int, ms)
     ms_step = ms / args.steps
 
     # Roofline of the dominant kernel (the tensor-core X-engine), live events.
