@@ -1142,15 +1142,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t ai = ar + TB;
             const uint32_t br = same ? ar : ar + 2 * TB;
             const uint32_t bi = same ? ai : ar + 3 * TB;
+            // Descriptors of the stage's four tiles; K-step k adds its byte offset
+            // (16-byte units) to the address field, which cannot carry: every
+            // shared-memory address is below 256 KiB.
+            const uint64_t dar0 = ptx::interleave_kmajor_desc(ar, kChunkStride, kGroupStride);
+            const uint64_t dai0 = ptx::interleave_kmajor_desc(ai, kChunkStride, kGroupStride);
+            const uint64_t dbr0 = ptx::interleave_kmajor_desc(br, kChunkStride, kGroupStride);
+            const uint64_t dbi0 = ptx::interleave_kmajor_desc(bi, kChunkStride, kGroupStride);
 #pragma unroll
             for (int k = 0; k < FmtT<FMT>::kChunks / 2; ++k) {
               const uint32_t acc = (st > g0 * FmtT<FMT>::kSteps || k > 0) ? 1u : 0u;
               // K-step k covers 16-byte chunks 2k and 2k + 1 (16 fp16 or 32 e4m3 samples).
-              const uint32_t ko = k * 2 * kChunkStride;
-              const uint64_t dar = ptx::interleave_kmajor_desc(ar + ko, kChunkStride, kGroupStride);
-              const uint64_t dai = ptx::interleave_kmajor_desc(ai + ko, kChunkStride, kGroupStride);
-              const uint64_t dbr = ptx::interleave_kmajor_desc(br + ko, kChunkStride, kGroupStride);
-              const uint64_t dbi = ptx::interleave_kmajor_desc(bi + ko, kChunkStride, kGroupStride);
+              const uint64_t kd = static_cast<uint64_t>(k * 2 * kChunkStride) >> 4;
+              const uint64_t dar = dar0 + kd, dai = dai0 + kd, dbr = dbr0 + kd, dbi = dbi0 + kd;
               if constexpr (FMT == kFmtF8) {
                 ptx::mma_f8_ss(d_re, dar, dbr, idesc, acc);       // Re += Ar Br^T
                 ptx::mma_f8_ss(d_re, dai, dbi, idesc, 1u);        // Re += Ai Bi^T
