@@ -312,6 +312,31 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks):
     res["precision"] = {"workload": w.name, "useful_ops": w.useful_ops, "forms": prec,
                         "errors": "Frobenius vs the FP64 oracle, sampled channels: tests/test_precision_gpu.py"}
 
+    # Large-N workload re-quantised to 4 bits (sigma 3 clipped to +-7, as a
+    # 4-bit digitiser delivers it) on the FP8 tensor path: exact for |x| <= 16.
+    w = synth.LARGE_N
+    x4 = synth.large_n_input(w, 0, device=dev).clamp_(-7, 7)
+    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "int8", precision=xc.XC_PREC_FP8)
+    out = eng.new_output()
+    eng.correlate(x4, out=out, stream=stream)
+    eng.synchronize(stream)
+    eng.set_option(xc.XC_OPT_PROFILE, 1)
+    ms = timed(lambda: eng.correlate(x4, out=out, stream=stream), k) / k
+    eng.synchronize(stream)  # raises on a range report
+    (_, kms), (_, nk) = eng.kernel_times(reset=True)
+    kms /= max(nk, 1)
+    ex = executed_planar(w, 1)
+    res["large_n_4bit_fp8"] = {
+        "workload": "large-N int8 N=256 P=2 F=1024 T=1000, one integration per call, "
+                    "samples clipped to +-7", "useful_ops": w.useful_ops,
+        "tops": w.useful_ops / (ms * 1e-3) / 1e12, "ms": ms, "kernel_ms": kms,
+        "executed_tflops": ex / (kms * 1e-3) / 1e12,
+        "frac_of_peak": ex / (kms * 1e-3) / 1e12 / (peaks["bf16_tflops"] * 2.0),
+        "peak": "%s x 2 (bf16 burst x nominal fp8/bf16 ratio)" % peaks["bf16_tflops"],
+        "exact": "bit-exact vs the int64 oracle: tests/test_fp8_int8_gpu.py"}
+    eng.close()
+    del x4, out
+
     # Batched workload: six subarrays in one persistent launch (graph replay).
     subs = [(b.nstation, b.nfreq, b.ntime) for b in synth.BATCHED]
     xs = [synth.int8_sky(b, device=dev) for b in synth.BATCHED]

@@ -69,7 +69,7 @@ typedef enum {
   XC_OK = 0,
   XC_ERR_INVALID_ARG = 1,   /* NULL pointer, a size <= 0, npol not 1 or 2, bad option */
   XC_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
-  XC_ERR_OVERFLOW_RISK = 3, /* XC_CI8 with ntime > XC_CI8_MAX_NTIME */
+  XC_ERR_OVERFLOW_RISK = 3, /* XC_CI8: ntime > XC_CI8_MAX_NTIME, or |x| > 16 on XC_PREC_FP8 */
   XC_ERR_ALIGNMENT = 4,     /* a device pointer not 16-byte aligned */
   XC_ERR_CUDA = 5,          /* a CUDA runtime/driver call failed */
   XC_ERR_TIMEOUT = 6,       /* a kernel's bounded wait ran out */
@@ -166,8 +166,12 @@ enum {
    * tests: the output is not computed. */
   XC_OPT_TEST_NO_PUBLISH = 100
 };
-/* Operand precision of float input on XC_ENGINE_TENSOR (Sec. 5 leaves the
- * precision of float voltages open; 8-bit input is always exact).  Every
+/* 8-bit input takes XC_PREC_FP16 (default, exact for all int8) or
+ * XC_PREC_FP8: e4m3 operands at twice the tensor rate and half the operand
+ * bytes, exact when every |x| <= 16 (4-bit to 5-bit digitiser data); a
+ * larger value makes xc_synchronize report XC_ERR_OVERFLOW_RISK.
+ * Operand precision of float input on XC_ENGINE_TENSOR (Sec. 5 leaves the
+ * precision of float voltages open).  Every
  * form scales each (channel, input) by a power of two 2^-e chosen from a
  * pre-pass over the integration (largest component of g x), so any finite
  * fp32 input is in range, and undoes it exactly in the epilogue; all forms

@@ -586,8 +586,8 @@ xc_status xc_set_option(xc_handle* h, int key, long long value) {
     case XC_OPT_PRECISION: {
       if (value != XC_PREC_FP16 && value != XC_PREC_HILO && value != XC_PREC_FP8)
         return fail(XC_ERR_INVALID_ARG, "unknown precision %lld", value);
-      if (h->dtype == XC_CI8 && value != XC_PREC_FP16)
-        return fail(XC_ERR_UNSUPPORTED, "8-bit input is exact; precision forms apply to float input");
+      if (h->dtype == XC_CI8 && value == XC_PREC_HILO)
+        return fail(XC_ERR_UNSUPPORTED, "8-bit input is exact in fp16; hi/lo applies to float input");
       const int fmt = static_cast<int>(value);
       const int slots = xc::planar_ring_slots(h->g, h->num_sms, fmt);
       const size_t need = static_cast<size_t>(slots) * xc::planar_slot_bytes(h->g, fmt);
@@ -749,6 +749,9 @@ xc_status xc_synchronize(xc_handle* h, void* stream) {
     if (e != cudaSuccess) return cuda_fail(e, "status reset");
     if (st & xc::kStatusTimeout)
       return fail(XC_ERR_TIMEOUT, "a kernel gave up on a bounded wait (status 0x%x)", st);
+    if (st & xc::kStatusRange)
+      return fail(XC_ERR_OVERFLOW_RISK,
+                  "8-bit input with |x| > 16 on the FP8 tensor path (results are not exact)");
     return fail(XC_ERR_CUDA, "device status 0x%x", st);
   }
   return succeed();

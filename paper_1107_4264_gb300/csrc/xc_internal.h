@@ -28,7 +28,7 @@ XC_HD void tri_coords(int64_t g, int64_t* bx, int64_t* by) {
 }
 
 // Device status word bits.
-enum : int { kStatusTimeout = 1 };
+enum : int { kStatusTimeout = 1, kStatusRange = 2 };
 
 // Geometry of one engine (device-side copy of the handle's sizes).
 struct Geometry {

@@ -412,6 +412,7 @@ __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int
       }
     }
     const bool apply = DT != 0 && (p.gains || p.in_amax);
+    bool unit_over_16 = false;
 #pragma unroll 1
     for (int g = 0; g < kUnitT / 16; ++g) {
       float2 v0[16], v1[16];
@@ -420,6 +421,12 @@ __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int
         const int t = x.ku * kUnitT + g * 16 + i;
         v0[i] = (a0 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a0, t) : make_float2(0.f, 0.f);
         v1[i] = (a1 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a1, t) : make_float2(0.f, 0.f);
+      }
+      if constexpr (DT == 0 && FMT == kFmtF8) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          unit_over_16 |= fmaxf(fmaxf(fabsf(v0[i].x), fabsf(v0[i].y)),
+                                fmaxf(fabsf(v1[i].x), fabsf(v1[i].y))) > 16.f;
       }
       if (apply) {
 #pragma unroll
@@ -486,6 +493,8 @@ __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int
       }
     }
     if (DT == 0 && lane == 0) atomicMax(p.amax + x.c, 128u);  // no scan: worst case
+    if (DT == 0 && FMT == kFmtF8 && __any_sync(0xffffffffu, unit_over_16) && lane == 0)
+      atomicOr(p.status, kStatusRange);  // e4m3 is exact only for |x| <= 16
     publish_unit(p, x.slot, lane);
     if (*abort_flag) return;
   }
@@ -514,9 +523,10 @@ __device__ __forceinline__ void drain_tma(uint32_t bar, uint32_t phase, bool pen
 // stores have drained by the time the proxy fence waits for them; a warp
 // that would have to wait for a slot publishes first (a consumer of the
 // slot's previous channel may need that unit).
-template <bool MULTI>
+template <int FMT, bool MULTI>
 __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int cw, int lane,
                               volatile int* abort_flag) {
+  static_assert(FMT == kFmtF16 || FMT == kFmtF8, "8-bit input: fp16 or e4m3 operands");
   const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
   const long long nw = static_cast<long long>(gridDim.x) * kNumConvWarps;
   const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
@@ -585,41 +595,74 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
       pend = nullptr;
     }
     const int ib = x.hb >> 1;
-    uint8_t* tre = ring_tile<kFmtF16>(p, x.slot, 0, x.kb, ib);
-    uint8_t* tim = ring_tile<kFmtF16>(p, x.slot, 1, x.kb, ib);
+    uint8_t* tre = ring_tile<FMT>(p, x.slot, 0, x.kb, ib);
+    uint8_t* tim = ring_tile<FMT>(p, x.slot, 1, x.kb, ib);
     const int row = (x.hb & 1) * 64 + 2 * lane;  // tile rows 2l and 2l + 1
     // Ring tiles are read back by every block of the channel: keep them in L2.
     const uint64_t pol_last = ptx::l2_policy_evict_last();
-    // max |x| over the unit from the converted (exact) fp16 values; zero-filled
-    // rows and samples contribute 0.
-    __half2 mx[2];
+    unsigned m = 0;  // max |x| over the unit (zero-filled rows and samples contribute 0)
+    if constexpr (FMT == kFmtF16) {
+      // max |x| from the converted (exact) fp16 values.
+      __half2 mx[2];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) mx[q] = __float2half2_rn(0.f);
-    // Rows 2l and 2l + 1 of one plane: bytes j and j + 2 of the words.
-    auto store8 = [&](uint8_t* dst, const uint32_t* W, uint32_t j, __half2& m) {
-      uint32_t v[8];
+      for (int q = 0; q < 2; ++q) mx[q] = __float2half2_rn(0.f);
+      // Rows 2l and 2l + 1 of one plane: bytes j and j + 2 of the words.
+      auto store8 = [&](uint8_t* dst, const uint32_t* W, uint32_t j, __half2& mq) {
+        uint32_t v[8];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        v[k] = pair_i8(W[2 * k], W[2 * k + 1], j);
-        v[4 + k] = pair_i8(W[2 * k], W[2 * k + 1], j + 2);
+        for (int k = 0; k < 4; ++k) {
+          v[k] = pair_i8(W[2 * k], W[2 * k + 1], j);
+          v[4 + k] = pair_i8(W[2 * k], W[2 * k + 1], j + 2);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k += 2)
+          mq = __hmax2(mq, __hmax2(__habs2(*reinterpret_cast<const __half2*>(&v[k])),
+                                   __habs2(*reinterpret_cast<const __half2*>(&v[k + 1]))));
+        ptx::st_global_v8_hint(dst, v, pol_last);
+      };
+#pragma unroll
+      for (int cc = 0; cc < kUnitT / 8; ++cc) {
+        const uint32_t off = (x.cbase + cc) * kChunkStride + row * 16;
+        store8(tre + off, w + 8 * cc, 0u, mx[0]);
+        store8(tim + off, w + 8 * cc, 1u, mx[1]);
       }
+      const __half2 mm = __hmax2(mx[0], mx[1]);
+      m = static_cast<unsigned>(fmaxf(__low2float(mm), __high2float(mm)));
+    } else {
+      // e4m3 operands: exact for |x| <= 16 (a larger value sets the range
+      // status bit below).  16-sample chunks; rows 2l and 2l + 1 per store.
+      uint32_t mb = 0;  // per-byte |x| maximum
 #pragma unroll
-      for (int k = 0; k < 8; k += 2)
-        m = __hmax2(m, __hmax2(__habs2(*reinterpret_cast<const __half2*>(&v[k])),
-                               __habs2(*reinterpret_cast<const __half2*>(&v[k + 1]))));
-      ptx::st_global_v8_hint(dst, v, pol_last);
-    };
+      for (int t = 0; t < kUnitT; ++t) mb = __vmaxu4(mb, __vabs4(w[t]));
+      m = max(max(mb & 0xffu, (mb >> 8) & 0xffu), max((mb >> 16) & 0xffu, mb >> 24));
+      auto cvt4 = [](uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t j) {
+        auto f = [j](uint32_t wv) {
+          return static_cast<float>(static_cast<int8_t>((wv >> (8 * j)) & 0xffu));
+        };
+        return e4m3x4(f(w0), f(w1), f(w2), f(w3));
+      };
 #pragma unroll
-    for (int cc = 0; cc < kUnitT / 8; ++cc) {
-      const uint32_t off = (x.cbase + cc) * kChunkStride + row * 16;
-      store8(tre + off, w + 8 * cc, 0u, mx[0]);
-      store8(tim + off, w + 8 * cc, 1u, mx[1]);
+      for (int cc = 0; cc < kUnitT / 16; ++cc) {
+        const uint32_t off = (x.cbase / 2 + cc) * kChunkStride + row * 16;
+        const uint32_t* W = w + 16 * cc;
+        uint32_t vr[8], vi[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          vr[k] = cvt4(W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3], 0);
+          vi[k] = cvt4(W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3], 1);
+          vr[4 + k] = cvt4(W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3], 2);
+          vi[4 + k] = cvt4(W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3], 3);
+        }
+        ptx::st_global_v8_hint(tre + off, vr, pol_last);
+        ptx::st_global_v8_hint(tim + off, vi, pol_last);
+      }
     }
-    const __half2 mm = __hmax2(mx[0], mx[1]);
-    unsigned m = static_cast<unsigned>(fmaxf(__low2float(mm), __high2float(mm)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) atomicMax(p.amax + x.c, m);
+    if (lane == 0) {
+      atomicMax(p.amax + x.c, m);
+      if (FMT == kFmtF8 && m > 16) atomicOr(p.status, kStatusRange);
+    }
     if (pend) {
       ++pend_n;
     } else {
@@ -1288,7 +1331,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int cw = warp - (2 + kNumEpiWarps);
     if constexpr (DT == 0) {
       if (bt.sub[0].tma_in) {  // set for every subarray or for none
-        converter_tma<MULTI>(bt, sbase + kConvOff + cw * kConvBufBytes, conv_bar(cw), cw, lane, abort_flag);
+        converter_tma<FMT, MULTI>(bt, sbase + kConvOff + cw * kConvBufBytes, conv_bar(cw), cw, lane,
+                                  abort_flag);
       } else {
         converter_direct<DT, FMT, MULTI>(bt, cw, lane, abort_flag);
       }
@@ -1318,7 +1362,10 @@ const void* kernel_of() {
 
 // Batches of several subarrays take 8-bit input.
 const void* select_kernel(int in_dtype, int fmt, bool multi) {
-  if (in_dtype == 0) return multi ? kernel_of<true, 0, kFmtF16, true>() : kernel_of<true, 0, kFmtF16>();
+  if (in_dtype == 0) {
+    if (fmt == kFmtF8) return multi ? nullptr : kernel_of<true, 0, kFmtF8>();
+    return multi ? kernel_of<true, 0, kFmtF16, true>() : kernel_of<true, 0, kFmtF16>();
+  }
   if (multi) return nullptr;
   if (in_dtype != 1 && in_dtype != 2) return nullptr;
   const bool h = in_dtype == 1;
@@ -1377,7 +1424,7 @@ Params sub_params(const XeLaunch& L) {
   p.nitems = static_cast<long long>(p.ntiles) * L.g.F;
   p.nkb = L.g.Tp / kBK;
   p.is_int = L.in_dtype == 0 ? 1 : 0;
-  const int fmt = p.is_int ? kFmtF16 : L.fmt;
+  const int fmt = p.is_int ? (L.fmt == kFmtF8 ? kFmtF8 : kFmtF16) : L.fmt;
   p.nkt = fmt_kt(fmt) * p.nkb;
   p.amax = L.amax;
   p.gains = static_cast<const float2*>(L.gains);
@@ -1422,13 +1469,17 @@ cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps,
                            PlanarKernel* k) {
   if (nsub < 1 || nsub > kMaxSub || !subs || !k) return cudaErrorInvalidValue;
   const int dt = subs[0].in_dtype;
-  const int fmt = dt == 0 ? kFmtF16 : subs[0].fmt;
+  // 8-bit input: fp16 operands, or e4m3 when asked for (exact for |x| <= 16).
+  auto fmt_of = [](const XeLaunch& L) {
+    return L.in_dtype == 0 ? (L.fmt == kFmtF8 ? kFmtF8 : kFmtF16) : L.fmt;
+  };
+  const int fmt = fmt_of(subs[0]);
   Batch* b = reinterpret_cast<Batch*>(k->args);
   memset(b, 0, sizeof(Batch));
   b->nsub = nsub;
   bool all_tma = true;
   for (int i = 0; i < nsub; ++i) {
-    if (subs[i].in_dtype != dt || (dt != 0 && subs[i].fmt != fmt)) return cudaErrorInvalidValue;
+    if (subs[i].in_dtype != dt || fmt_of(subs[i]) != fmt) return cudaErrorInvalidValue;
     if (subs[i].ring_slots < 1 || subs[i].ring_slots > kMaxRingSlots) return cudaErrorInvalidValue;
     b->sub[i] = sub_params(subs[i]);
     if (maps && maps[i]) {

@@ -150,9 +150,10 @@ def test_precision_options_validated(dev):
     eng = xc.Correlator(8, 2, 2, 64, "int8")
     try:
         with pytest.raises(xc.XcError):
-            eng.set_option(xc.XC_OPT_PRECISION, xc.XC_PREC_FP8)
+            eng.set_option(xc.XC_OPT_PRECISION, xc.XC_PREC_HILO)
         with pytest.raises(xc.XcError):
             eng.set_option(xc.XC_OPT_FP64_BLOCK, 128)
+        eng.set_option(xc.XC_OPT_PRECISION, xc.XC_PREC_FP8)  # exact for |x| <= 16
     finally:
         eng.close()
     eng = xc.Correlator(8, 2, 2, 64, "float32")
