@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -76,6 +77,8 @@ size_t sample_bytes(xc_dtype d) { return d == XC_CI8 ? 1 : (d == XC_CF16 ? 2 : 4
 // captured graph (memsets + one persistent launch).
 struct BatchSub {
   xc::Geometry g{};
+  xc::Geometry pg{};   // planar engine's geometry: `pack` channels per virtual channel
+  int pack = 1;
   size_t in_bytes = 0, out_bytes = 0;
   void* ring = nullptr;
   int slots_base = 0;  // ring depth 1x (xc::planar_ring_slots)
@@ -114,6 +117,10 @@ struct xc_handle {
   unsigned* chan_amax = nullptr;  // [F] per-channel max |x| (planar engine)
   CUtensorMap ring_tmap;     // interleaved form: {Tp, R, ring_slots}
   int planar_slots = 0;       // planar form: xc::planar_slot_bytes() per slot
+  // Planar engine geometry: small arrays pack `pack` consecutive channels into
+  // one virtual channel (xc::planar_geometry); pg is that virtual geometry.
+  xc::Geometry pg{};
+  int pack = 1;
   size_t ring_bytes = 0;
   // Float input on the planar engine: operand precision, scale pre-pass
   // buffer [F][n] and the FP64 block sums (allocated on use).
@@ -240,7 +247,8 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
   }
   if (h->engine == XC_ENGINE_TENSOR) {
     xc::XeLaunch X;
-    X.g = h->g;
+    X.g = h->pg;
+    X.pack = h->pack;
     X.in = in;
     X.in_dtype = static_cast<int>(h->dtype);
     X.out = out;
@@ -261,8 +269,8 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     // Input in TMA boxes when its rows are 16-byte strided.
     CUtensorMap in_map;
     const CUtensorMap* im = nullptr;
-    if (input_map_possible(h->dtype, h->g)) {
-      if (encode_input_map(&in_map, in, h->g, h->dtype) != XC_OK) return t_status;
+    if (input_map_possible(h->dtype, h->pg)) {
+      if (encode_input_map(&in_map, in, h->pg, h->dtype) != XC_OK) return t_status;
       im = &in_map;
     }
     if (tm) tm->nkern = 1;
@@ -525,11 +533,12 @@ xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_d
     return nullptr;
   }
   h->ring_slots = xc::xengine_ring_slots(h->g);
-  h->planar_slots = xc::planar_ring_slots(h->g, h->num_sms, XC_PREC_FP16);
+  h->pg = xc::planar_geometry(h->g, &h->pack);
+  h->planar_slots = xc::planar_ring_slots(h->pg, h->num_sms, XC_PREC_FP16);
   const int slots = std::max({h->ring_slots, h->planar_slots, xc::kMaxRingSlots});
   h->ring_bytes = std::max(static_cast<size_t>(h->ring_slots) * R * Tp * 2,
                            static_cast<size_t>(h->planar_slots) *
-                               xc::planar_slot_bytes(h->g, XC_PREC_FP16));
+                               xc::planar_slot_bytes(h->pg, XC_PREC_FP16));
   e = cudaMalloc(&h->ring, h->ring_bytes);
   if (e == cudaSuccess)
     e = cudaMalloc(reinterpret_cast<void**>(&h->counters), 2 * sizeof(unsigned) * slots);
@@ -589,8 +598,8 @@ xc_status xc_set_option(xc_handle* h, int key, long long value) {
       if (h->dtype == XC_CI8 && value == XC_PREC_HILO)
         return fail(XC_ERR_UNSUPPORTED, "8-bit input is exact in fp16; hi/lo applies to float input");
       const int fmt = static_cast<int>(value);
-      const int slots = xc::planar_ring_slots(h->g, h->num_sms, fmt);
-      const size_t need = static_cast<size_t>(slots) * xc::planar_slot_bytes(h->g, fmt);
+      const int slots = xc::planar_ring_slots(h->pg, h->num_sms, fmt);
+      const size_t need = static_cast<size_t>(slots) * xc::planar_slot_bytes(h->pg, fmt);
       if (need > h->ring_bytes) {
         // Work already queued may still use the ring.
         cudaError_t e = cudaDeviceSynchronize();
@@ -825,8 +834,8 @@ namespace {
 
 // Work of subarray i in MMA block-steps: blocks per channel x channels x K-blocks.
 double batch_work(const BatchSub& b) {
-  const double nib = (static_cast<double>(b.g.N) * b.g.P + 127) / 128;
-  return nib * (nib + 1) / 2 * b.g.F * (b.g.Tp / 64);
+  const double nib = std::ceil((static_cast<double>(b.pg.N) * b.pg.P) / 128);
+  return nib * (nib + 1) / 2 * b.pg.F * (b.pg.Tp / 64);
 }
 
 // Candidate c: work-list order (c % 3: as given, largest first, smallest
@@ -866,7 +875,8 @@ xc_status batch_prepare(xc_handle* h, const void* const* in, void* const* out,
       return fail(XC_ERR_ALIGNMENT, "subarray %d: buffers must be 16-byte aligned", i);
     xc::XeLaunch& X = L[j];
     X = xc::XeLaunch{};
-    X.g = s.g;
+    X.g = s.pg;
+    X.pack = s.pack;
     X.in = in[i];
     X.in_dtype = static_cast<int>(h->dtype);
     X.out = out[i];
@@ -880,8 +890,8 @@ xc_status batch_prepare(xc_handle* h, const void* const* in, void* const* out,
     X.timeout_ns = h->timeout_ns;
     X.status = h->d_status;
     mp[j] = nullptr;
-    if (h->dtype == XC_CI8 && s.g.R % 16 == 0) {
-      if (encode_input_map(&maps[j], in[i], s.g) != XC_OK) return t_status;
+    if (h->dtype == XC_CI8 && s.pg.R % 16 == 0) {
+      if (encode_input_map(&maps[j], in[i], s.pg) != XC_OK) return t_status;
       mp[j] = &maps[j];
     }
   }
@@ -941,11 +951,12 @@ xc_handle* xc_batch_create(int nsub, const int* nstation, const int* nfreq, cons
     s.g.NB = static_cast<int64_t>(nstation[i]) * (nstation[i] + 1) / 2;
     s.in_bytes = static_cast<size_t>(ntime[i]) * nfreq[i] * nstation[i] * npol * 2;
     s.out_bytes = static_cast<size_t>(nfreq[i]) * s.g.NB * npol * npol * 2 * 4;
-    const int64_t slot_bytes = xc::planar_slot_bytes(s.g, XC_PREC_FP16);
-    s.slots_base = xc::planar_ring_slots(s.g, h->num_sms, XC_PREC_FP16);
+    s.pg = xc::planar_geometry(s.g, &s.pack);
+    const int64_t slot_bytes = xc::planar_slot_bytes(s.pg, XC_PREC_FP16);
+    s.slots_base = xc::planar_ring_slots(s.pg, h->num_sms, XC_PREC_FP16);
     const int64_t cap2 = std::max<int64_t>(s.slots_base, (512ll << 20) / std::max<int64_t>(slot_bytes, 1));
     s.max_slots = static_cast<int>(std::min<int64_t>(
-        {static_cast<int64_t>(xc::kMaxRingSlots), static_cast<int64_t>(s.g.F), 2ll * s.slots_base, cap2}));
+        {static_cast<int64_t>(xc::kMaxRingSlots), static_cast<int64_t>(s.pg.F), 2ll * s.slots_base, cap2}));
     s.max_slots = std::max(s.max_slots, s.slots_base);
     ring_off[i] = ring_total;
     ring_total += static_cast<size_t>(s.max_slots) * slot_bytes;

@@ -47,6 +47,9 @@ struct XeLaunch {
   double* acc64 = nullptr;  // FP64 block sums in the output layout (NULL: off)
   int f64_block = 0;        // samples per fp32 block when acc64 is set (multiple of 64)
   int test_no_publish = 0;  // test hook (XC_OPT_TEST_NO_PUBLISH)
+  // Planar engine: g is the virtual geometry of planar_geometry(), with `pack`
+  // consecutive real channels in each virtual channel (1: no packing).
+  int pack = 1;
   int grid;
   unsigned long long timeout_ns;
   int* status;
@@ -62,6 +65,12 @@ constexpr int kMaxRingSlots = 256;
 // in 128-row x 1 x kPlanarUnitT boxes).
 constexpr int kPlanarUnitT = 64;
 int planar_ring_slots(const Geometry& g, int grid, int fmt);
+// Small arrays (n = N P <= 64 inputs): k consecutive channels, k the largest
+// divisor of F with k n <= 128, are correlated as one virtual channel of k N
+// stations.  The input [T][F][n] is the same memory as [T][F / k][k n], so
+// nothing moves; one 128 x 128 block then holds the k channels' own blocks on
+// its diagonal.  Returns that virtual geometry and k (1 for larger arrays).
+Geometry planar_geometry(const Geometry& g, int* pack);
 int64_t planar_slot_bytes(const Geometry& g, int fmt);
 
 // One planar launch over up to kMaxSub subarrays (same input type and

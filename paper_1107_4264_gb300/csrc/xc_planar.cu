@@ -139,6 +139,14 @@ struct Params {
   unsigned long long timeout_ns;
   int* status;
   int test_no_publish;  // test hook: converted units are never published
+  // Small arrays: `pack` consecutive channels form one virtual channel of
+  // pack * Nr stations (g, n, F above are the virtual geometry; the input
+  // [T][F][n] is the same memory as [T][F / pack][pack * n]).  The epilogue
+  // keeps only each real channel's own block and stores it at real indices.
+  int pack;
+  int Nr;              // real stations per channel
+  int64_t NBr;         // real baselines per channel
+  int gain_n;          // real inputs per channel (gains are indexed a mod gain_n)
 };
 
 // One launch over up to kMaxSub subarrays (Sec. 4.2's channel-major raster
@@ -400,8 +408,8 @@ __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int
     float2 g0 = make_float2(1.f, 0.f), g1 = make_float2(1.f, 0.f);
     if (DT != 0) {
       if (p.gains) {
-        g0 = a0 < p.n ? p.gains[a0] : make_float2(0.f, 0.f);
-        g1 = a1 < p.n ? p.gains[a1] : make_float2(0.f, 0.f);
+        g0 = a0 < p.n ? p.gains[a0 % p.gain_n] : make_float2(0.f, 0.f);
+        g1 = a1 < p.n ? p.gains[a1 % p.gain_n] : make_float2(0.f, 0.f);
       }
       if (p.in_amax) {
         const unsigned* am = p.in_amax + static_cast<int64_t>(x.c) * p.n;
@@ -809,8 +817,8 @@ __device__ void converter_tma_float(const Batch& bt, uint32_t buf, uint32_t bar,
     // y = g x 2^-e.
     float2 g0 = make_float2(1.f, 0.f), g1 = make_float2(1.f, 0.f);
     if (p.gains) {
-      g0 = a0 < p.n ? p.gains[a0] : make_float2(0.f, 0.f);
-      g1 = a1 < p.n ? p.gains[a1] : make_float2(0.f, 0.f);
+      g0 = a0 < p.n ? p.gains[a0 % p.gain_n] : make_float2(0.f, 0.f);
+      g1 = a1 < p.n ? p.gains[a1 % p.gain_n] : make_float2(0.f, 0.f);
     }
     if (p.in_amax) {
       const unsigned* am = p.in_amax + static_cast<int64_t>(x.c) * p.n;
@@ -902,25 +910,36 @@ __device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint
     }
   };
   if (a >= p.n) return;
+  // Real channel, row station and first column station (packed channels:
+  // columns of another channel of the pack fall outside 0 <= s2 <= s1).
+  int fr = f, s1 = a / g.P, s2_0 = b0 / g.P;
+  if (p.pack > 1) {
+    const int j = s1 / p.Nr;
+    s1 -= j * p.Nr;
+    s2_0 -= j * p.Nr;
+    fr = f * p.pack + j;
+  }
+  const int64_t krow = static_cast<int64_t>(fr) * p.NBr + static_cast<int64_t>(s1) * (s1 + 1) / 2;
   if (g.P == 2) {
-    const int s1 = a >> 1, p1 = a & 1;
-    const int64_t krow = static_cast<int64_t>(f) * g.NB + static_cast<int64_t>(s1) * (s1 + 1) / 2;
-    const int s2_0 = b0 >> 1;
+    const int p1 = a & 1;
     using V4 = typename std::conditional<IS_INT, int4, float4>::type;
-    V4* o4 = reinterpret_cast<V4*>(out + (krow * 4 + p1 * 2) * 2) + (s2_0 * 2);  // (p1,0),(p1,1) of s2_0
+    V4* o4 = reinterpret_cast<V4*>(out + (krow * 4 + p1 * 2) * 2);  // (p1,0),(p1,1) of s2 at o4[2 s2]
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       V4 old[8];
       if (add) {
         // Loads of a half first: independent of the stores that follow.
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (s2_0 + 8 * h + j <= s1) old[j] = o4[2 * (8 * h + j)];
+        for (int j = 0; j < 8; ++j) {
+          const int s2 = s2_0 + 8 * h + j;
+          if (s2 >= 0 && s2 <= s1) old[j] = o4[2 * s2];
+        }
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int jj = 8 * h + j;
-        if (s2_0 + jj <= s1) {
+        const int s2 = s2_0 + jj;
+        if (s2 >= 0 && s2 <= s1) {
           V4 v;
           v.x = val(re[2 * jj]);
           v.y = val(im[2 * jj]);
@@ -932,27 +951,28 @@ __device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint
             v.z += old[j].z;
             v.w += old[j].w;
           }
-          o4[2 * jj] = v;
+          o4[2 * s2] = v;
         }
       }
     }
   } else {
-    const int s1 = a;
-    const int64_t krow = static_cast<int64_t>(f) * g.NB + static_cast<int64_t>(s1) * (s1 + 1) / 2;
     using V2 = typename std::conditional<IS_INT, int2, float2>::type;
-    V2* o2 = reinterpret_cast<V2*>(out + krow * 2) + b0;
+    V2* o2 = reinterpret_cast<V2*>(out + krow * 2);  // baseline s2 at o2[s2]
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       V2 old[8];
       if (add) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (b0 + 8 * h + j <= s1) old[j] = o2[8 * h + j];
+        for (int j = 0; j < 8; ++j) {
+          const int s2 = s2_0 + 8 * h + j;
+          if (s2 >= 0 && s2 <= s1) old[j] = o2[s2];
+        }
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int jj = 8 * h + j;
-        if (b0 + jj <= s1) {
+        const int s2 = s2_0 + jj;
+        if (s2 >= 0 && s2 <= s1) {
           V2 v;
           v.x = val(re[jj]);
           v.y = val(im[jj]);
@@ -960,7 +980,7 @@ __device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint
             v.x += old[j].x;
             v.y += old[j].y;
           }
-          o2[jj] = v;
+          o2[s2] = v;
         }
       }
     }
@@ -989,16 +1009,23 @@ __device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const 
                                                 bool last) {
   if (a >= p.n) return;
   const int P = p.g.P;
-  const int s1 = a / P, p1 = a - s1 * P;
-  const int64_t krow = static_cast<int64_t>(f) * p.g.NB + static_cast<int64_t>(s1) * (s1 + 1) / 2;
+  int s1 = a / P, joff = 0, fr = f;
+  const int p1 = a - s1 * P;
+  if (p.pack > 1) {  // packed channels: real channel and stations
+    const int j = s1 / p.Nr;
+    joff = j * p.Nr;
+    s1 -= joff;
+    fr = f * p.pack + j;
+  }
+  const int64_t krow = static_cast<int64_t>(fr) * p.NBr + static_cast<int64_t>(s1) * (s1 + 1) / 2;
   const bool load_old = !first || p.accumulate;
   double2* ws = reinterpret_cast<double2*>(p.acc64);
   float2* out = static_cast<float2*>(p.out);
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const int b = b0 + j;
-    const int s2 = b / P, p2 = b - s2 * P;
-    if (s2 > s1) continue;
+    const int s2v = b / P, p2 = b - s2v * P, s2 = s2v - joff;
+    if (s2 < 0 || s2 > s1) continue;
     const int64_t idx = (krow + s2) * P * P + p1 * P + p2;
     double2 v = make_double2(static_cast<double>(__uint_as_float(re[j])),
                              static_cast<double>(__uint_as_float(im[j])));
@@ -1245,11 +1272,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       int f, bx, by;
       item_coords(it - bt.item_base[sb], p.ntiles, &f, &bx, &by);
       const int a = by * kBlk + q * 32 + lane;  // this thread's row input
-      // Pieces 0..last can reach the lower station triangle for this warp.
+      // Pieces piece0..last can reach the lower station triangle for this
+      // warp (packed channels: only from the first column of the lowest
+      // row's real channel on).
       const int s1_hi = min(p.g.N - 1, (by * kBlk + q * 32 + 31) / P);
       int last = -1;
       for (int piece = 0; piece < kBlk / 32; ++piece)
         if ((bx * kBlk + piece * 32) / P <= s1_hi) last = piece;
+      int piece0 = 0;
+      if (p.pack > 1) {
+        const int col0 = (by * kBlk + q * 32) / P / p.Nr * p.Nr * P;  // first column of that channel
+        piece0 = max(0, (col0 - bx * kBlk) / 32);
+        if (piece0 > last) last = -1;  // no row of this warp is valid
+      }
       const bool rdy = channel_ready(p, f, abort_flag);
       if (!__all_sync(0xffffffffu, rdy)) {
         ok = false;
@@ -1281,7 +1316,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
           }
 #pragma unroll 1
-          for (int piece = 0; piece <= last; ++piece) {
+          for (int piece = piece0; piece <= last; ++piece) {
             uint32_t vr[32], vi[32];
             ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + piece * 32, vr);
             ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + 128 + piece * 32, vi);
@@ -1385,13 +1420,13 @@ template <int DT>
 __global__ void __launch_bounds__(128) input_amax_kernel(const void* __restrict__ in,
                                                          const float2* __restrict__ gains,
                                                          unsigned* __restrict__ amax, Geometry g,
-                                                         int n) {
+                                                         int n, int gain_n) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = blockIdx.y;
   if (a >= n) return;
   const int t0 = blockIdx.z * 128;
   const int t1 = min(g.T, t0 + 128);
-  const float2 ga = gains ? gains[a] : make_float2(1.f, 0.f);
+  const float2 ga = gains ? gains[a % gain_n] : make_float2(1.f, 0.f);
   float m = 0.f;
 #pragma unroll 8
   for (int t = t0; t < t1; ++t) {
@@ -1442,6 +1477,10 @@ Params sub_params(const XeLaunch& L) {
   p.timeout_ns = L.timeout_ns;
   p.status = L.status;
   p.test_no_publish = L.test_no_publish;
+  p.pack = std::max(1, L.pack);
+  p.Nr = L.g.N / p.pack;
+  p.NBr = static_cast<int64_t>(p.Nr) * (p.Nr + 1) / 2;
+  p.gain_n = p.Nr * L.g.P;
   return p;
 }
 
@@ -1450,6 +1489,26 @@ Params sub_params(const XeLaunch& L) {
 int64_t planar_slot_bytes(const Geometry& g, int fmt) {
   const int64_t nib = (static_cast<int64_t>(g.N) * g.P + kBlk - 1) / kBlk;
   return 2 * fmt_kt(fmt) * (g.Tp / kBK) * nib * fmt_tile_bytes(fmt);
+}
+
+Geometry planar_geometry(const Geometry& g, int* pack) {
+  int k = 1;
+  const int64_t n = static_cast<int64_t>(g.N) * g.P;
+  if (n <= kBlk / 2) {
+    for (int c = static_cast<int>(kBlk / n); c >= 2; --c) {
+      if (g.F % c == 0) {
+        k = c;
+        break;
+      }
+    }
+  }
+  Geometry v = g;
+  v.N = g.N * k;
+  v.F = g.F / k;
+  v.R = g.R * k;
+  v.NB = static_cast<int64_t>(v.N) * (v.N + 1) / 2;
+  if (pack) *pack = k;
+  return v;
 }
 
 int planar_ring_slots(const Geometry& g, int grid, int fmt) {
@@ -1514,10 +1573,11 @@ cudaError_t planar_setup(const XeLaunch* subs, int nsub, cudaStream_t s) {
       const dim3 ag((n + 127) / 128, L.g.F, (L.g.T + 127) / 128);
       if (ag.z > 65535u) return cudaErrorInvalidConfiguration;
       const float2* gains = static_cast<const float2*>(L.gains);
+      const int gain_n = n / std::max(1, L.pack);
       if (L.in_dtype == 1)
-        input_amax_kernel<1><<<ag, 128, 0, s>>>(L.in, gains, L.in_amax, L.g, n);
+        input_amax_kernel<1><<<ag, 128, 0, s>>>(L.in, gains, L.in_amax, L.g, n, gain_n);
       else
-        input_amax_kernel<2><<<ag, 128, 0, s>>>(L.in, gains, L.in_amax, L.g, n);
+        input_amax_kernel<2><<<ag, 128, 0, s>>>(L.in, gains, L.in_amax, L.g, n, gain_n);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
