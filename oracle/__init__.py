@@ -8,7 +8,9 @@ of Clark, La Plante & Greenhill each function follows:
 * ``correlate_i8`` / ``correlate_f64`` -- Sec. 2.1 Eq. (outer) with the dual
   polarisation, lower-triangle packing of Sec. 2.1 / Sec. 4.2 and the input
   ordering of Sec. 4.1;
-* ``backward_f64`` -- the adjoint of the float form (not in the paper).
+* ``backward_f64`` -- the adjoint of the float form (not in the paper);
+* ``channelize_f64`` -- the F-engine of Sec. 2 (blockwise DFT of each
+  station's signal) with the corner turn into the X-engine's input order.
 
 Arrays use the engine's layouts: input ``[T][F][N][P][2]``, output
 ``[F][N(N+1)/2][P*P][2]``.
@@ -35,7 +37,7 @@ def build(force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:
         return out
     os.makedirs(os.path.dirname(out), exist_ok=True)
     tmp = out + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", tmp, src]
+    cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
@@ -57,6 +59,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.xco_correlate_f64.restype = i32
     lib.xco_backward_f64.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, vp]
     lib.xco_backward_f64.restype = i32
+    lib.xco_channelize_f64.argtypes = [vp, i32, i32, i32, i32, ctypes.c_double, vp, i32, vp]
+    lib.xco_channelize_f64.restype = i32
     return lib
 
 
@@ -141,3 +145,25 @@ def backward_f64(x: np.ndarray, grad_out: np.ndarray, gains: Optional[np.ndarray
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     return gx, gg
+
+
+def channelize_f64(x: np.ndarray, nchan: int, scale: float = 1.0,
+                   sel: Optional[Sequence[Sequence[int]]] = None,
+                   lib: Optional[ctypes.CDLL] = None) -> np.ndarray:
+    """F-engine: ``x[N][P][T*nchan][2]`` (each station's complex stream) ->
+    ``X[T][nchan][N][P][2]`` with ``X[t][f] = scale * sum_m x[t*nchan + m]
+    exp(-2 pi i f m / nchan)``; with ``sel`` (a list of (t, f) pairs) only
+    those outputs, as ``[len(sel)][N][P][2]``."""
+    lib = lib or load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    N, P, L, two = x.shape
+    assert two == 2 and L % nchan == 0
+    T = L // nchan
+    s = None if sel is None else np.ascontiguousarray(np.asarray(sel, dtype=np.int32).reshape(-1, 2))
+    nout = T * nchan if s is None else len(s)
+    out = np.zeros((nout, N, P, 2), dtype=np.float64)
+    rc = lib.xco_channelize_f64(_ptr(x), N, P, nchan, T, float(scale),
+                                None if s is None else _ptr(s), 0 if s is None else len(s), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    return out if s is not None else out.reshape(T, nchan, N, P, 2)

@@ -37,10 +37,20 @@
  * H = G + G^H:  grad_y = H y,  grad_x = conj(g) grad_y,
  * grad_g = sum_{f,t} conj(x) grad_y.
  *
+ * F-engine (Sec. 2, the FX correlator): each station's signal is Fourier
+ * transformed in blocks of F consecutive complex samples, giving F channels
+ * per block,  X_t(f) = sum_{m<F} x(t F + m) exp(-2 pi i f m / F), and the
+ * corner turn reorders the result from station-major to the X-engine's order
+ * (station fastest, then channel, then block; Sec. 4.1).  Readings: the
+ * transform carries a caller-given real factor `scale` (the paper leaves the
+ * normalisation open); channel f is the f-th DFT bin (DC first), not
+ * re-centred.
+ *
  * Every function follows the definition with plain loops in the order
  * channel -> baseline -> polarisation pair -> time; OpenMP only splits the
- * independent channels across threads.
+ * independent channels (blocks for the F-engine) across threads.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -264,5 +274,57 @@ int xco_backward_f64(const double* in, const double* gains, const double* grad_o
       }
   }
   free(gg_all);
+  return bad ? -1 : 0;
+}
+
+/*
+ * F-engine, Sec. 2: the DFT definition over each block of F samples of each
+ * station and polarisation, written in the corner-turned order.
+ *   in  [N][P][T*F][2]  (station-major streams)
+ *   out [T][F][N][P][2] when sel is NULL, else [nsel][N][P][2] for the
+ *       (block, channel) pairs sel[2 i], sel[2 i + 1].
+ * The phase index f*m is reduced mod F before the cosine and sine, so every
+ * twiddle is one of the F exact roots of unity.
+ */
+int xco_channelize_f64(const double* in, int N, int P, int F, int T, double scale,
+                       const int32_t* sel, int nsel, double* out) {
+  if (N <= 0 || P <= 0 || F <= 0 || T <= 0 || (sel && nsel <= 0)) return -1;
+  const int64_t n = (int64_t)N * P;
+  const int64_t nout = sel ? nsel : (int64_t)T * F;
+  double* wr = (double*)malloc((size_t)F * sizeof(double));
+  double* wi = (double*)malloc((size_t)F * sizeof(double));
+  if (!wr || !wi) {
+    free(wr);
+    free(wi);
+    return -1;
+  }
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int j = 0; j < F; ++j) {
+    wr[j] = cos(two_pi * (double)j / (double)F);
+    wi[j] = -sin(two_pi * (double)j / (double)F);
+  }
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+  for (int64_t o = 0; o < nout; ++o) {
+    const int64_t t = sel ? sel[2 * o] : o / F;
+    const int64_t f = sel ? sel[2 * o + 1] : o % F;
+    if (t < 0 || t >= T || f < 0 || f >= F) {
+      bad = 1;
+      continue;
+    }
+    for (int64_t a = 0; a < n; ++a) {
+      const double* x = in + (a * T * F + t * F) * 2;
+      double re = 0.0, im = 0.0;
+      for (int64_t m = 0; m < F; ++m) {
+        const int64_t j = (f * m) % F;
+        re += x[2 * m] * wr[j] - x[2 * m + 1] * wi[j];
+        im += x[2 * m] * wi[j] + x[2 * m + 1] * wr[j];
+      }
+      out[(o * n + a) * 2] = scale * re;
+      out[(o * n + a) * 2 + 1] = scale * im;
+    }
+  }
+  free(wr);
+  free(wi);
   return bad ? -1 : 0;
 }

@@ -14,7 +14,11 @@ oracle disagrees with:
 * the statistical expectation for injected point sources (this fixes the
   conjugation convention: the phase of V_ab is phi_a - phi_b);
 * the int32 range argument of the 8-bit path (Sec. 5 input, int64 oracle);
-* central finite differences of the FP64 forward for the adjoint.
+* central finite differences of the FP64 forward for the adjoint;
+* for the F-engine (Sec. 2): numpy's FFT on random blocks (the library
+  special case), the closed form of a pure tone, Parseval's identity, a
+  delta's phase ramp in the corner-turned position, and the FX closed form of
+  a tone shared by all stations.
 """
 from __future__ import annotations
 
@@ -241,6 +245,84 @@ def pin_adjoint_finite_differences(lib):
         assert abs(fd - gg[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, gg[i])
 
 
+def _fx(x):
+    """[N][P][L][2] complex streams -> complex128 [N][P][L]."""
+    return _cx(x)
+
+
+def pin_fengine_numpy_fft(lib):
+    """Random blocks, several channel counts (not only powers of two):
+    X[t][f][s][p] = scale * fft(x[s][p][t F : (t + 1) F])[f]."""
+    rng = np.random.default_rng(31)
+    for N, P, F, T in ((2, 2, 16, 3), (3, 1, 12, 2), (1, 2, 64, 2), (2, 2, 5, 4)):
+        x = rng.standard_normal((N, P, T * F, 2))
+        got = _cx(oracle.channelize_f64(x, F, 0.75, lib=lib))
+        ref = np.fft.fft(_fx(x).reshape(N, P, T, F), axis=-1) * 0.75
+        np.testing.assert_allclose(got, np.transpose(ref, (2, 3, 0, 1)), rtol=0, atol=1e-11)
+
+
+def pin_fengine_tone(lib):
+    """x(tau) = A_sp exp(2 pi i k0 tau / F): every block gives scale * F * A_sp
+    in channel k0 and nothing elsewhere."""
+    rng = np.random.default_rng(32)
+    N, P, F, T, k0, scale = 3, 2, 32, 3, 5, 0.5
+    A = rng.standard_normal((N, P)) + 1j * rng.standard_normal((N, P))
+    tau = np.arange(T * F)
+    z = A[:, :, None] * np.exp(2j * np.pi * k0 * tau / F)[None, None, :]
+    x = np.stack([z.real, z.imag], axis=-1)
+    got = _cx(oracle.channelize_f64(x, F, scale, lib=lib))
+    want = np.zeros((T, F, N, P), dtype=np.complex128)
+    want[:, k0] = scale * F * A[None]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-10)
+
+
+def pin_fengine_parseval(lib):
+    """sum_f |X_t(f)|^2 = F sum_m |x(t F + m)|^2 for each block, station, pol."""
+    rng = np.random.default_rng(33)
+    N, P, F, T = 2, 2, 24, 3
+    x = rng.standard_normal((N, P, T * F, 2))
+    X = _cx(oracle.channelize_f64(x, F, 1.0, lib=lib))          # [T][F][N][P]
+    e_out = (np.abs(X) ** 2).sum(axis=1)                           # [T][N][P]
+    e_in = (np.abs(_fx(x).reshape(N, P, T, F)) ** 2).sum(axis=-1)  # [N][P][T]
+    np.testing.assert_allclose(e_out, F * np.transpose(e_in, (2, 0, 1)), rtol=1e-12)
+
+
+def pin_fengine_delta_layout(lib):
+    """A unit sample at (s0, p0, tau0) lands in block tau0 // F of station s0,
+    pol p0 only, as the phase ramp scale * exp(-2 pi i f (tau0 mod F) / F)."""
+    N, P, F, T, scale = 3, 2, 16, 4, 2.0
+    s0, p0, tau0 = 2, 1, 2 * 16 + 7
+    x = np.zeros((N, P, T * F, 2))
+    x[s0, p0, tau0, 0] = 1.0
+    got = _cx(oracle.channelize_f64(x, F, scale, lib=lib))
+    want = np.zeros((T, F, N, P), dtype=np.complex128)
+    want[tau0 // F, :, s0, p0] = scale * np.exp(-2j * np.pi * np.arange(F) * (tau0 % F) / F)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+def pin_fengine_fx_tone(lib):
+    """FX: stations seeing one tone A_a exp(2 pi i k0 tau / F) give, after the
+    F-engine and the X-engine, V_ab = T (scale F)^2 A_a conj(A_b) in channel k0
+    and zero in every other channel."""
+    rng = np.random.default_rng(34)
+    N, P, F, T, k0, scale = 3, 2, 16, 5, 3, 0.25
+    A = rng.standard_normal((N, P)) + 1j * rng.standard_normal((N, P))
+    tau = np.arange(T * F)
+    z = A[:, :, None] * np.exp(2j * np.pi * k0 * tau / F)[None, None, :]
+    X = oracle.channelize_f64(np.stack([z.real, z.imag], axis=-1), F, scale, lib=lib)
+    V = _cx(oracle.correlate_f64(X, lib=lib))                     # [F][NB][P*P]
+    for s1 in range(N):
+        for s2 in range(s1 + 1):
+            k = s1 * (s1 + 1) // 2 + s2
+            for p1 in range(P):
+                for p2 in range(P):
+                    want = T * (scale * F) ** 2 * A[s1, p1] * np.conj(A[s2, p2])
+                    np.testing.assert_allclose(V[k0, k, p1 * P + p2], want, rtol=1e-9)
+    mask = np.ones(F, dtype=bool)
+    mask[k0] = False
+    assert np.abs(V[mask]).max() < 1e-8 * np.abs(V[k0]).max()
+
+
 ALL_PINS = [
     pin_brute_force_int,
     pin_brute_force_float,
@@ -252,4 +334,9 @@ ALL_PINS = [
     pin_point_source_statistics,
     pin_int32_bound,
     pin_adjoint_finite_differences,
+    pin_fengine_numpy_fft,
+    pin_fengine_tone,
+    pin_fengine_parseval,
+    pin_fengine_delta_layout,
+    pin_fengine_fx_tone,
 ]

@@ -26,6 +26,12 @@ MUTANTS = [
     ("adjoint_no_hermitian_part", "H[(b * n + a) * 2 + 1] -= go[1];", "H[(b * n + a) * 2 + 1] += go[1];", 0),
     ("adjoint_grad_x_no_conj", "gx[1] = gr * gyi - gi * gyr;", "gx[1] = gr * gyi + gi * gyr;", 0),
     ("adjoint_grad_g_conj", "+= x[0] * gyi - x[1] * gyr;", "+= x[0] * gyi + x[1] * gyr;", 0),
+    ("fengine_exponent_sign", "wi[j] = -sin(", "wi[j] = sin(", 0),
+    ("fengine_block_offset", "in + (a * T * F + t * F) * 2", "in + (a * T * F + t) * 2", 0),
+    ("fengine_dropped_scale", "out[(o * n + a) * 2] = scale * re;", "out[(o * n + a) * 2] = re;", 0),
+    ("fengine_station_pol_swapped", "in + (a * T * F + t * F) * 2",
+     "in + (((a % P) * N + a / P) * T * F + t * F) * 2", 0),
+    ("fengine_phase_index", "const int64_t j = (f * m) % F;", "const int64_t j = (f + m) % F;", 0),
 ]
 
 
@@ -49,7 +55,7 @@ def test_pins_catch_mutant(name, old, new, nth, tmp_path):
     src.write_text(mutated)
     so = tmp_path / ("liboracle_%s.so" % name)
     subprocess.run(["gcc", "-O1", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", str(so),
-                    str(src)], check=True)
+                    str(src), "-lm"], check=True)
     lib = oracle.load(str(so))
     caught = []
     for pin in oracle_pins.ALL_PINS:
