@@ -362,6 +362,42 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks):
     eng.close()
     del x4, out
 
+    # F-engine (Sec. 2) at the Large-N shape: 8-bit station streams
+    # [N][P][T F] -> fp16 channels already in the X-engine's layout, then the
+    # FX chain (F-engine + fp16 X-engine).  The 1 GB of Large-N int8 sky data
+    # is read as the streams (the transform's cost does not depend on values).
+    w = synth.LARGE_N
+    F = w.nfreq
+    xs8 = synth.large_n_input(w, 0, device=dev).view(w.nstation, w.npol, w.ntime * F, 2)
+    X16 = torch.empty((w.ntime, F, w.nstation, w.npol, 2), dtype=torch.float16, device=dev)
+    scale = 1.0 / F ** 0.5
+    xc.channelize(xs8, F, scale, "float16", out=X16, stream=stream)
+    ms_f = timed(lambda: xc.channelize(xs8, F, scale, "float16", out=X16, stream=stream), k) / k
+    nbytes = xs8.numel() * xs8.element_size() + X16.numel() * X16.element_size()
+    ntrans = w.nstation * w.npol * w.ntime
+    eng = xc.Correlator(w.nstation, w.npol, F, w.ntime, "float16")
+    out = eng.new_output()
+    eng.correlate(X16, out=out, stream=stream)
+    eng.synchronize(stream)
+
+    def fx():
+        xc.channelize(xs8, F, scale, "float16", out=X16, stream=stream)
+        eng.correlate(X16, out=out, stream=stream)
+
+    ms_fx = timed(fx, k) / k
+    eng.synchronize(stream)
+    eng.close()
+    res["fengine"] = {
+        "workload": "F-engine: N=256 x 2 pols, 8-bit streams of 1000 blocks x 1024 samples -> "
+                    "fp16 [T][F][N][P] (corner-turned), scale 1/sqrt(F)",
+        "ms": ms_f, "bytes": nbytes, "gbs": nbytes / (ms_f * 1e-3) / 1e9,
+        "frac_of_hbm": nbytes / (ms_f * 1e-3) / 1e9 / peaks["hbm_gbs"],
+        "peak": "%s GB/s (measured HBM copy)" % peaks["hbm_gbs"],
+        "fft_gflops": 5.0 * F * (F.bit_length() - 1) * ntrans / (ms_f * 1e-3) / 1e9,
+        "fx_chain": {"ms": ms_fx, "x_engine": "planar fp16 (float16 input)",
+                     "useful_tops": w.useful_ops / (ms_fx * 1e-3) / 1e12}}
+    del xs8, X16, out
+
     # Batched workload: six subarrays in one persistent launch (graph replay).
     subs = [(b.nstation, b.nfreq, b.ntime) for b in synth.BATCHED]
     xs = [synth.int8_sky(b, device=dev) for b in synth.BATCHED]

@@ -303,6 +303,34 @@ xc_status xc_correlate_noalloc(int nstation, int npol, int nfreq, int ntime, xc_
                                const void* in, void* out, int* status, void* stream);
 
 /*
+ * F-engine (Sec. 2, the FX correlator): channelises each station's signal by
+ * Fourier transforming blocks of nchan consecutive complex samples, and
+ * writes the result corner-turned, in exactly the input layout xc_correlate
+ * takes (station fastest, then channel, then block; Sec. 4.1), so the two
+ * calls chain on one stream with no reordering in between:
+ *
+ *   out[t][f][s][p] = scale * sum_{m < nchan} in[s][p][t nchan + m] exp(-2 pi i f m / nchan)
+ *
+ *   in:  device, [nstation][npol][nblock * nchan] complex samples ({re, im}
+ *        interleaved) of in_dtype (XC_CI8, XC_CF16 or XC_CF32): each station
+ *        and polarisation's sample stream, contiguous in time.
+ *   out: device, [nblock][nchan][nstation][npol] complex of out_dtype
+ *        (XC_CF16 or XC_CF32); it is xc_correlate's input for
+ *        nfreq = nchan, ntime = nblock.
+ *   nchan: a power of two from 16 to 4096 (else XC_ERR_UNSUPPORTED); channel
+ *        f is DFT bin f (DC first, not re-centred).
+ *   scale: real factor on every output.  The paper leaves the normalisation
+ *        open; 1/sqrt(nchan) keeps the transform unitary, and with fp16
+ *        output it keeps 8-bit input in range (|out| <= 128 sqrt(2 nchan)).
+ *   stream: cudaStream_t as void*; stream-ordered, returns once queued.
+ * Buffers are caller-owned and 16-byte aligned (XC_ERR_ALIGNMENT); NULL or
+ * sizes <= 0 give XC_ERR_INVALID_ARG.  Arithmetic is fp32 throughout
+ * (radix-16 FFT), about 1e-6 relative before the output rounding.
+ */
+xc_status xc_channelize(const void* in, xc_dtype in_dtype, int nstation, int npol, int nchan,
+                        int nblock, float scale, void* out, xc_dtype out_dtype, void* stream);
+
+/*
  * Batched form: many subarrays of uneven size correlated by ONE persistent
  * tensor-core launch (Sec. 4.2's channel-major block raster continued from
  * one subarray to the next), replayed from a CUDA graph captured on first

@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libxc.so")
 
-SOURCES = ["xc_api.cpp", "xc_form.cu", "xc_tc.cu", "xc_fp32.cu", "xc_noalloc.cu", "xc_xengine.cu", "xc_xengine2.cu", "xc_planar.cu", "xc_adjoint.cu", "xc_adjoint_tc.cu"]
+SOURCES = ["xc_api.cpp", "xc_form.cu", "xc_tc.cu", "xc_fp32.cu", "xc_noalloc.cu", "xc_xengine.cu", "xc_xengine2.cu", "xc_planar.cu", "xc_adjoint.cu", "xc_adjoint_tc.cu", "xc_fengine.cu"]
 HEADERS = ["xc_internal.h", "xc_launch.h", "xc_ptx.cuh", "xc_convert.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

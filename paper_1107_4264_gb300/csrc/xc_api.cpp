@@ -826,6 +826,41 @@ xc_status xc_correlate_stream(xc_handle* h, const void* host_in, int n_integrati
   return succeed();
 }
 
+// -------------------------------------------------------------- F-engine
+
+xc_status xc_channelize(const void* in, xc_dtype in_dtype, int nstation, int npol, int nchan,
+                        int nblock, float scale, void* out, xc_dtype out_dtype, void* stream) {
+  if (!in || !out) return fail(XC_ERR_INVALID_ARG, "NULL buffer");
+  if (nstation <= 0 || nblock <= 0 || (npol != 1 && npol != 2))
+    return fail(XC_ERR_INVALID_ARG, "bad sizes (nstation=%d npol=%d nblock=%d)", nstation, npol,
+                nblock);
+  if (in_dtype != XC_CI8 && in_dtype != XC_CF16 && in_dtype != XC_CF32)
+    return fail(XC_ERR_INVALID_ARG, "unknown input type %d", static_cast<int>(in_dtype));
+  if (out_dtype != XC_CF16 && out_dtype != XC_CF32)
+    return fail(XC_ERR_INVALID_ARG, "output type must be XC_CF16 or XC_CF32");
+  if (nchan < 16 || nchan > 4096 || (nchan & (nchan - 1)) != 0)
+    return fail(XC_ERR_UNSUPPORTED, "nchan=%d: powers of two from 16 to 4096 are supported", nchan);
+  const int64_t n = static_cast<int64_t>(nstation) * npol;
+  if (n > (1LL << 24) || static_cast<int64_t>(nblock) * nchan > (1LL << 36) / n)
+    return fail(XC_ERR_UNSUPPORTED, "problem too large");
+  if (!aligned16(in) || !aligned16(out)) return fail(XC_ERR_ALIGNMENT, "buffers must be 16-byte aligned");
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(XC_ERR_NO_DEVICE, "no usable CUDA device");
+  }
+  if (!(major == 10 && minor == 3))
+    return fail(XC_ERR_NO_DEVICE, "device %d is sm_%d%d; this library is built for sm_103a only", dev,
+                major, minor);
+  cudaError_t e = xc::launch_fengine(in, static_cast<int>(in_dtype), out, static_cast<int>(out_dtype),
+                                     static_cast<int>(n), nchan, nblock, scale,
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "F-engine launch");
+  return succeed();
+}
+
 // ------------------------------------------------------------------ batch
 
 }  // extern "C"

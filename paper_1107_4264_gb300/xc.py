@@ -41,7 +41,7 @@ EXPORTS = [
     "xc_last_error_message", "xc_status_string", "xc_set_option", "xc_synchronize",
     "xc_correlate_stream", "xc_input_bytes", "xc_output_bytes", "xc_tri_index", "xc_tri_coords",
     "xc_version", "xc_kernel_times", "xc_correlate_noalloc", "xc_set_gains", "xc_get_grad_gains",
-    "xc_batch_create", "xc_batch_correlate", "xc_batch_tune",
+    "xc_batch_create", "xc_batch_correlate", "xc_batch_tune", "xc_channelize",
 ]
 
 _lib: Optional[ctypes.CDLL] = None
@@ -81,6 +81,7 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "xc_batch_correlate": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i32),
         "xc_batch_tune": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, i32,
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)], i32),
+        "xc_channelize": ([vp, i32, i32, i32, i32, i32, ctypes.c_float, vp, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -203,6 +204,12 @@ def xc_correlate_noalloc(nstation: int, npol: int, nfreq: int, ntime: int, in_dt
                                        status_ptr or None, stream)
 
 
+def xc_channelize(in_ptr: int, in_dtype: int, nstation: int, npol: int, nchan: int, nblock: int,
+                  scale: float, out_ptr: int, out_dtype: int, stream: int = 0) -> int:
+    return load().xc_channelize(in_ptr, in_dtype, nstation, npol, nchan, nblock, scale, out_ptr,
+                                out_dtype, stream)
+
+
 def xc_version() -> str:
     return load().xc_version().decode()
 
@@ -322,6 +329,32 @@ class Correlator:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ F-engine
+
+
+def channelize(x, nchan: int, scale: float = 1.0, out_dtype: str = "float16", out=None,
+               stream=None):
+    """F-engine: ``x[N][P][T*nchan][2]`` (int8, float16 or float32 on the GPU,
+    each station's complex stream) -> ``[T][nchan][N][P][2]`` of ``out_dtype``,
+    the DFT of every block of nchan samples times ``scale``, already in
+    :class:`Correlator`'s input layout.  Stream-ordered (current stream by
+    default); raises XcError on a bad argument."""
+    import torch
+    assert x.is_cuda and x.is_contiguous() and x.dim() == 4 and x.shape[-1] == 2
+    N, P, L, _ = x.shape
+    if L % nchan:
+        raise ValueError("samples per stream (%d) not a multiple of nchan (%d)" % (L, nchan))
+    T = L // nchan
+    odt = {"float16": torch.float16, "float32": torch.float32}[out_dtype]
+    if out is None:
+        out = torch.empty((T, nchan, N, P, 2), dtype=odt, device=x.device)
+    assert out.is_contiguous() and out.dtype == odt and tuple(out.shape) == (T, nchan, N, P, 2)
+    s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    _check(xc_channelize(x.data_ptr(), _DTYPES[str(x.dtype).replace("torch.", "")], N, P, nchan, T,
+                         float(scale), out.data_ptr(), _DTYPES[out_dtype], s))
+    return out
 
 
 # ------------------------------------------------------------ autograd

@@ -1,0 +1,140 @@
+"""GPU parity of the F-engine (Sec. 2): xc_channelize against the oracle's
+DFT definition, through the C ABI.
+
+Cases span every pass structure of the radix-16 kernel (log2 nchan = 4 .. 12:
+radix-16 passes only, or with a radix-2/4/8 last pass), station counts below,
+at and above the transforms one CTA holds (8192 / nchan), both polarisation
+counts, every input type and both output types.  fp32 output must agree with
+the FP64 oracle to 2e-6 (Frobenius, relative) and 1e-5 of the largest bin;
+fp16 output to 1e-3 (its rounding is 2^-11 relative).  At the Large-N size
+(N=256 x 2 pols, 1024 channels, 1000 blocks) sampled (block, channel)
+outputs are checked one by one.  The FX chain (F-engine into the X-engine)
+is checked against the oracle's F-engine followed by its X-engine."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1107_4264_gb300 import build as engine_build
+from paper_1107_4264_gb300 import synth, xc
+
+pytestmark = pytest.mark.gpu
+
+TORCH_DT = {"int8": torch.int8, "float16": torch.float16, "float32": torch.float32}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    engine_build.build()
+    xc.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch.device("cuda:0")
+
+
+def streams(N, P, L, dtype, seed):
+    """Station-major complex streams [N][P][L][2]: uniform int8 in [-128, 127],
+    or Gaussian float (sigma 3) rounded to the storage type."""
+    if dtype == "int8":
+        return synth.uniform_int8((N, P, L, 2), -128, 127, seed)
+    g = torch.Generator().manual_seed(seed)
+    return (3.0 * torch.randn((N, P, L, 2), generator=g)).to(TORCH_DT[dtype])
+
+
+def rel_errors(got, want):
+    d = got - want
+    frob = np.linalg.norm(d) / np.linalg.norm(want)
+    return frob, np.abs(d).max() / np.abs(want).max()
+
+
+# (N, P, nchan, nblock, input type, output type)
+CASES = [
+    (3, 2, 16, 5, "int8", "float32"),
+    (5, 1, 32, 3, "float32", "float32"),
+    (70, 2, 64, 2, "float16", "float32"),
+    (33, 2, 128, 2, "int8", "float16"),
+    (17, 2, 256, 3, "float32", "float16"),
+    (9, 2, 512, 2, "int8", "float32"),
+    (9, 2, 1024, 2, "float32", "float32"),
+    (3, 1, 2048, 2, "float16", "float16"),
+    (4, 2, 4096, 2, "int8", "float32"),
+    (1, 1, 2048, 3, "float32", "float32"),
+]
+
+
+@pytest.mark.parametrize("N,P,F,T,idt,odt", CASES,
+                         ids=["N%d_P%d_F%d_T%d_%s_%s" % c for c in CASES])
+def test_channelize_matches_oracle(N, P, F, T, idt, odt, dev):
+    x = streams(N, P, T * F, idt, 70 + N + F)
+    scale = 1.0 / np.sqrt(F)
+    got = xc.channelize(x.to(dev), F, scale, odt).cpu().double().numpy()
+    want = oracle.channelize_f64(x.double().numpy(), F, scale)
+    frob, mx = rel_errors(got, want)
+    print(f"\nF={F} {idt}->{odt}: frobenius {frob:.2e} max {mx:.2e}")
+    if odt == "float32":
+        assert frob <= 2e-6 and mx <= 1e-5, (frob, mx)
+    else:
+        assert frob <= 1e-3 and mx <= 1e-3, (frob, mx)
+
+
+def test_channelize_tone_lands_in_one_bin(dev):
+    N, P, F, T, k0 = 4, 2, 1024, 3, 37
+    tau = torch.arange(T * F, dtype=torch.float64)
+    ph = 2 * np.pi * k0 * tau / F
+    amp = torch.arange(1, N * P + 1, dtype=torch.float64).reshape(N, P, 1)
+    x = torch.stack([amp * torch.cos(ph), amp * torch.sin(ph)], dim=-1).float().contiguous()
+    X = xc.channelize(x.to(dev), F, 1.0, "float32").cpu().double().numpy()
+    mag = np.hypot(X[..., 0], X[..., 1])                       # [T][F][N][P]
+    np.testing.assert_allclose(mag[:, k0], np.broadcast_to(F * amp.numpy()[None, :, :, 0], mag[:, k0].shape),
+                               rtol=2e-6)
+    others = np.delete(mag, k0, axis=1)
+    assert others.max() < 1e-5 * mag[:, k0].max()
+
+
+def test_channelize_large_n_sampled(dev):
+    N, P, F, T = 256, 2, 1024, 1000
+    x = synth.uniform_int8((N, P, T * F, 2), -128, 127, 71, device=dev)
+    scale = 1.0 / np.sqrt(F)
+    X = xc.channelize(x, F, scale, "float16")
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(72)
+    for t in (0, 517, T - 1):
+        chans = sorted(set(rng.integers(0, F, 6).tolist()) | {0, F - 1})
+        xt = x[:, :, t * F:(t + 1) * F].cpu().double().numpy()
+        want = oracle.channelize_f64(xt, F, scale, sel=[(0, f) for f in chans])
+        got = X[t, chans].cpu().double().numpy()
+        frob, mx = rel_errors(got, want)
+        assert frob <= 1e-3 and mx <= 1e-3, (t, frob, mx)
+
+
+def test_fx_chain_matches_oracle(dev):
+    """F-engine then X-engine on the GPU against the oracle's F-engine then
+    its X-engine: sky-like streams (common sources plus noise per station)."""
+    N, P, F, T = 24, 2, 64, 40
+    g = torch.Generator().manual_seed(73)
+    common = torch.randn((T * F, 2), generator=g)
+    x = (torch.randn((N, P, T * F, 2), generator=g) + 0.5 * common).mul(4).round().clamp(-127, 127)
+    x = x.to(torch.int8).contiguous()
+    scale = 1.0 / np.sqrt(F)
+    eng = xc.Correlator(N, P, F, T, "float16")
+    try:
+        X = xc.channelize(x.to(dev), F, scale, "float16")
+        got = eng.correlate(X, sync=True).cpu().double().numpy()
+    finally:
+        eng.close()
+    Xo = oracle.channelize_f64(x.double().numpy(), F, scale)
+    want = oracle.correlate_f64(Xo)
+    frob, _ = rel_errors(got, want)
+    assert frob <= 2e-3, frob
+
+
+def test_channelize_argument_errors(dev):
+    x = torch.zeros((2, 2, 96, 2), dtype=torch.int8, device=dev)
+    with pytest.raises(xc.XcError) as e:
+        xc.channelize(x, 48)  # not a power of two
+    assert "XC_ERR_UNSUPPORTED" in str(e.value)
+    out = torch.empty((1, 16 * 6 + 1), dtype=torch.float32, device=dev)
+    st = xc.xc_channelize(x.data_ptr(), xc.XC_CI8, 2, 2, 16, 6, 1.0, out.data_ptr() + 4,
+                          xc.XC_CF32, 0)
+    assert st == xc.XC_ERR_ALIGNMENT
+    assert xc.xc_channelize(x.data_ptr(), xc.XC_CI8, 0, 2, 16, 6, 1.0, out.data_ptr(),
+                            xc.XC_CF32, 0) == xc.XC_ERR_INVALID_ARG
