@@ -65,6 +65,11 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision, batched and differentiable workloads")
     ap.add_argument("--form-steps", type=int, default=5)
+    ap.add_argument("--fengine", action="store_true",
+                    help="instead of the bench line: the F-engine alone at the Large-N shape "
+                         "(N=256 x 2 pols, 1024 channels), fp16 and fp32 output, one JSON object")
+    ap.add_argument("--fengine-blocks", type=int, default=1000,
+                    help="blocks (samples per stream / 1024) for --fengine (smaller for profiling)")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the bench line: kernel TOPS over N (fixed work) and over T at "
                          "fixed F*T (output traffic), one JSON object")
@@ -700,12 +705,51 @@ def run_xc(args):
     return 0
 
 
+def run_fengine(args):
+    """F-engine alone: N=256 x 2 pols of 8-bit station streams, 1024 channels,
+    --fengine-blocks blocks, into fp16 and into fp32 (corner-turned), timed
+    with CUDA events over --steps calls after --warmup."""
+    import torch
+
+    from paper_1107_4264_gb300 import build as engine_build
+    from paper_1107_4264_gb300 import synth, xc
+
+    engine_build.build()
+    xc.load()
+    dev = torch.device("cuda")
+    N, P, F, T = 256, 2, 1024, args.fengine_blocks
+    x = synth.uniform_int8((N, P, T * F, 2), -128, 127, 4242, device=dev)
+    peaks, kind = load_peaks()
+    res = {"fengine": "N=%d x %d pols, %d channels, %d blocks, 8-bit streams" % (N, P, F, T)}
+    for odt in ("float16", "float32"):
+        out = torch.empty((T, F, N, P, 2), dtype=getattr(torch, odt), device=dev)
+        for _ in range(max(args.warmup, 1)):
+            xc.channelize(x, F, 1.0 / 32, odt, out=out)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            xc.channelize(x, F, 1.0 / 32, odt, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        nbytes = x.numel() + out.numel() * out.element_size()
+        res[odt] = {"ms": ms, "gbs": nbytes / ms / 1e6,
+                    "frac_of_hbm": nbytes / ms / 1e6 / peaks["hbm_gbs"], "peak_kind": kind}
+        del out
+    print(json.dumps(res))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.fengine:
+        return run_fengine(args)
     return run_xc(args)
 
 
