@@ -67,7 +67,7 @@ def parse_args():
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--fengine", action="store_true",
                     help="instead of the bench line: the F-engine alone at the Large-N shape "
-                         "(N=256 x 2 pols, 1024 channels), fp16 and fp32 output, one JSON object")
+                         "(N=256 x 2 pols, 1024 channels), fp16, fp32 and 8-bit output, one JSON object")
     ap.add_argument("--fengine-blocks", type=int, default=1000,
                     help="blocks (samples per stream / 1024) for --fengine (smaller for profiling)")
     ap.add_argument("--sweep", action="store_true",
@@ -392,6 +392,25 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks):
     ms_fx = timed(fx, k) / k
     eng.synchronize(stream)
     eng.close()
+    # The same chain with the F-engine output requantised to 8 bits (scale
+    # 2/sqrt(F): rms about 6 codes on this data) into the exact 8-bit X-engine.
+    del X16
+    X8 = torch.empty((w.ntime, F, w.nstation, w.npol, 2), dtype=torch.int8, device=dev)
+    eng8 = xc.Correlator(w.nstation, w.npol, F, w.ntime, "int8")
+    out8 = eng8.new_output()
+    scale8 = 2.0 / F ** 0.5
+
+    def fx8():
+        xc.channelize(xs8, F, scale8, "int8", out=X8, stream=stream)
+        eng8.correlate(X8, out=out8, stream=stream)
+
+    fx8()
+    eng8.synchronize(stream)
+    ms_f8 = timed(lambda: xc.channelize(xs8, F, scale8, "int8", out=X8, stream=stream), k) / k
+    ms_fx8 = timed(fx8, k) / k
+    eng8.synchronize(stream)
+    eng8.close()
+    del X8, out8
     res["fengine"] = {
         "workload": "F-engine: N=256 x 2 pols, 8-bit streams of 1000 blocks x 1024 samples -> "
                     "fp16 [T][F][N][P] (corner-turned), scale 1/sqrt(F)",
@@ -400,8 +419,11 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks):
         "peak": "%s GB/s (measured HBM copy)" % peaks["hbm_gbs"],
         "fft_gflops": 5.0 * F * (F.bit_length() - 1) * ntrans / (ms_f * 1e-3) / 1e9,
         "fx_chain": {"ms": ms_fx, "x_engine": "planar fp16 (float16 input)",
-                     "useful_tops": w.useful_ops / (ms_fx * 1e-3) / 1e12}}
-    del xs8, X16, out
+                     "useful_tops": w.useful_ops / (ms_fx * 1e-3) / 1e12},
+        "fengine_int8_out_ms": ms_f8,
+        "fx_chain_int8": {"ms": ms_fx8, "x_engine": "planar int8 (exact), F-engine requantised to 8 bits",
+                          "useful_tops": w.useful_ops / (ms_fx8 * 1e-3) / 1e12}}
+    del xs8, out
 
     # Batched workload: six subarrays in one persistent launch (graph replay).
     subs = [(b.nstation, b.nfreq, b.ntime) for b in synth.BATCHED]
@@ -707,7 +729,7 @@ def run_xc(args):
 
 def run_fengine(args):
     """F-engine alone: N=256 x 2 pols of 8-bit station streams, 1024 channels,
-    --fengine-blocks blocks, into fp16 and into fp32 (corner-turned), timed
+    --fengine-blocks blocks, into fp16, fp32 and 8-bit codes (corner-turned), timed
     with CUDA events over --steps calls after --warmup."""
     import torch
 
@@ -721,7 +743,7 @@ def run_fengine(args):
     x = synth.uniform_int8((N, P, T * F, 2), -128, 127, 4242, device=dev)
     peaks, kind = load_peaks()
     res = {"fengine": "N=%d x %d pols, %d channels, %d blocks, 8-bit streams" % (N, P, F, T)}
-    for odt in ("float16", "float32"):
+    for odt in ("float16", "float32", "int8"):
         out = torch.empty((T, F, N, P, 2), dtype=getattr(torch, odt), device=dev)
         for _ in range(max(args.warmup, 1)):
             xc.channelize(x, F, 1.0 / 32, odt, out=out)

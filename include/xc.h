@@ -314,9 +314,15 @@ xc_status xc_correlate_noalloc(int nstation, int npol, int nfreq, int ntime, xc_
  *   in:  device, [nstation][npol][nblock * nchan] complex samples ({re, im}
  *        interleaved) of in_dtype (XC_CI8, XC_CF16 or XC_CF32): each station
  *        and polarisation's sample stream, contiguous in time.
- *   out: device, [nblock][nchan][nstation][npol] complex of out_dtype
- *        (XC_CF16 or XC_CF32); it is xc_correlate's input for
- *        nfreq = nchan, ntime = nblock.
+ *   out: device, [nblock][nchan][nstation][npol] complex of out_dtype; it is
+ *        xc_correlate's input for nfreq = nchan, ntime = nblock.
+ *        XC_CF16 / XC_CF32: the value above, rounded to the type.
+ *        XC_CI8: requantised to 8 bits, each component rounded to the nearest
+ *        integer (ties to even) and saturated at +-127, the form the 8-bit
+ *        X-engine correlates exactly (Sec. 5: 8-bit X-engine input).  The
+ *        rounding decision is taken on the fp32 value, so a component within
+ *        about 1e-6 relative of a half-integer may round the other way than
+ *        in exact arithmetic.
  *   nchan: a power of two from 16 to 4096 (else XC_ERR_UNSUPPORTED); channel
  *        f is DFT bin f (DC first, not re-centred).
  *   scale: real factor on every output.  The paper leaves the normalisation

@@ -10,7 +10,9 @@ of Clark, La Plante & Greenhill each function follows:
   ordering of Sec. 4.1;
 * ``backward_f64`` -- the adjoint of the float form (not in the paper);
 * ``channelize_f64`` -- the F-engine of Sec. 2 (blockwise DFT of each
-  station's signal) with the corner turn into the X-engine's input order.
+  station's signal) with the corner turn into the X-engine's input order;
+  ``requantise_i8`` -- its 8-bit requantisation (nearest integer, ties to
+  even, saturated at +-127), the 8-bit X-engine input of Sec. 5.
 
 Arrays use the engine's layouts: input ``[T][F][N][P][2]``, output
 ``[F][N(N+1)/2][P*P][2]``.
@@ -167,3 +169,9 @@ def channelize_f64(x: np.ndarray, nchan: int, scale: float = 1.0,
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     return out if s is not None else out.reshape(T, nchan, N, P, 2)
+
+
+def requantise_i8(X: np.ndarray) -> np.ndarray:
+    """8-bit requantisation of F-engine output: each component rounded to the
+    nearest integer (ties to even) and saturated at +-127, as int8."""
+    return np.clip(np.rint(np.asarray(X, dtype=np.float64)), -127, 127).astype(np.int8)

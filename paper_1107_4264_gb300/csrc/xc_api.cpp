@@ -836,8 +836,8 @@ xc_status xc_channelize(const void* in, xc_dtype in_dtype, int nstation, int npo
                 nblock);
   if (in_dtype != XC_CI8 && in_dtype != XC_CF16 && in_dtype != XC_CF32)
     return fail(XC_ERR_INVALID_ARG, "unknown input type %d", static_cast<int>(in_dtype));
-  if (out_dtype != XC_CF16 && out_dtype != XC_CF32)
-    return fail(XC_ERR_INVALID_ARG, "output type must be XC_CF16 or XC_CF32");
+  if (out_dtype != XC_CI8 && out_dtype != XC_CF16 && out_dtype != XC_CF32)
+    return fail(XC_ERR_INVALID_ARG, "unknown output type %d", static_cast<int>(out_dtype));
   if (nchan < 16 || nchan > 4096 || (nchan & (nchan - 1)) != 0)
     return fail(XC_ERR_UNSUPPORTED, "nchan=%d: powers of two from 16 to 4096 are supported", nchan);
   const int64_t n = static_cast<int64_t>(nstation) * npol;

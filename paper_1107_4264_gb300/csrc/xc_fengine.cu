@@ -6,9 +6,10 @@
 // in the ordering of Sec. 4.1).  Input is station-major [N][P][T F]: the
 // F-engine is independent per station, the X-engine per channel.
 //
-// One CTA transforms G = 8192 / F blocks (G consecutive inputs a = s P + p of
-// one block index t) in shared memory and writes them corner-turned, so each
-// output channel f receives G consecutive inputs in one contiguous run.
+// One CTA transforms G = 8192 / F (or 16384 / F) blocks (G consecutive inputs
+// a = s P + p of one block index t) in shared memory and writes them
+// corner-turned, so each output channel f receives G consecutive inputs in one
+// contiguous run.
 //
 // Each transform is a Stockham radix-16 FFT (a radix-2/4/8 first pass when
 // log2 F is not a multiple of 4, so that only radix-16 passes carry
@@ -32,9 +33,10 @@
 namespace xc {
 namespace {
 
-constexpr int kPts = 16;                      // points per thread per pass
-constexpr int kCtaPoints = 8192;              // G * F per CTA
-constexpr int kFThreads = kCtaPoints / kPts;  // 512
+constexpr int kPts = 16;  // points per thread per pass
+// A CTA holds 2^LOGP points (G = 2^LOGP / F transforms, 2^LOGP / 16 threads):
+// 2^13 with two CTAs per SM, or 2^14 with one, whose longer corner-turn runs
+// (G consecutive inputs per channel) fill whole 32-byte sectors for 8-bit output.
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -130,8 +132,7 @@ __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 // float2 elements between the padded rows of consecutive transforms: at least
 // F + F / 16, congruent mod 16 to 16 / min(G, 16), so that a warp's
 // corner-turn reads (G rows, 32 / G bins each) spread over all banks.
-__host__ __device__ __forceinline__ int row_stride(int F) {
-  const int G = 8192 / F;
+__host__ __device__ __forceinline__ int row_stride(int F, int G) {
   const int target = 16 / (G < 16 ? G : 16);
   const int base = F + F / 16;
   return base + (((target - base) % 16) + 16) % 16;
@@ -215,17 +216,18 @@ __device__ __forceinline__ void later_passes(float2 (&v)[kPts], float2* buf, int
 }
 
 // in [n][T F] complex (in_dt: 0 int8, 1 fp16, 2 fp32), out [T][F][n] complex
-// (out_dt: 1 fp16, 2 fp32), F = 2^LOGF.  grid = (T, ceil(n / G)), block =
-// kFThreads, dynamic shared memory G row_stride(F) float2.
-template <int LOGF>
-__global__ void __launch_bounds__(kFThreads, 2)
+// (out_dt: 0 int8 requantised, 1 fp16, 2 fp32), F = 2^LOGF.  grid = (T, ceil(n / G)), block =
+// 2^LOGP / 16 threads, dynamic shared memory G row_stride(F, G) float2.
+template <int LOGF, int LOGP>
+__global__ void __launch_bounds__((1 << LOGP) / kPts, (1 << 14) >> LOGP)
     fengine_kernel(const void* __restrict__ in, void* __restrict__ out, int n, int T, float scale,
                    int in_dt, int out_dt) {
   constexpr int F = 1 << LOGF;
-  constexpr int G = kCtaPoints / F, LOGG = 13 - LOGF;
+  constexpr int G = (1 << LOGP) / F, LOGG = LOGP - LOGF;
+  constexpr int kFThreads = (1 << LOGP) / kPts;
   constexpr int tpf = F / kPts;
   extern __shared__ float2 fsm[];
-  const int stride = row_stride(F);
+  const int stride = row_stride(F, G);
   const int g = threadIdx.x >> (LOGF - 4);  // transform of this thread within the CTA
   const int j = threadIdx.x & (tpf - 1);
   const int t = blockIdx.x;
@@ -278,34 +280,48 @@ __global__ void __launch_bounds__(kFThreads, 2)
     const int64_t o = o0 + i * ostep;
     if (out_dt == 1) {
       static_cast<__half2*>(out)[o] = __floats2half2_rn(X.x * scale, X.y * scale);
+    } else if (out_dt == 0) {
+      // Requantised to 8 bits: nearest integer (ties to even), saturated at +-127.
+      const int qr = max(-127, min(127, __float2int_rn(X.x * scale)));
+      const int qi = max(-127, min(127, __float2int_rn(X.y * scale)));
+      static_cast<char2*>(out)[o] = make_char2(static_cast<signed char>(qr), static_cast<signed char>(qi));
     } else {
       static_cast<float2*>(out)[o] = make_float2(X.x * scale, X.y * scale);
     }
   }
 }
 
-template <int LOGF>
-cudaError_t launch_f(const void* in, int in_dt, void* out, int out_dt, int n, int T, float scale,
-                     cudaStream_t s) {
-  constexpr int F = 1 << LOGF, G = kCtaPoints / F;
-  const size_t smem = static_cast<size_t>(G) * row_stride(F) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(fengine_kernel<LOGF>,
+template <int LOGF, int LOGP>
+cudaError_t launch_fp(const void* in, int in_dt, void* out, int out_dt, int n, int T, float scale,
+                      cudaStream_t s) {
+  constexpr int F = 1 << LOGF, G = (1 << LOGP) / F;
+  const size_t smem = static_cast<size_t>(G) * row_stride(F, G) * sizeof(float2);
+  if ((n + G - 1) / G > 65535) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(fengine_kernel<LOGF, LOGP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const dim3 grid(static_cast<unsigned>(T), static_cast<unsigned>((n + G - 1) / G));
-  fengine_kernel<LOGF><<<grid, kFThreads, smem, s>>>(in, out, n, T, scale, in_dt, out_dt);
+  fengine_kernel<LOGF, LOGP><<<grid, (1 << LOGP) / kPts, smem, s>>>(in, out, n, T, scale, in_dt,
+                                                                    out_dt);
   return cudaGetLastError();
+}
+
+// CTA size by output type: 8-bit codes (2 bytes per complex value) take the
+// larger CTA, whose corner-turn runs cover whole 32-byte sectors.
+template <int LOGF>
+cudaError_t launch_f(const void* in, int in_dt, void* out, int out_dt, int n, int T, float scale,
+                     cudaStream_t s) {
+  if (out_dt == 0) return launch_fp<LOGF, 14>(in, in_dt, out, out_dt, n, T, scale, s);
+  return launch_fp<LOGF, 13>(in, in_dt, out, out_dt, n, T, scale, s);
 }
 
 }  // namespace
 
 cudaError_t launch_fengine(const void* in, int in_dtype, void* out, int out_dtype, int n, int F,
                            int T, float scale, cudaStream_t s) {
-  if (n <= 0 || T <= 0 || in_dtype < 0 || in_dtype > 2 || (out_dtype != 1 && out_dtype != 2))
+  if (n <= 0 || T <= 0 || in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 2)
     return cudaErrorInvalidValue;
-  if (F >= 16 && (n + kCtaPoints / F - 1) / (kCtaPoints / F) > 65535)
-    return cudaErrorInvalidConfiguration;
   switch (F) {
     case 16: return launch_f<4>(in, in_dtype, out, out_dtype, n, T, scale, s);
     case 32: return launch_f<5>(in, in_dtype, out, out_dtype, n, T, scale, s);

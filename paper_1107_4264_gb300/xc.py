@@ -339,15 +339,16 @@ def channelize(x, nchan: int, scale: float = 1.0, out_dtype: str = "float16", ou
     """F-engine: ``x[N][P][T*nchan][2]`` (int8, float16 or float32 on the GPU,
     each station's complex stream) -> ``[T][nchan][N][P][2]`` of ``out_dtype``,
     the DFT of every block of nchan samples times ``scale``, already in
-    :class:`Correlator`'s input layout.  Stream-ordered (current stream by
-    default); raises XcError on a bad argument."""
+    :class:`Correlator`'s input layout; ``out_dtype="int8"`` requantises each
+    component to the nearest integer, saturated at +-127.  Stream-ordered
+    (current stream by default); raises XcError on a bad argument."""
     import torch
     assert x.is_cuda and x.is_contiguous() and x.dim() == 4 and x.shape[-1] == 2
     N, P, L, _ = x.shape
     if L % nchan:
         raise ValueError("samples per stream (%d) not a multiple of nchan (%d)" % (L, nchan))
     T = L // nchan
-    odt = {"float16": torch.float16, "float32": torch.float32}[out_dtype]
+    odt = {"int8": torch.int8, "float16": torch.float16, "float32": torch.float32}[out_dtype]
     if out is None:
         out = torch.empty((T, nchan, N, P, 2), dtype=odt, device=x.device)
     assert out.is_contiguous() and out.dtype == odt and tuple(out.shape) == (T, nchan, N, P, 2)

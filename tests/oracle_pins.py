@@ -323,6 +323,17 @@ def pin_fengine_fx_tone(lib):
     assert np.abs(V[mask]).max() < 1e-8 * np.abs(V[k0]).max()
 
 
+def pin_requantise_truth_table(lib):
+    """8-bit requantisation: nearest integer with ties to even, saturated at
+    +-127 (both signs), on hand-picked values."""
+    x = np.array([-0.5, 0.5, 1.5, 2.5, -1.5, 126.5, 127.49, 127.5, 200.0, -127.5, -128.0, -300.0,
+                  3.2, -3.7])
+    want = np.array([0, 0, 2, 2, -2, 126, 127, 127, 127, -127, -127, -127, 3, -4], dtype=np.int8)
+    got = oracle.requantise_i8(x)
+    assert got.dtype == np.int8
+    np.testing.assert_array_equal(got, want)
+
+
 ALL_PINS = [
     pin_brute_force_int,
     pin_brute_force_float,
@@ -339,4 +350,5 @@ ALL_PINS = [
     pin_fengine_parseval,
     pin_fengine_delta_layout,
     pin_fengine_fx_tone,
+    pin_requantise_truth_table,
 ]

@@ -9,7 +9,10 @@ the FP64 oracle to 2e-6 (Frobenius, relative) and 1e-5 of the largest bin;
 fp16 output to 1e-3 (its rounding is 2^-11 relative).  At the Large-N size
 (N=256 x 2 pols, 1024 channels, 1000 blocks) sampled (block, channel)
 outputs are checked one by one.  The FX chain (F-engine into the X-engine)
-is checked against the oracle's F-engine followed by its X-engine."""
+is checked against the oracle's F-engine followed by its X-engine.  Output
+requantised to 8 bits must equal the oracle's requantisation except at
+rounding boundaries (within 1e-3 of x.5), where the fp32 kernel may round
+one code the other way; the 8-bit FX chain is then bit-exact on those codes."""
 import numpy as np
 import pytest
 import torch
@@ -125,6 +128,53 @@ def test_fx_chain_matches_oracle(dev):
     want = oracle.correlate_f64(Xo)
     frob, _ = rel_errors(got, want)
     assert frob <= 2e-3, frob
+
+
+def check_requantised(got, Xs, tol=1e-3):
+    """Codes equal the oracle's requantisation of the exact values, except
+    where an exact value lies within tol of a rounding boundary (x.5), where
+    the fp32 kernel may round the other way by one."""
+    want = oracle.requantise_i8(Xs)
+    diff = got.astype(np.int64) - want.astype(np.int64)
+    frac = np.abs(np.abs(Xs - np.floor(Xs)) - 0.5)
+    bad = (diff != 0) & ~((np.abs(diff) == 1) & (frac < tol))
+    assert not bad.any(), (int(bad.sum()), Xs[bad][:5], got[bad][:5], want[bad][:5])
+    return int((diff != 0).sum())
+
+
+@pytest.mark.parametrize("F,idt", [(256, "int8"), (1024, "float32"), (64, "float16")])
+def test_channelize_requantised_int8(F, idt, dev):
+    N, P, T = 8, 2, 6
+    x = streams(N, P, T * F, idt, 80 + F)
+    scale = 0.5 / np.sqrt(F)  # output rms about 37 for int8 input: some components saturate
+    if idt != "int8":
+        scale *= 74.0 / 3.0
+    got = xc.channelize(x.to(dev), F, scale, "int8").cpu().numpy()
+    Xs = oracle.channelize_f64(x.double().numpy(), F, scale)
+    flips = check_requantised(got, Xs)
+    assert np.abs(Xs).max() > 127  # saturation exercised
+    print(f"\nF={F} {idt}->int8: {flips} boundary flips of {got.size}")
+
+
+def test_fx_chain_int8_is_exact_on_the_codes(dev):
+    """F-engine requantised to 8 bits, then the exact 8-bit X-engine: the
+    visibilities equal the oracle's X-engine on the same codes bit for bit,
+    and the codes are the oracle's requantisation up to boundary flips."""
+    N, P, F, T = 20, 2, 128, 30
+    g = torch.Generator().manual_seed(81)
+    common = torch.randn((T * F, 2), generator=g)
+    x = (torch.randn((N, P, T * F, 2), generator=g) + 0.5 * common).mul(4).round().clamp(-127, 127)
+    x = x.to(torch.int8).contiguous()
+    scale = 2.0 / np.sqrt(F)
+    eng = xc.Correlator(N, P, F, T, "int8")
+    try:
+        codes = xc.channelize(x.to(dev), F, scale, "int8")
+        vis = eng.correlate(codes, sync=True).cpu().numpy()
+    finally:
+        eng.close()
+    codes = codes.cpu().numpy()
+    np.testing.assert_array_equal(vis, oracle.correlate_i8(codes))
+    check_requantised(codes, oracle.channelize_f64(x.double().numpy(), F, scale))
 
 
 def test_channelize_argument_errors(dev):
