@@ -12,7 +12,9 @@ of Clark, La Plante & Greenhill each function follows:
 * ``channelize_f64`` -- the F-engine of Sec. 2 (blockwise DFT of each
   station's signal) with the corner turn into the X-engine's input order;
   ``requantise_i8`` -- its 8-bit requantisation (nearest integer, ties to
-  even, saturated at +-127), the 8-bit X-engine input of Sec. 5.
+  even, saturated at +-127), the 8-bit X-engine input of Sec. 5;
+  ``channelize_pfb_f64`` -- the same with a polyphase front end (taps
+  h[p][m] over ntaps consecutive blocks; not in the paper).
 
 Arrays use the engine's layouts: input ``[T][F][N][P][2]``, output
 ``[F][N(N+1)/2][P*P][2]``.
@@ -63,6 +65,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.xco_backward_f64.restype = i32
     lib.xco_channelize_f64.argtypes = [vp, i32, i32, i32, i32, ctypes.c_double, vp, i32, vp]
     lib.xco_channelize_f64.restype = i32
+    lib.xco_channelize_pfb_f64.argtypes = [vp, i32, i32, i32, i32, vp, i32, ctypes.c_double, vp]
+    lib.xco_channelize_pfb_f64.restype = i32
     return lib
 
 
@@ -175,3 +179,22 @@ def requantise_i8(X: np.ndarray) -> np.ndarray:
     """8-bit requantisation of F-engine output: each component rounded to the
     nearest integer (ties to even) and saturated at +-127, as int8."""
     return np.clip(np.rint(np.asarray(X, dtype=np.float64)), -127, 127).astype(np.int8)
+
+
+def channelize_pfb_f64(x: np.ndarray, taps: np.ndarray, scale: float = 1.0,
+                       lib: Optional[ctypes.CDLL] = None) -> np.ndarray:
+    """Polyphase F-engine: ``taps[ntaps][nchan]`` real, ``x[N][P][T*nchan][2]``
+    -> ``X[T-ntaps+1][nchan][N][P][2]`` with ``X[t][f] = scale * sum_m
+    exp(-2 pi i f m / nchan) sum_p taps[p][m] x[(t+p)*nchan + m]``."""
+    lib = lib or load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    h = np.ascontiguousarray(taps, dtype=np.float64)
+    N, P, L, two = x.shape
+    ntaps, F = h.shape
+    assert two == 2 and L % F == 0
+    T = L // F
+    out = np.zeros((T - ntaps + 1, F, N, P, 2), dtype=np.float64)
+    rc = lib.xco_channelize_pfb_f64(_ptr(x), N, P, F, T, _ptr(h), ntaps, float(scale), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    return out

@@ -44,7 +44,10 @@
  * (station fastest, then channel, then block; Sec. 4.1).  Readings: the
  * transform carries a caller-given real factor `scale` (the paper leaves the
  * normalisation open); channel f is the f-th DFT bin (DC first), not
- * re-centred.
+ * re-centred.  The optional polyphase front end (not in the paper; the usual
+ * F-engine filter) weights ntaps consecutive blocks with caller-given taps
+ * h[p][m] and sums them before the DFT:
+ *   y_t(m) = sum_{p<ntaps} h[p][m] x((t + p) F + m),   t < T - ntaps + 1.
  *
  * Every function follows the definition with plain loops in the order
  * channel -> baseline -> polarisation pair -> time; OpenMP only splits the
@@ -327,4 +330,52 @@ int xco_channelize_f64(const double* in, int N, int P, int F, int T, double scal
   free(wr);
   free(wi);
   return bad ? -1 : 0;
+}
+
+/*
+ * Polyphase F-engine: the DFT definition applied to the tap-weighted sum of
+ * ntaps consecutive blocks, y_t(m) = sum_p h[p F + m] x((t + p) F + m), for
+ * the T - ntaps + 1 output blocks; h is [ntaps][F] real.  Same layouts as
+ * xco_channelize_f64, out [T - ntaps + 1][F][N][P][2].
+ */
+int xco_channelize_pfb_f64(const double* in, int N, int P, int F, int T, const double* h,
+                           int ntaps, double scale, double* out) {
+  if (N <= 0 || P <= 0 || F <= 0 || ntaps <= 0 || T < ntaps || !h) return -1;
+  const int64_t n = (int64_t)N * P;
+  const int64_t Tout = (int64_t)T - ntaps + 1;
+  double* wr = (double*)malloc((size_t)F * sizeof(double));
+  double* wi = (double*)malloc((size_t)F * sizeof(double));
+  if (!wr || !wi) {
+    free(wr);
+    free(wi);
+    return -1;
+  }
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int j = 0; j < F; ++j) {
+    wr[j] = cos(two_pi * (double)j / (double)F);
+    wi[j] = -sin(two_pi * (double)j / (double)F);
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t o = 0; o < Tout * F; ++o) {
+    const int64_t t = o / F, f = o % F;
+    for (int64_t a = 0; a < n; ++a) {
+      double re = 0.0, im = 0.0;
+      for (int64_t m = 0; m < F; ++m) {
+        double yr = 0.0, yi = 0.0;
+        for (int p = 0; p < ntaps; ++p) {
+          const double* x = in + (a * T * F + (t + p) * F + m) * 2;
+          yr += h[(int64_t)p * F + m] * x[0];
+          yi += h[(int64_t)p * F + m] * x[1];
+        }
+        const int64_t j = (f * m) % F;
+        re += yr * wr[j] - yi * wi[j];
+        im += yr * wi[j] + yi * wr[j];
+      }
+      out[(o * n + a) * 2] = scale * re;
+      out[(o * n + a) * 2 + 1] = scale * im;
+    }
+  }
+  free(wr);
+  free(wi);
+  return 0;
 }

@@ -334,6 +334,52 @@ def pin_requantise_truth_table(lib):
     np.testing.assert_array_equal(got, want)
 
 
+def pin_pfb_single_unit_tap_is_dft(lib):
+    """One tap of ones: the polyphase F-engine is the plain blockwise DFT."""
+    rng = np.random.default_rng(35)
+    N, P, F, T = 2, 2, 16, 3
+    x = rng.standard_normal((N, P, T * F, 2))
+    got = oracle.channelize_pfb_f64(x, np.ones((1, F)), 0.5, lib=lib)
+    ref = np.fft.fft(_fx(x).reshape(N, P, T, F), axis=-1) * 0.5
+    np.testing.assert_allclose(_cx(got), np.transpose(ref, (2, 3, 0, 1)), rtol=0, atol=1e-11)
+
+
+def pin_pfb_delta_taps(lib):
+    """A unit sample at tau0 = b0 F + m0 reaches output block t = b0 - p through
+    tap p only: X_t(f) = scale h[p][m0] exp(-2 pi i f m0 / F), every other
+    block, station and pol zero."""
+    rng = np.random.default_rng(36)
+    N, P, F, T, ntaps, scale = 2, 2, 8, 6, 3, 1.5
+    h = rng.standard_normal((ntaps, F))
+    s0, p0, b0, m0 = 1, 0, 3, 5
+    x = np.zeros((N, P, T * F, 2))
+    x[s0, p0, b0 * F + m0, 0] = 1.0
+    got = _cx(oracle.channelize_pfb_f64(x, h, scale, lib=lib))  # [T-ntaps+1][F][N][P]
+    want = np.zeros_like(got)
+    ramp = np.exp(-2j * np.pi * np.arange(F) * m0 / F)
+    for p in range(ntaps):
+        t = b0 - p
+        if 0 <= t < T - ntaps + 1:
+            want[t, :, s0, p0] = scale * h[p, m0] * ramp
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+def pin_pfb_tone_response(lib):
+    """A bin-centred tone exp(2 pi i k0 tau / F) through taps h gives, in every
+    output block, scale * DFT(H)[f - k0] with H[m] = sum_p h[p][m] (numpy FFT)."""
+    rng = np.random.default_rng(37)
+    N, P, F, T, ntaps, k0, scale = 1, 2, 32, 7, 4, 9, 0.25
+    h = rng.standard_normal((ntaps, F))
+    tau = np.arange(T * F)
+    z = np.broadcast_to(np.exp(2j * np.pi * k0 * tau / F), (N, P, T * F))
+    x = np.stack([z.real, z.imag], axis=-1)
+    got = _cx(oracle.channelize_pfb_f64(x, h, scale, lib=lib))
+    Hf = np.fft.fft(h.sum(axis=0))
+    want = scale * Hf[(np.arange(F) - k0) % F]
+    np.testing.assert_allclose(got, np.broadcast_to(want[None, :, None, None], got.shape),
+                               rtol=0, atol=1e-10)
+
+
 ALL_PINS = [
     pin_brute_force_int,
     pin_brute_force_float,
@@ -351,4 +397,7 @@ ALL_PINS = [
     pin_fengine_delta_layout,
     pin_fengine_fx_tone,
     pin_requantise_truth_table,
+    pin_pfb_single_unit_tap_is_dft,
+    pin_pfb_delta_taps,
+    pin_pfb_tone_response,
 ]

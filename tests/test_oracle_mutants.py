@@ -32,6 +32,9 @@ MUTANTS = [
     ("fengine_station_pol_swapped", "in + (a * T * F + t * F) * 2",
      "in + (((a % P) * N + a / P) * T * F + t * F) * 2", 0),
     ("fengine_phase_index", "const int64_t j = (f * m) % F;", "const int64_t j = (f + m) % F;", 0),
+    ("pfb_time_direction", "(t + p) * F + m) * 2;", "(t + ntaps - 1 - p) * F + m) * 2;", 0),
+    ("pfb_tap_index", "yr += h[(int64_t)p * F + m] * x[0];", "yr += h[(int64_t)m * ntaps + p] * x[0];", 0),
+    ("pfb_dropped_imag_tap", "yi += h[(int64_t)p * F + m] * x[1];", "yi += x[1];", 0),
 ]
 
 

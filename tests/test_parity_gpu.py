@@ -107,11 +107,13 @@ def test_accumulate_mode(engine_name, engine, dev):
         eng.close()
 
 
-def test_integrated_pipeline_matches_direct(dev):
+@pytest.mark.parametrize("N,F", [(48, 4), (16, 8)], ids=["N48", "N16_packed"])
+def test_integrated_pipeline_matches_direct(N, F, dev):
     """Algorithm 1 (Sec. 5): integrations streamed from pinned host memory
     through two device buffers give the same visibilities as direct calls,
-    in dump mode (one output per integration) and accumulate mode."""
-    T, F, N, P, nint = 200, 4, 48, 2, 5
+    in dump mode (one output per integration) and accumulate mode (N=16:
+    four channels packed per tensor-core block)."""
+    T, P, nint = 200, 2, 5
     xs = torch.stack([synth.uniform_int8((T, F, N, P, 2), -128, 127, 100 + i) for i in range(nint)])
     host = xs.pin_memory()
     want = [oracle.correlate_i8(xs[i].numpy()) for i in range(nint)]
