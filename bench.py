@@ -760,6 +760,21 @@ def run_fengine(args):
         res[odt] = {"ms": ms, "gbs": nbytes / ms / 1e6,
                     "frac_of_hbm": nbytes / ms / 1e6 / peaks["hbm_gbs"], "peak_kind": kind}
         del out
+    # Polyphase front end, 4 taps (T - 3 output blocks), fp16 out.
+    taps = torch.ones((4, F), device=dev)
+    out = torch.empty((T - 3, F, N, P, 2), dtype=torch.float16, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        xc.channelize(x, F, 1.0 / 64, "float16", out=out, taps=taps)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        xc.channelize(x, F, 1.0 / 64, "float16", out=out, taps=taps)
+    e1.record()
+    torch.cuda.synchronize()
+    res["polyphase_4_taps_float16"] = {"ms": e0.elapsed_time(e1) / args.steps,
+                                       "output_blocks": T - 3}
     print(json.dumps(res))
     return 0
 

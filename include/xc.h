@@ -337,6 +337,24 @@ xc_status xc_channelize(const void* in, xc_dtype in_dtype, int nstation, int npo
                         int nblock, float scale, void* out, xc_dtype out_dtype, void* stream);
 
 /*
+ * Polyphase F-engine (not in the paper; the usual F-engine filter in front
+ * of the DFT): as xc_channelize, but each output block is the DFT of ntaps
+ * consecutive input blocks weighted by real taps,
+ *
+ *   out[t][f][s][p] = scale * sum_m exp(-2 pi i f m / nchan)
+ *                             * sum_{q < ntaps} taps[q][m] in[s][p][(t + q) nchan + m]
+ *
+ * for the nblock - ntaps + 1 output blocks (out holds that many).
+ *   taps: device, [ntaps][nchan] float32, 16-byte aligned (e.g. a windowed
+ *         sinc prototype of ntaps * nchan coefficients); NULL is
+ *         XC_ERR_INVALID_ARG.  ntaps from 1 to min(64, nblock).
+ * Everything else as xc_channelize; one unit tap gives xc_channelize.
+ */
+xc_status xc_channelize_pfb(const void* in, xc_dtype in_dtype, int nstation, int npol, int nchan,
+                            int nblock, const float* taps, int ntaps, float scale, void* out,
+                            xc_dtype out_dtype, void* stream);
+
+/*
  * Batched form: many subarrays of uneven size correlated by ONE persistent
  * tensor-core launch (Sec. 4.2's channel-major block raster continued from
  * one subarray to the next), replayed from a CUDA graph captured on first

@@ -828,8 +828,11 @@ xc_status xc_correlate_stream(xc_handle* h, const void* host_in, int n_integrati
 
 // -------------------------------------------------------------- F-engine
 
-xc_status xc_channelize(const void* in, xc_dtype in_dtype, int nstation, int npol, int nchan,
-                        int nblock, float scale, void* out, xc_dtype out_dtype, void* stream) {
+namespace {
+
+xc_status channelize_impl(const void* in, xc_dtype in_dtype, int nstation, int npol, int nchan,
+                          int nblock, const float* taps, int ntaps, float scale, void* out,
+                          xc_dtype out_dtype, void* stream) {
   if (!in || !out) return fail(XC_ERR_INVALID_ARG, "NULL buffer");
   if (nstation <= 0 || nblock <= 0 || (npol != 1 && npol != 2))
     return fail(XC_ERR_INVALID_ARG, "bad sizes (nstation=%d npol=%d nblock=%d)", nstation, npol,
@@ -838,12 +841,15 @@ xc_status xc_channelize(const void* in, xc_dtype in_dtype, int nstation, int npo
     return fail(XC_ERR_INVALID_ARG, "unknown input type %d", static_cast<int>(in_dtype));
   if (out_dtype != XC_CI8 && out_dtype != XC_CF16 && out_dtype != XC_CF32)
     return fail(XC_ERR_INVALID_ARG, "unknown output type %d", static_cast<int>(out_dtype));
+  if (ntaps < 1 || ntaps > 64 || ntaps > nblock)
+    return fail(XC_ERR_INVALID_ARG, "ntaps=%d: 1 to min(64, nblock=%d)", ntaps, nblock);
   if (nchan < 16 || nchan > 4096 || (nchan & (nchan - 1)) != 0)
     return fail(XC_ERR_UNSUPPORTED, "nchan=%d: powers of two from 16 to 4096 are supported", nchan);
   const int64_t n = static_cast<int64_t>(nstation) * npol;
   if (n > (1LL << 24) || static_cast<int64_t>(nblock) * nchan > (1LL << 36) / n)
     return fail(XC_ERR_UNSUPPORTED, "problem too large");
-  if (!aligned16(in) || !aligned16(out)) return fail(XC_ERR_ALIGNMENT, "buffers must be 16-byte aligned");
+  if (!aligned16(in) || !aligned16(out) || (taps && !aligned16(taps)))
+    return fail(XC_ERR_ALIGNMENT, "buffers must be 16-byte aligned");
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
@@ -855,10 +861,26 @@ xc_status xc_channelize(const void* in, xc_dtype in_dtype, int nstation, int npo
     return fail(XC_ERR_NO_DEVICE, "device %d is sm_%d%d; this library is built for sm_103a only", dev,
                 major, minor);
   cudaError_t e = xc::launch_fengine(in, static_cast<int>(in_dtype), out, static_cast<int>(out_dtype),
-                                     static_cast<int>(n), nchan, nblock, scale,
+                                     static_cast<int>(n), nchan, nblock, scale, taps, ntaps,
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "F-engine launch");
   return succeed();
+}
+
+}  // namespace
+
+xc_status xc_channelize(const void* in, xc_dtype in_dtype, int nstation, int npol, int nchan,
+                        int nblock, float scale, void* out, xc_dtype out_dtype, void* stream) {
+  return channelize_impl(in, in_dtype, nstation, npol, nchan, nblock, nullptr, 1, scale, out,
+                         out_dtype, stream);
+}
+
+xc_status xc_channelize_pfb(const void* in, xc_dtype in_dtype, int nstation, int npol, int nchan,
+                            int nblock, const float* taps, int ntaps, float scale, void* out,
+                            xc_dtype out_dtype, void* stream) {
+  if (!taps) return fail(XC_ERR_INVALID_ARG, "NULL taps");
+  return channelize_impl(in, in_dtype, nstation, npol, nchan, nblock, taps, ntaps, scale, out,
+                         out_dtype, stream);
 }
 
 // ------------------------------------------------------------------ batch

@@ -1,6 +1,8 @@
 // F-engine of the FX correlator (Sec. 2): each station's signal is Fourier
 // transformed in blocks of F consecutive complex samples,
 //     X_t(f) = scale * sum_{m<F} x(t F + m) exp(-2 pi i f m / F),
+// optionally after a polyphase front end (taps h[p][m] over ntaps
+// consecutive blocks: x(t F + m) becomes sum_p h[p][m] x((t + p) F + m)),
 // and the result is written in the X-engine's input order [T][F][N][P]
 // (station fastest, then channel, then block: the corner turn of Sec. 2,
 // in the ordering of Sec. 4.1).  Input is station-major [N][P][T F]: the
@@ -27,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "xc_launch.h"
 
@@ -216,12 +219,14 @@ __device__ __forceinline__ void later_passes(float2 (&v)[kPts], float2* buf, int
 }
 
 // in [n][T F] complex (in_dt: 0 int8, 1 fp16, 2 fp32), out [T][F][n] complex
-// (out_dt: 0 int8 requantised, 1 fp16, 2 fp32), F = 2^LOGF.  grid = (T, ceil(n / G)), block =
-// 2^LOGP / 16 threads, dynamic shared memory G row_stride(F, G) float2.
+// (out_dt: 0 int8 requantised, 1 fp16, 2 fp32), F = 2^LOGF; T input blocks.
+// taps (NULL: none) is [ntaps][F] real: output block t transforms
+// sum_p taps[p][m] x((t + p) F + m).  grid = (T - ntaps + 1, ceil(n / G)),
+// block = 2^LOGP / 16 threads, dynamic shared memory G row_stride(F, G) float2.
 template <int LOGF, int LOGP>
 __global__ void __launch_bounds__((1 << LOGP) / kPts, (1 << 14) >> LOGP)
     fengine_kernel(const void* __restrict__ in, void* __restrict__ out, int n, int T, float scale,
-                   int in_dt, int out_dt) {
+                   int in_dt, int out_dt, const float* __restrict__ taps, int ntaps) {
   constexpr int F = 1 << LOGF;
   constexpr int G = (1 << LOGP) / F, LOGG = LOGP - LOGF;
   constexpr int kFThreads = (1 << LOGP) / kPts;
@@ -246,6 +251,41 @@ __global__ void __launch_bounds__((1 << LOGP) / kPts, (1 << 14) >> LOGP)
     if (a >= n) {
 #pragma unroll
       for (int e = 0; e < kPts; ++e) v[e] = make_float2(0.f, 0.f);
+    } else if (taps) {
+      // Polyphase front end: tap-weighted sum of ntaps consecutive blocks;
+      // per tap, eight taps and eight samples are loaded before they are used.
+#pragma unroll
+      for (int e = 0; e < kPts; ++e) v[e] = make_float2(0.f, 0.f);
+      auto accumulate = [&](auto dt) {
+        constexpr int DT = decltype(dt)::value;
+#pragma unroll 1
+        for (int p = 0; p < ntaps; ++p) {
+          const float* hp = taps + static_cast<int64_t>(p) * F + j;
+          const int64_t bp = base + static_cast<int64_t>(p) * F;
+#pragma unroll
+          for (int e0 = 0; e0 < kPts; e0 += 8) {
+            float h[8];
+            float2 xs[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              h[e] = __ldg(hp + at(e0 + e));
+              xs[e] = load_sample<DT>(in, bp + at(e0 + e));
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              v[e0 + e].x = fmaf(h[e], xs[e].x, v[e0 + e].x);
+              v[e0 + e].y = fmaf(h[e], xs[e].y, v[e0 + e].y);
+            }
+          }
+        }
+      };
+      if (in_dt == 0) {
+        accumulate(std::integral_constant<int, 0>());
+      } else if (in_dt == 1) {
+        accumulate(std::integral_constant<int, 1>());
+      } else {
+        accumulate(std::integral_constant<int, 2>());
+      }
     } else if (in_dt == 0) {
 #pragma unroll
       for (int e = 0; e < kPts; ++e) v[e] = load_sample<0>(in, base + at(e));
@@ -293,7 +333,7 @@ __global__ void __launch_bounds__((1 << LOGP) / kPts, (1 << 14) >> LOGP)
 
 template <int LOGF, int LOGP>
 cudaError_t launch_fp(const void* in, int in_dt, void* out, int out_dt, int n, int T, float scale,
-                      cudaStream_t s) {
+                      const float* taps, int ntaps, cudaStream_t s) {
   constexpr int F = 1 << LOGF, G = (1 << LOGP) / F;
   const size_t smem = static_cast<size_t>(G) * row_stride(F, G) * sizeof(float2);
   if ((n + G - 1) / G > 65535) return cudaErrorInvalidConfiguration;
@@ -301,9 +341,9 @@ cudaError_t launch_fp(const void* in, int in_dt, void* out, int out_dt, int n, i
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  const dim3 grid(static_cast<unsigned>(T), static_cast<unsigned>((n + G - 1) / G));
+  const dim3 grid(static_cast<unsigned>(T - ntaps + 1), static_cast<unsigned>((n + G - 1) / G));
   fengine_kernel<LOGF, LOGP><<<grid, (1 << LOGP) / kPts, smem, s>>>(in, out, n, T, scale, in_dt,
-                                                                    out_dt);
+                                                                    out_dt, taps, ntaps);
   return cudaGetLastError();
 }
 
@@ -311,27 +351,28 @@ cudaError_t launch_fp(const void* in, int in_dt, void* out, int out_dt, int n, i
 // larger CTA, whose corner-turn runs cover whole 32-byte sectors.
 template <int LOGF>
 cudaError_t launch_f(const void* in, int in_dt, void* out, int out_dt, int n, int T, float scale,
-                     cudaStream_t s) {
-  if (out_dt == 0) return launch_fp<LOGF, 14>(in, in_dt, out, out_dt, n, T, scale, s);
-  return launch_fp<LOGF, 13>(in, in_dt, out, out_dt, n, T, scale, s);
+                     const float* taps, int ntaps, cudaStream_t s) {
+  if (out_dt == 0) return launch_fp<LOGF, 14>(in, in_dt, out, out_dt, n, T, scale, taps, ntaps, s);
+  return launch_fp<LOGF, 13>(in, in_dt, out, out_dt, n, T, scale, taps, ntaps, s);
 }
 
 }  // namespace
 
 cudaError_t launch_fengine(const void* in, int in_dtype, void* out, int out_dtype, int n, int F,
-                           int T, float scale, cudaStream_t s) {
-  if (n <= 0 || T <= 0 || in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 2)
+                           int T, float scale, const float* taps, int ntaps, cudaStream_t s) {
+  if (n <= 0 || T <= 0 || in_dtype < 0 || in_dtype > 2 || out_dtype < 0 || out_dtype > 2 ||
+      ntaps < 1 || ntaps > T || (!taps && ntaps != 1))
     return cudaErrorInvalidValue;
   switch (F) {
-    case 16: return launch_f<4>(in, in_dtype, out, out_dtype, n, T, scale, s);
-    case 32: return launch_f<5>(in, in_dtype, out, out_dtype, n, T, scale, s);
-    case 64: return launch_f<6>(in, in_dtype, out, out_dtype, n, T, scale, s);
-    case 128: return launch_f<7>(in, in_dtype, out, out_dtype, n, T, scale, s);
-    case 256: return launch_f<8>(in, in_dtype, out, out_dtype, n, T, scale, s);
-    case 512: return launch_f<9>(in, in_dtype, out, out_dtype, n, T, scale, s);
-    case 1024: return launch_f<10>(in, in_dtype, out, out_dtype, n, T, scale, s);
-    case 2048: return launch_f<11>(in, in_dtype, out, out_dtype, n, T, scale, s);
-    case 4096: return launch_f<12>(in, in_dtype, out, out_dtype, n, T, scale, s);
+    case 16: return launch_f<4>(in, in_dtype, out, out_dtype, n, T, scale, taps, ntaps, s);
+    case 32: return launch_f<5>(in, in_dtype, out, out_dtype, n, T, scale, taps, ntaps, s);
+    case 64: return launch_f<6>(in, in_dtype, out, out_dtype, n, T, scale, taps, ntaps, s);
+    case 128: return launch_f<7>(in, in_dtype, out, out_dtype, n, T, scale, taps, ntaps, s);
+    case 256: return launch_f<8>(in, in_dtype, out, out_dtype, n, T, scale, taps, ntaps, s);
+    case 512: return launch_f<9>(in, in_dtype, out, out_dtype, n, T, scale, taps, ntaps, s);
+    case 1024: return launch_f<10>(in, in_dtype, out, out_dtype, n, T, scale, taps, ntaps, s);
+    case 2048: return launch_f<11>(in, in_dtype, out, out_dtype, n, T, scale, taps, ntaps, s);
+    case 4096: return launch_f<12>(in, in_dtype, out, out_dtype, n, T, scale, taps, ntaps, s);
   }
   return cudaErrorInvalidValue;
 }

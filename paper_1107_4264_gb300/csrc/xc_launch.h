@@ -73,11 +73,12 @@ int planar_ring_slots(const Geometry& g, int grid, int fmt);
 Geometry planar_geometry(const Geometry& g, int* pack);
 
 // F-engine (xc_fengine.cu): in [n][T F] complex (in_dtype 0 int8, 1 fp16,
-// 2 fp32) -> out [T][F][n] complex (out_dtype 0 int8 requantised, 1 fp16,
-// 2 fp32), the DFT of each block of F samples times `scale`; F a power of two
-// in [16, 4096].
+// 2 fp32) -> out [T - ntaps + 1][F][n] complex (out_dtype 0 int8
+// requantised, 1 fp16, 2 fp32), the DFT of each block of F samples (after the
+// polyphase taps [ntaps][F] when taps is not NULL) times `scale`; F a power
+// of two in [16, 4096]; taps NULL needs ntaps = 1.
 cudaError_t launch_fengine(const void* in, int in_dtype, void* out, int out_dtype, int n, int F,
-                           int T, float scale, cudaStream_t s);
+                           int T, float scale, const float* taps, int ntaps, cudaStream_t s);
 int64_t planar_slot_bytes(const Geometry& g, int fmt);
 
 // One planar launch over up to kMaxSub subarrays (same input type and

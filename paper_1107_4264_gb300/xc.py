@@ -42,6 +42,7 @@ EXPORTS = [
     "xc_correlate_stream", "xc_input_bytes", "xc_output_bytes", "xc_tri_index", "xc_tri_coords",
     "xc_version", "xc_kernel_times", "xc_correlate_noalloc", "xc_set_gains", "xc_get_grad_gains",
     "xc_batch_create", "xc_batch_correlate", "xc_batch_tune", "xc_channelize",
+    "xc_channelize_pfb",
 ]
 
 _lib: Optional[ctypes.CDLL] = None
@@ -82,6 +83,7 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "xc_batch_tune": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, i32,
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)], i32),
         "xc_channelize": ([vp, i32, i32, i32, i32, i32, ctypes.c_float, vp, i32, vp], i32),
+        "xc_channelize_pfb": ([vp, i32, i32, i32, i32, i32, vp, i32, ctypes.c_float, vp, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -210,6 +212,13 @@ def xc_channelize(in_ptr: int, in_dtype: int, nstation: int, npol: int, nchan: i
                                 out_dtype, stream)
 
 
+def xc_channelize_pfb(in_ptr: int, in_dtype: int, nstation: int, npol: int, nchan: int,
+                      nblock: int, taps_ptr: int, ntaps: int, scale: float, out_ptr: int,
+                      out_dtype: int, stream: int = 0) -> int:
+    return load().xc_channelize_pfb(in_ptr, in_dtype, nstation, npol, nchan, nblock, taps_ptr,
+                                    ntaps, scale, out_ptr, out_dtype, stream)
+
+
 def xc_version() -> str:
     return load().xc_version().decode()
 
@@ -335,26 +344,39 @@ class Correlator:
 
 
 def channelize(x, nchan: int, scale: float = 1.0, out_dtype: str = "float16", out=None,
-               stream=None):
+               stream=None, taps=None):
     """F-engine: ``x[N][P][T*nchan][2]`` (int8, float16 or float32 on the GPU,
     each station's complex stream) -> ``[T][nchan][N][P][2]`` of ``out_dtype``,
     the DFT of every block of nchan samples times ``scale``, already in
     :class:`Correlator`'s input layout; ``out_dtype="int8"`` requantises each
-    component to the nearest integer, saturated at +-127.  Stream-ordered
-    (current stream by default); raises XcError on a bad argument."""
+    component to the nearest integer, saturated at +-127.  With ``taps``
+    (float32 ``[ntaps][nchan]`` on the GPU) a polyphase front end weights
+    ntaps consecutive blocks before each DFT and T - ntaps + 1 blocks come
+    out.  Stream-ordered (current stream by default); raises XcError on a bad
+    argument."""
     import torch
     assert x.is_cuda and x.is_contiguous() and x.dim() == 4 and x.shape[-1] == 2
     N, P, L, _ = x.shape
     if L % nchan:
         raise ValueError("samples per stream (%d) not a multiple of nchan (%d)" % (L, nchan))
     T = L // nchan
+    ntaps = 1 if taps is None else taps.shape[0]
+    if taps is not None:
+        assert taps.is_cuda and taps.is_contiguous() and taps.dtype == torch.float32
+        assert tuple(taps.shape) == (ntaps, nchan)
+    Tout = T - ntaps + 1
     odt = {"int8": torch.int8, "float16": torch.float16, "float32": torch.float32}[out_dtype]
     if out is None:
-        out = torch.empty((T, nchan, N, P, 2), dtype=odt, device=x.device)
-    assert out.is_contiguous() and out.dtype == odt and tuple(out.shape) == (T, nchan, N, P, 2)
+        out = torch.empty((max(Tout, 0), nchan, N, P, 2), dtype=odt, device=x.device)
+    assert out.is_contiguous() and out.dtype == odt and tuple(out.shape) == (Tout, nchan, N, P, 2)
     s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
-    _check(xc_channelize(x.data_ptr(), _DTYPES[str(x.dtype).replace("torch.", "")], N, P, nchan, T,
-                         float(scale), out.data_ptr(), _DTYPES[out_dtype], s))
+    idt = _DTYPES[str(x.dtype).replace("torch.", "")]
+    if taps is None:
+        _check(xc_channelize(x.data_ptr(), idt, N, P, nchan, T, float(scale), out.data_ptr(),
+                             _DTYPES[out_dtype], s))
+    else:
+        _check(xc_channelize_pfb(x.data_ptr(), idt, N, P, nchan, T, taps.data_ptr(), ntaps,
+                                 float(scale), out.data_ptr(), _DTYPES[out_dtype], s))
     return out
 
 

@@ -12,7 +12,9 @@ outputs are checked one by one.  The FX chain (F-engine into the X-engine)
 is checked against the oracle's F-engine followed by its X-engine.  Output
 requantised to 8 bits must equal the oracle's requantisation except at
 rounding boundaries (within 1e-3 of x.5), where the fp32 kernel may round
-one code the other way; the 8-bit FX chain is then bit-exact on those codes."""
+one code the other way; the 8-bit FX chain is then bit-exact on those codes.
+The polyphase front end (random taps, 1 to 8 of them) is checked the same
+way against the oracle's tap-weighted DFT."""
 import numpy as np
 import pytest
 import torch
@@ -175,6 +177,49 @@ def test_fx_chain_int8_is_exact_on_the_codes(dev):
     codes = codes.cpu().numpy()
     np.testing.assert_array_equal(vis, oracle.correlate_i8(codes))
     check_requantised(codes, oracle.channelize_f64(x.double().numpy(), F, scale))
+
+
+# (N, P, nchan, input blocks, ntaps, input type, output type)
+PFB_CASES = [
+    (5, 2, 64, 9, 4, "int8", "float32"),
+    (9, 2, 1024, 6, 3, "float32", "float32"),
+    (33, 2, 256, 5, 1, "float16", "float16"),
+    (8, 1, 2048, 4, 4, "float32", "float32"),
+    (8, 2, 1024, 10, 8, "int8", "int8"),
+]
+
+
+@pytest.mark.parametrize("N,P,F,T,ntaps,idt,odt", PFB_CASES,
+                         ids=["N%d_P%d_F%d_T%d_taps%d_%s_%s" % c for c in PFB_CASES])
+def test_polyphase_matches_oracle(N, P, F, T, ntaps, idt, odt, dev):
+    x = streams(N, P, T * F, idt, 90 + F + ntaps)
+    g = torch.Generator().manual_seed(91 + ntaps)
+    taps = torch.randn((ntaps, F), generator=g)
+    sx = 74.0 if idt == "int8" else 3.0
+    scale = 37.0 / (sx * np.sqrt(ntaps * F))  # output rms about 37
+    got = xc.channelize(x.to(dev), F, scale, odt, taps=taps.to(dev)).cpu()
+    want = oracle.channelize_pfb_f64(x.double().numpy(), taps.double().numpy(), scale)
+    assert tuple(got.shape) == want.shape == (T - ntaps + 1, F, N, P, 2)
+    if odt == "int8":
+        check_requantised(got.numpy(), want)
+        return
+    frob, mx = rel_errors(got.double().numpy(), want)
+    print(f"\npfb F={F} taps={ntaps} {idt}->{odt}: frobenius {frob:.2e} max {mx:.2e}")
+    if odt == "float32":
+        assert frob <= 2e-6 and mx <= 1e-5, (frob, mx)
+    else:
+        assert frob <= 1e-3 and mx <= 1e-3, (frob, mx)
+
+
+def test_polyphase_argument_errors(dev):
+    x = torch.zeros((2, 2, 64 * 4, 2), dtype=torch.int8, device=dev)
+    taps = torch.ones((5, 64), device=dev)
+    with pytest.raises(xc.XcError) as e:
+        xc.channelize(x, 64, taps=taps)  # 5 taps over 4 blocks
+    assert "XC_ERR_INVALID_ARG" in str(e.value)
+    out = torch.empty((1, 64, 2, 2, 2), dtype=torch.float32, device=dev)
+    assert xc.xc_channelize_pfb(x.data_ptr(), xc.XC_CI8, 2, 2, 64, 4, 0, 4, 1.0, out.data_ptr(),
+                                xc.XC_CF32, 0) == xc.XC_ERR_INVALID_ARG
 
 
 def test_channelize_argument_errors(dev):
