@@ -909,7 +909,12 @@ __device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint
       return __uint_as_float(u);
     }
   };
-  if (a >= p.n) return;
+  // Two polarisations, overwrite, 32-byte aligned output: the lanes of a
+  // station's two rows (a, a ^ 1; both valid or both not, n being even)
+  // exchange halves so that each writes whole 32-byte baseline records.
+  const bool pairs = g.P == 2 && !add && (reinterpret_cast<uintptr_t>(out) & 31) == 0;
+  const bool valid = a < p.n;
+  if (!valid && !pairs) return;
   // Real channel, row station and first column station (packed channels:
   // columns of another channel of the pack fall outside 0 <= s2 <= s1).
   int fr = f, s1 = a / g.P, s2_0 = b0 / g.P;
@@ -920,7 +925,39 @@ __device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint
     fr = f * p.pack + j;
   }
   const int64_t krow = static_cast<int64_t>(fr) * p.NBr + static_cast<int64_t>(s1) * (s1 + 1) / 2;
-  if (g.P == 2) {
+  if (pairs) {
+    const int p1 = a & 1;
+    uint32_t* o8 = reinterpret_cast<uint32_t*>(out + krow * 8);  // record of s2 at o8 + 8 s2
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      // This lane's products for column stations 2m (A) and 2m + 1 (B) of the piece.
+      uint32_t A[4], B[4], rec[8];
+      auto bits = [&](uint32_t u) -> uint32_t {  // the stored word: int32 value or fp32 bits
+        if constexpr (IS_INT) {
+          return static_cast<uint32_t>(val(u));
+        } else {
+          return u;
+        }
+      };
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        A[2 * q] = bits(re[4 * m + q]);
+        A[2 * q + 1] = bits(im[4 * m + q]);
+        B[2 * q] = bits(re[4 * m + 2 + q]);
+        B[2 * q + 1] = bits(im[4 * m + 2 + q]);
+      }
+      // Row p1 = 0 writes baseline 2m, row p1 = 1 baseline 2m + 1; each sends
+      // the partner the half it needs.
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t got = __shfl_xor_sync(0xffffffffu, p1 ? A[k] : B[k], 1);
+        rec[k] = p1 ? got : A[k];
+        rec[4 + k] = p1 ? B[k] : got;
+      }
+      const int s2 = s2_0 + 2 * m + p1;
+      if (valid && s2 >= 0 && s2 <= s1) ptx::st_global_v8(o8 + 8 * static_cast<int64_t>(s2), rec);
+    }
+  } else if (g.P == 2) {
     const int p1 = a & 1;
     using V4 = typename std::conditional<IS_INT, int4, float4>::type;
     V4* o4 = reinterpret_cast<V4*>(out + (krow * 4 + p1 * 2) * 2);  // (p1,0),(p1,1) of s2 at o4[2 s2]

@@ -135,6 +135,13 @@ __device__ __forceinline__ void st_global_v8_hint(void* p, const uint32_t (&v)[8
       : "memory");
 }
 
+// 32-byte global store (p 32-byte aligned).
+__device__ __forceinline__ void st_global_v8(void* p, const uint32_t (&v)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+
 // 16-byte global store that does not allocate in L1, with an L2 policy.
 __device__ __forceinline__ void st_global_v4_hint(void* p, uint32_t a, uint32_t b, uint32_t c,
                                                   uint32_t d, uint64_t pol) {
