@@ -67,6 +67,46 @@ def test_null_handle_calls(lib):
     lib.xc_destroy(None)  # NULL-safe
 
 
+# Fake, 16-byte aligned addresses: every case below is rejected by the host-side
+# argument checks before any device call, so nothing is dereferenced.
+_IN, _OUT, _TAPS = 0x10000, 0x20000, 0x30000
+
+
+@pytest.mark.parametrize("args,status", [
+    ((None, xc.XC_CI8, 4, 2, 64, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_INVALID_ARG),
+    ((_IN, xc.XC_CI8, 4, 2, 64, 8, 1.0, None, xc.XC_CF16, None), xc.XC_ERR_INVALID_ARG),
+    ((_IN, xc.XC_CI8, 0, 2, 64, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_INVALID_ARG),
+    ((_IN, xc.XC_CI8, 4, 3, 64, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_INVALID_ARG),
+    ((_IN, xc.XC_CI8, 4, 2, 64, 0, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_INVALID_ARG),
+    ((_IN, 9, 4, 2, 64, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_INVALID_ARG),
+    ((_IN, xc.XC_CI8, 4, 2, 64, 8, 1.0, _OUT, 9, None), xc.XC_ERR_INVALID_ARG),
+    ((_IN, xc.XC_CI8, 4, 2, 48, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_UNSUPPORTED),
+    ((_IN, xc.XC_CI8, 4, 2, 8, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_UNSUPPORTED),
+    ((_IN, xc.XC_CI8, 4, 2, 8192, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_UNSUPPORTED),
+    ((_IN + 4, xc.XC_CI8, 4, 2, 64, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_ALIGNMENT),
+    ((_IN, xc.XC_CI8, 4, 2, 64, 8, 1.0, _OUT + 8, xc.XC_CF16, None), xc.XC_ERR_ALIGNMENT),
+], ids=["null_in", "null_out", "no_station", "npol3", "no_block", "in_type", "out_type",
+        "nchan48", "nchan8", "nchan8192", "in_misaligned", "out_misaligned"])
+def test_channelize_rejects_bad_arguments(lib, args, status):
+    assert lib.xc_channelize(*args) == status
+    assert lib.xc_last_error() == status
+    assert lib.xc_last_error_message()
+
+
+@pytest.mark.parametrize("taps,ntaps,nblock,status", [
+    (None, 4, 8, xc.XC_ERR_INVALID_ARG),    # no taps
+    (_TAPS, 0, 8, xc.XC_ERR_INVALID_ARG),   # no tap
+    (_TAPS, 9, 8, xc.XC_ERR_INVALID_ARG),   # more taps than blocks
+    (_TAPS, 65, 100, xc.XC_ERR_INVALID_ARG),  # above 64 taps
+    (_TAPS + 4, 4, 8, xc.XC_ERR_ALIGNMENT),
+], ids=["null_taps", "zero_taps", "taps_gt_blocks", "taps_gt_64", "taps_misaligned"])
+def test_channelize_pfb_rejects_bad_arguments(lib, taps, ntaps, nblock, status):
+    st = lib.xc_channelize_pfb(_IN, xc.XC_CI8, 4, 2, 64, nblock, taps, ntaps, 1.0, _OUT,
+                               xc.XC_CF16, None)
+    assert st == status
+    assert lib.xc_last_error() == status
+
+
 def test_tri_map_round_trip_exhaustive(lib):
     # every block of the lower triangle up to 4000 block rows (8e6 blocks)
     n = 4000
