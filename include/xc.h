@@ -330,8 +330,10 @@ xc_status xc_correlate_noalloc(int nstation, int npol, int nfreq, int ntime, xc_
  *        output it keeps 8-bit input in range (|out| <= 128 sqrt(2 nchan)).
  *   stream: cudaStream_t as void*; stream-ordered, returns once queued.
  * Buffers are caller-owned and 16-byte aligned (XC_ERR_ALIGNMENT); NULL or
- * sizes <= 0 give XC_ERR_INVALID_ARG.  Arithmetic is fp32 throughout
- * (radix-16 FFT), about 1e-6 relative before the output rounding.
+ * sizes <= 0 give XC_ERR_INVALID_ARG; more than 65535 * 8192 / nchan
+ * station-polarisations (65535 * 16384 / nchan for XC_CI8 output) give
+ * XC_ERR_UNSUPPORTED.  Arithmetic is fp32 throughout (radix-16 FFT), about
+ * 1e-6 relative before the output rounding.
  */
 xc_status xc_channelize(const void* in, xc_dtype in_dtype, int nstation, int npol, int nchan,
                         int nblock, float scale, void* out, xc_dtype out_dtype, void* stream);

@@ -848,6 +848,13 @@ xc_status channelize_impl(const void* in, xc_dtype in_dtype, int nstation, int n
   const int64_t n = static_cast<int64_t>(nstation) * npol;
   if (n > (1LL << 24) || static_cast<int64_t>(nblock) * nchan > (1LL << 36) / n)
     return fail(XC_ERR_UNSUPPORTED, "problem too large");
+  // One CTA transforms G consecutive inputs of one block (G = 8192 / nchan,
+  // 16384 / nchan for 8-bit output); the input groups form the grid's second
+  // dimension (at most 65535).
+  const int64_t G = (out_dtype == XC_CI8 ? 16384 : 8192) / nchan;
+  if ((n + G - 1) / G > 65535)
+    return fail(XC_ERR_UNSUPPORTED, "nstation*npol=%lld above %lld for nchan=%d",
+                static_cast<long long>(n), static_cast<long long>(65535 * G), nchan);
   if (!aligned16(in) || !aligned16(out) || (taps && !aligned16(taps)))
     return fail(XC_ERR_ALIGNMENT, "buffers must be 16-byte aligned");
   int dev = 0, major = 0, minor = 0;

@@ -83,10 +83,11 @@ _IN, _OUT, _TAPS = 0x10000, 0x20000, 0x30000
     ((_IN, xc.XC_CI8, 4, 2, 48, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_UNSUPPORTED),
     ((_IN, xc.XC_CI8, 4, 2, 8, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_UNSUPPORTED),
     ((_IN, xc.XC_CI8, 4, 2, 8192, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_UNSUPPORTED),
+    ((_IN, xc.XC_CI8, 2 ** 22, 2, 4096, 1, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_UNSUPPORTED),
     ((_IN + 4, xc.XC_CI8, 4, 2, 64, 8, 1.0, _OUT, xc.XC_CF16, None), xc.XC_ERR_ALIGNMENT),
     ((_IN, xc.XC_CI8, 4, 2, 64, 8, 1.0, _OUT + 8, xc.XC_CF16, None), xc.XC_ERR_ALIGNMENT),
 ], ids=["null_in", "null_out", "no_station", "npol3", "no_block", "in_type", "out_type",
-        "nchan48", "nchan8", "nchan8192", "in_misaligned", "out_misaligned"])
+        "nchan48", "nchan8", "nchan8192", "too_many_inputs", "in_misaligned", "out_misaligned"])
 def test_channelize_rejects_bad_arguments(lib, args, status):
     assert lib.xc_channelize(*args) == status
     assert lib.xc_last_error() == status
