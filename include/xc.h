@@ -88,10 +88,16 @@ typedef enum {
 
 /*
  * Create an engine for fixed sizes on the current CUDA device.
- *   nstation N >= 1, npol P in {1, 2}, nfreq F >= 1, ntime T >= 1.
- * Allocates the workspace (a ring of fp16 operand slots for a few channels,
- * at most 16 and about 32 MiB, plus counters and a status word).  Returns
- * NULL on error; the reason is in xc_last_error().
+ *   nstation N >= 1, npol P in {1, 2}, nfreq F >= 1 (at most 65535),
+ *   ntime T >= 1.
+ * Allocates the workspace: a ring of tensor-core operand tiles for the
+ * channels in flight (about 1.6 x 152 / (blocks per channel) + 4 channel
+ * slots, at most 256 MiB; 60 MiB for N=256 x 2 pols, T=1000, sized to stay
+ * in L2), plus counters and a status word.  Small arrays (N*P <= 64) have k
+ * consecutive channels correlated together in one tensor-core block (k the
+ * largest divisor of F with k*N*P <= 128); this is internal and changes
+ * neither layouts nor results.  Returns NULL on error; the reason is in
+ * xc_last_error().
  */
 xc_handle* xc_create(int nstation, int npol, int nfreq, int ntime, xc_dtype in_dtype);
 
