@@ -158,11 +158,11 @@ const char* xc_status_string(xc_status s);
 
 /* Option keys for xc_set_option. */
 enum {
-  XC_OPT_ENGINE = 1,     /* XC_ENGINE_TENSOR (default) or XC_ENGINE_FP32 */
+  XC_OPT_ENGINE = 1,     /* XC_ENGINE_* below (default XC_ENGINE_TENSOR) */
   XC_OPT_ACCUMULATE = 2, /* 0: out = V (default); 1: out += V */
   XC_OPT_TIMEOUT_MS = 3, /* bound on any in-kernel wait, milliseconds (default 2000) */
   XC_OPT_PROFILE = 4,    /* 1: time every kernel with CUDA events (see xc_kernel_times) */
-  XC_OPT_PRECISION = 5,  /* float input, XC_ENGINE_TENSOR: XC_PREC_* (default FP16) */
+  XC_OPT_PRECISION = 5,  /* XC_ENGINE_TENSOR: XC_PREC_* (default FP16; 8-bit input: FP16 or FP8) */
   XC_OPT_FP64_BLOCK = 6, /* float input, XC_ENGINE_TENSOR: T_blk > 0 enables FP64 block sums */
   /* Test hook for the failure-detection path (XC_ENGINE_TENSOR): 1 makes the
    * operand converters skip publishing converted units, so every wait of the
