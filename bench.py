@@ -233,11 +233,12 @@ def cpu_model():
     return "unknown"
 
 
-def cpu_oracle_sample(x_cpu_chans, w, channels):
+def cpu_oracle_sample(x_cpu_chans, w, channels, threads=None):
     """Time the CPU oracle, as it stands, on `channels` channels of one
-    integration.  Returns (seconds, ops, threads)."""
+    integration, on `threads` threads (default: every host core).  Returns
+    (seconds, ops, threads used)."""
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     oracle.set_num_threads(threads)
     t0 = time.perf_counter()
     oracle.correlate_i8(x_cpu_chans)
@@ -711,11 +712,14 @@ def run_xc(args):
         nchan = min(args.cpu_channels or w.nfreq // 2, w.nfreq)
         xs_cpu = xs[0][:, :nchan].contiguous().cpu().numpy()
         dt, ops, thr = cpu_oracle_sample(xs_cpu, w, nchan)
+        dt1, ops1, _ = cpu_oracle_sample(xs_cpu[:, :1].copy(), w, 1, threads=1)
         result["cpu_baseline"] = {
             "value": ops / dt / 1e12, "unit": UNIT, "cores": thr, "kind": "oracle",
             "sample": "%d of %d channels of integration 0 (N=256 x 2 pols, T=1000), %.1f s"
                       % (nchan, w.nfreq, dt),
             "cpu": cpu_model(),
+            "single_thread": {"value": ops1 / dt1 / 1e12, "unit": UNIT,
+                              "sample": "1 channel on 1 thread, %.2f s" % dt1},
         }
 
     eng.close()
