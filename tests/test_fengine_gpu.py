@@ -144,9 +144,14 @@ def check_requantised(got, Xs, tol=1e-3):
     return int((diff != 0).sum())
 
 
-@pytest.mark.parametrize("F,idt", [(256, "int8"), (1024, "float32"), (64, "float16")])
-def test_channelize_requantised_int8(F, idt, dev):
-    N, P, T = 8, 2, 6
+# N*P a multiple of 8 takes the 16-byte store path; N*P = 5 and nchan = 4096
+# (4 transforms per CTA) take the per-code stores.
+@pytest.mark.parametrize("F,idt,N,P", [(256, "int8", 8, 2), (1024, "float32", 8, 2),
+                                       (64, "float16", 8, 2), (128, "int8", 5, 1),
+                                       (4096, "int8", 4, 2), (2048, "float32", 12, 2)],
+                         ids=["F256_n16", "F1024_n16", "F64_n16", "F128_n5", "F4096_n8", "F2048_n24"])
+def test_channelize_requantised_int8(F, idt, N, P, dev):
+    T = 6
     x = streams(N, P, T * F, idt, 80 + F)
     scale = 0.5 / np.sqrt(F)  # output rms about 37 for int8 input: some components saturate
     if idt != "int8":
