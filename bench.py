@@ -89,15 +89,11 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def planar_pack(n, F):
-    """Channels the planar engine packs into one virtual channel: the largest
-    divisor k of F with k n <= 128 when n <= 64, else 1."""
-    if n > 64:
-        return 1
-    for k in range(128 // n, 1, -1):
-        if F % k == 0:
-            return k
-    return 1
+def planar_pack(N, P, F):
+    """Channels the planar engine packs into one virtual channel (asked of the
+    library: the largest divisor k of F with k N P <= 128 when N P <= 64)."""
+    from paper_1107_4264_gb300 import xc
+    return xc.load().xc_channels_packed(N, P, F)
 
 
 def executed_ops(N, P, F, T, steps_per_block=1):
@@ -105,7 +101,7 @@ def executed_ops(N, P, F, T, steps_per_block=1):
     128 x 128 block of the (virtual, packed) channel, 128 rows times the
     block's columns trimmed to a multiple of 16, over T padded to 64."""
     n = N * P
-    k = planar_pack(n, F)
+    k = planar_pack(N, P, F)
     nv, fv = k * n, F // k
     nb = (nv + 127) // 128
     macs = 0
@@ -501,7 +497,7 @@ def run_sweep(args):
         useful = 8 * F * T * 4 * N * (N + 1) // 2
         executed = executed_ops(N, 2, F, T)
         in_b, out_b = T * F * N * 4, F * N * (N + 1) // 2 * 4 * 8
-        return {"N": N, "F": F, "T": T, "channels_packed": planar_pack(2 * N, F),
+        return {"N": N, "F": F, "T": T, "channels_packed": planar_pack(N, 2, F),
                 "kernel_ms": ms, "tops": useful / ms / 1e9,
                 "executed_tflops": executed / ms / 1e9, "useful_fraction": useful / executed,
                 "hbm_gbs_algorithmic": (in_b + out_b) / ms / 1e6}

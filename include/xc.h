@@ -272,6 +272,14 @@ int64_t xc_tri_index(int64_t bx, int64_t by);
 void xc_tri_coords(int64_t g, int64_t* bx, int64_t* by);
 
 /*
+ * Channels the tensor-core engine correlates together in one 128-input block
+ * for these sizes (see xc_create): k, the largest divisor of nfreq with
+ * k * nstation * npol <= 128, when nstation * npol <= 64; else 1.  Host-side,
+ * no device work; returns 0 for sizes <= 0.
+ */
+int xc_channels_packed(int nstation, int npol, int nfreq);
+
+/*
  * No-allocation X-engine (the paper has no counterpart; this is a service
  * for callers of this library).
  *

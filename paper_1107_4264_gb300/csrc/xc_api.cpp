@@ -447,6 +447,21 @@ const char* xc_version(void) { return "xc 0.1 (sm_103a)"; }
 
 int64_t xc_tri_index(int64_t bx, int64_t by) { return xc::tri_index(bx, by); }
 
+int xc_channels_packed(int nstation, int npol, int nfreq) {
+  if (nstation <= 0 || npol <= 0 || nfreq <= 0) return 0;
+  xc::Geometry g{};
+  g.N = nstation;
+  g.P = npol;
+  g.F = nfreq;
+  g.T = 1;
+  g.R = 2 * npol * nstation;
+  g.Tp = 64;
+  g.NB = static_cast<int64_t>(nstation) * (nstation + 1) / 2;
+  int pack = 1;
+  (void)xc::planar_geometry(g, &pack);
+  return pack;
+}
+
 void xc_tri_coords(int64_t g, int64_t* bx, int64_t* by) {
   int64_t x = 0, y = 0;
   xc::tri_coords(g, &x, &y);

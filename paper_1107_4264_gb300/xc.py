@@ -42,7 +42,7 @@ EXPORTS = [
     "xc_correlate_stream", "xc_input_bytes", "xc_output_bytes", "xc_tri_index", "xc_tri_coords",
     "xc_version", "xc_kernel_times", "xc_correlate_noalloc", "xc_set_gains", "xc_get_grad_gains",
     "xc_batch_create", "xc_batch_correlate", "xc_batch_tune", "xc_channelize",
-    "xc_channelize_pfb",
+    "xc_channelize_pfb", "xc_channels_packed",
 ]
 
 _lib: Optional[ctypes.CDLL] = None
@@ -84,6 +84,7 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)], i32),
         "xc_channelize": ([vp, i32, i32, i32, i32, i32, ctypes.c_float, vp, i32, vp], i32),
         "xc_channelize_pfb": ([vp, i32, i32, i32, i32, i32, vp, i32, ctypes.c_float, vp, i32, vp], i32),
+        "xc_channels_packed": ([i32, i32, i32], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

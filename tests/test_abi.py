@@ -108,6 +108,23 @@ def test_channelize_pfb_rejects_bad_arguments(lib, taps, ntaps, nblock, status):
     assert lib.xc_last_error() == status
 
 
+def test_channels_packed_rule(lib):
+    """The packing decision: k = the largest divisor of F with k n <= 128 for
+    n = N P <= 64 inputs, else 1 (restated here from its documentation)."""
+    def rule(N, P, F):
+        n = N * P
+        if n > 64:
+            return 1
+        return max(k for k in range(1, 128 // n + 1) if F % k == 0)
+    for N in (1, 2, 3, 5, 8, 16, 24, 32, 33, 64, 200):
+        for P in (1, 2):
+            for F in (1, 2, 3, 7, 8, 12, 60, 64, 1024, 65535, 65528):
+                assert lib.xc_channels_packed(N, P, F) == rule(N, P, F), (N, P, F)
+    assert lib.xc_channels_packed(16, 2, 1024) == 4
+    assert lib.xc_channels_packed(256, 2, 1024) == 1
+    assert lib.xc_channels_packed(0, 2, 8) == 0
+
+
 def test_tri_map_round_trip_exhaustive(lib):
     # every block of the lower triangle up to 4000 block rows (8e6 blocks)
     n = 4000
