@@ -70,6 +70,8 @@ def parse_args():
                          "(N=256 x 2 pols, 1024 channels), fp16, fp32 and 8-bit output, one JSON object")
     ap.add_argument("--fengine-blocks", type=int, default=1000,
                     help="blocks (samples per stream / 1024) for --fengine (smaller for profiling)")
+    ap.add_argument("--tile", choices=["auto", "128", "pair", "wide"], default="auto",
+                    help="tile shape of the tensor-core engine (default: the library's choice)")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the bench line: kernel TOPS over N (fixed work) and over T at "
                          "fixed F*T (output traffic), one JSON object")
@@ -550,7 +552,10 @@ def run_xc(args):
     outs = torch.empty((nint,) + w.out_shape, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "int8", engine=xc.XC_ENGINE_TENSOR)
+    tile = {"auto": xc.XC_TILE_AUTO, "128": xc.XC_TILE_128, "pair": xc.XC_TILE_PAIR,
+            "wide": xc.XC_TILE_WIDE}[args.tile]
+    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "int8", engine=xc.XC_ENGINE_TENSOR,
+                        tile=tile)
     eng.set_option(xc.XC_OPT_PROFILE, 1)
 
     def step():

@@ -164,6 +164,7 @@ enum {
   XC_OPT_PROFILE = 4,    /* 1: time every kernel with CUDA events (see xc_kernel_times) */
   XC_OPT_PRECISION = 5,  /* XC_ENGINE_TENSOR: XC_PREC_* (default FP16; 8-bit input: FP16 or FP8) */
   XC_OPT_FP64_BLOCK = 6, /* float input, XC_ENGINE_TENSOR: T_blk > 0 enables FP64 block sums */
+  XC_OPT_TILE = 7,       /* XC_ENGINE_TENSOR tile shape: XC_TILE_* below (default XC_TILE_AUTO) */
   /* Test hook for the failure-detection path (XC_ENGINE_TENSOR): 1 makes the
    * operand converters skip publishing converted units, so every wait of the
    * kernel's consumers runs out after XC_OPT_TIMEOUT_MS; the kernel then
@@ -194,6 +195,20 @@ enum {
  * `out` is not read); with 0 it restarts every call.  Setting the option to a
  * positive value zeroes the running sum (after waiting for the device). */
 enum { XC_PREC_FP16 = 0, XC_PREC_HILO = 1, XC_PREC_FP8 = 2 };
+/* Tile shapes of XC_ENGINE_TENSOR (results are identical; only speed differs):
+ *   XC_TILE_128 : 128 x 128 complex blocks of V, one per CTA (tcgen05
+ *     cta_group::1, two TMEM accumulator sets).
+ *   XC_TILE_PAIR: two 128 x 128 blocks sharing a column block per pair of
+ *     CTAs on two SMs, one 256 x 128 MMA per step (tcgen05 cta_group::2);
+ *     each SM stages its 128 rows and half of the 128 columns.
+ *   XC_TILE_WIDE: two 128 x 128 blocks sharing a row block per CTA, one
+ *     128 x 256 MMA per step (N = 256; one TMEM accumulator set): a quarter
+ *     fewer shared-memory and L2 operand bytes per MAC than XC_TILE_128.  Not
+ *     with XC_PREC_HILO (XC_ERR_UNSUPPORTED at the call).
+ *   XC_TILE_AUTO: XC_TILE_128, the fastest shape measured on the Large-N
+ *     workload.  A batch handle takes the shape xc_batch_tune chose
+ *     (XC_TILE_AUTO restores the default). */
+enum { XC_TILE_AUTO = 0, XC_TILE_128 = 1, XC_TILE_PAIR = 2, XC_TILE_WIDE = 3 };
 /* Engines:
  *   XC_ENGINE_TENSOR (default): one fused persistent tcgen05 kernel in
  *     planar complex form (real and imaginary fp16 operand planes, four MMAs

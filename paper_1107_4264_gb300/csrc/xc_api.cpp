@@ -93,6 +93,8 @@ struct BatchState {
   unsigned* ctr_all = nullptr;
   int order[XC_BATCH_MAX_SUB];
   int depth = 1;
+  int shape = xc::kPlanar128;  // tile shape (xc::kPlanar*), tuned by xc_batch_tune
+  int shape_default = xc::kPlanar128;
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -126,6 +128,7 @@ struct xc_handle {
   // buffer [F][n] and the FP64 block sums (allocated on use).
   int precision = XC_PREC_FP16;
   int fp64_block = 0;
+  int tile = XC_TILE_AUTO;  // planar engine tile shape (XC_OPT_TILE)
   int test_no_publish = 0;
   unsigned* in_amax = nullptr;
   double* acc64 = nullptr;
@@ -164,6 +167,17 @@ xc_status encode_operand_map(CUtensorMap* map, void* base, int64_t R, int64_t Tp
 xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g,
                            xc_dtype dtype = XC_CI8);
 bool input_map_possible(xc_dtype dtype, const xc::Geometry& g);
+void batch_drop_graph(BatchState* b);
+
+// Planar tile shape for an XC_TILE_* option value (-1: not available).
+int planar_shape(int tile, const xc::Geometry& pg, int fmt) {
+  switch (tile) {
+    case XC_TILE_128: return xc::kPlanar128;
+    case XC_TILE_PAIR: return xc::kPlanarPair;
+    case XC_TILE_WIDE: return fmt == XC_PREC_HILO ? -1 : xc::kPlanarWide;
+    default: return xc::planar_default_shape(pg, fmt);
+  }
+}
 
 void release(xc_handle* h) {
   if (!h) return;
@@ -274,7 +288,9 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
       im = &in_map;
     }
     if (tm) tm->nkern = 1;
-    e = xc::launch_planar(im, X, s);
+    const int shape = planar_shape(h->tile, h->pg, X.in_dtype == 0 ? 0 : h->precision);
+    if (shape < 0) return fail(XC_ERR_UNSUPPORTED, "hi/lo operands do not run on XC_TILE_WIDE");
+    e = xc::launch_planar(im, X, shape, s);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core X-engine launch");
     if (tm) cudaEventRecord(tm->ev[1], s);
     return succeed();
@@ -634,6 +650,16 @@ xc_status xc_set_option(xc_handle* h, int key, long long value) {
       h->planar_slots = slots;
       return succeed();
     }
+    case XC_OPT_TILE:
+      if (value != XC_TILE_AUTO && value != XC_TILE_128 && value != XC_TILE_PAIR && value != XC_TILE_WIDE)
+        return fail(XC_ERR_INVALID_ARG, "unknown tile shape %lld", value);
+      if (h->batch) {
+        h->batch->shape = value == XC_TILE_AUTO ? h->batch->shape_default
+                                                : planar_shape(static_cast<int>(value), h->pg, 0);
+        batch_drop_graph(h->batch);
+      }
+      h->tile = static_cast<int>(value);
+      return succeed();
     case XC_OPT_TEST_NO_PUBLISH:
       if (value != 0 && value != 1) return fail(XC_ERR_INVALID_ARG, "TEST_NO_PUBLISH must be 0 or 1");
       h->test_no_publish = static_cast<int>(value);
@@ -941,7 +967,7 @@ void batch_drop_graph(BatchState* b) {
 // Launch descriptions of the subarrays in work-list order, their input
 // maps, and the kernel parameter block in b->k.
 xc_status batch_prepare(xc_handle* h, const void* const* in, void* const* out,
-                        const int* order, int depth, xc::XeLaunch* L) {
+                        const int* order, int depth, int shape, xc::XeLaunch* L) {
   BatchState* b = h->batch;
   if (!in || !out) return fail(XC_ERR_INVALID_ARG, "NULL pointer array");
   CUtensorMap maps[XC_BATCH_MAX_SUB];
@@ -974,7 +1000,7 @@ xc_status batch_prepare(xc_handle* h, const void* const* in, void* const* out,
       mp[j] = &maps[j];
     }
   }
-  cudaError_t e = xc::planar_prepare(L, mp, b->nsub, &b->k);
+  cudaError_t e = xc::planar_prepare(L, mp, b->nsub, &b->k, shape);
   if (e != cudaSuccess) return cuda_fail(e, "batch launch preparation");
   return XC_OK;
 }
@@ -1065,6 +1091,10 @@ xc_handle* xc_batch_create(int nsub, const int* nstation, const int* nfreq, cons
     b->order[i] = i;
   }
   b->depth = 1;
+  // The larger shape pays when some subarray has more than one block row.
+  for (int i = 0; i < nsub; ++i)
+    b->shape_default = std::max(b->shape_default, xc::planar_default_shape(b->sub[i].pg, 0));
+  b->shape = b->shape_default;
   succeed();
   return h;
 }
@@ -1074,7 +1104,7 @@ xc_status xc_batch_correlate(xc_handle* h, const void* const* in, void* const* o
   BatchState* b = h->batch;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   xc::XeLaunch L[XC_BATCH_MAX_SUB];
-  xc_status st = batch_prepare(h, in, out, b->order, b->depth, L);
+  xc_status st = batch_prepare(h, in, out, b->order, b->depth, b->shape, L);
   if (st != XC_OK) return st;
   if (b->k.grid <= 0) return succeed();
   cudaError_t e = cudaSuccess;
@@ -1148,7 +1178,7 @@ xc_status xc_batch_tune(xc_handle* h, const void* const* in, void* const* out, v
     int order[XC_BATCH_MAX_SUB], depth = 1;
     batch_schedule(b, c, order, &depth);
     xc::XeLaunch L[XC_BATCH_MAX_SUB];
-    st = batch_prepare(h, in, out, order, depth, L);
+    st = batch_prepare(h, in, out, order, depth, b->shape, L);
     if (st != XC_OK) break;
     float t = 0.f;
     for (int r = 0; r <= reps && e == cudaSuccess; ++r) {

@@ -27,6 +27,43 @@ XC_HD void tri_coords(int64_t g, int64_t* bx, int64_t* by) {
   *bx = g - y * (y + 1) / 2;
 }
 
+// Work items of the CTA-pair engine: the nib(nib+1)/2 lower blocks (r, c),
+// r >= c, of a channel with nib block rows, two per item, both sharing
+// their column block.  In column c the rows c, c+1, ... pair off from the
+// diagonal down (floor((nib-c)/2) items).  A column with an odd count leaves
+// its last block (nib-1, c); that block is taken transposed, as rows c times
+// columns nib-1 (the mirror block), so the leftovers of the columns
+// c = nib-1, nib-3, ... all have column block nib-1 and pair among
+// themselves, the very last one alone when their count is odd.
+XC_HD int pair_items(int nib) {
+  const int L = (nib + 1) / 2;  // leftovers
+  return nib * nib / 4 + (L + 1) / 2;
+}
+
+// Item i (0 <= i < pair_items(nib)): row blocks a0, a1 of the pair's two
+// CTAs and their common column block b.  a_k < b marks a transposed block;
+// *single is set when the item holds one block only (a1 repeats a0 and the
+// second CTA's result is discarded).
+XC_HD void pair_coords(int i, int nib, int* a0, int* a1, int* b, int* single) {
+  for (int c = 0; c < nib; ++c) {
+    const int m = (nib - c) / 2;
+    if (i < m) {
+      *a0 = c + 2 * i;
+      *a1 = *a0 + 1;
+      *b = c;
+      *single = 0;
+      return;
+    }
+    i -= m;
+  }
+  const int L = (nib + 1) / 2;
+  const int k0 = 2 * i, k1 = k0 + 1;
+  *b = nib - 1;
+  *a0 = nib - 1 - 2 * k0;
+  *single = k1 >= L ? 1 : 0;
+  *a1 = *single ? *a0 : nib - 1 - 2 * k1;
+}
+
 // Device status word bits.
 enum : int { kStatusTimeout = 1, kStatusRange = 2 };
 

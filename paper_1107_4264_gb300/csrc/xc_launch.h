@@ -58,8 +58,14 @@ cudaError_t launch_xengine(const CUtensorMap* tmap, const XeLaunch& p, cudaStrea
 // Planar complex form (separate real/imaginary fp16 planes, 4 MMAs per step
 // into D_re/D_im).  The ring holds planar_slot_bytes() per channel slot;
 // `in_map` (8-bit input with R % 16 == 0, else NULL) is {R, F, T} int8 in
-// 128 x 1 x 64 boxes.
-cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& p, cudaStream_t s);
+// 128 x 1 x 64 boxes.  shape: kPlanar128 (128 x 128 blocks on single CTAs),
+// kPlanarPair (two blocks sharing a column block on a CTA pair, tcgen05
+// cta_group::2) or kPlanarWide (two blocks sharing a row block on one CTA,
+// N = 256 MMAs).
+enum : int { kPlanar128 = 0, kPlanarPair = 1, kPlanarWide = 2 };
+cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& p, int shape, cudaStream_t s);
+// The default shape for a (virtual) geometry and operand format.
+int planar_default_shape(const Geometry& g, int fmt);
 constexpr int kMaxRingSlots = 256;
 // Samples per converter unit of the planar engine (8-bit input arrives by TMA
 // in 128-row x 1 x kPlanarUnitT boxes).
@@ -93,9 +99,11 @@ struct PlanarKernel {
   alignas(128) unsigned char args[kBatchArgBytes];  // holds the kernel's Batch (128-byte aligned)
   const void* func = nullptr;
   int grid = 0, block = 0, smem = 0;
+  int shape = kPlanar128;  // kPlanarPair: clusters of two, fixed in the kernel
 };
+// The grid is capped at the CTAs (clusters) that can be resident at once.
 cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps, int nsub,
-                           PlanarKernel* k);
+                           PlanarKernel* k, int shape);
 cudaError_t planar_setup(const XeLaunch* subs, int nsub, cudaStream_t s);
 cudaError_t planar_launch(PlanarKernel& k, cudaStream_t s);
 // Same as launch_xengine, on CTA pairs (tcgen05 cta_group::2, 256 x 256 blocks).

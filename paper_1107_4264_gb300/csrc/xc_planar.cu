@@ -1,1431 +1,20 @@
-// xc_planar.cu -- fused persistent tensor-core X-engine, planar complex form.
-//
-// Eq. (outer) of Sec. 2.1 per channel f: V_f = sum_t x_f(t) x_f(t)^H over
-// n = N*P complex inputs.  With the real and imaginary parts of the inputs
-// as separate fp16 operand planes Xr, Xi (n rows x T samples, K-major),
-//
-//     Re V = Xr Xr^T + Xi Xi^T,      Im V = Xi Xr^T - Xr Xi^T,
-//
-// so a 128 x 128 block of V (rows a, columns b) is four tcgen05 MMAs per
-// 16-sample step into two TMEM accumulators,
-//     D_re += Ar Br^T,  D_re += Ai Bi^T,  D_im += Ai Br^T,  D_im += Ar (-Bi)^T,
-// the last with the instruction descriptor's negate-B bit.  Four operand
-// tiles feed 4 MMAs (half the shared-memory and L2 bytes per MAC of the
-// interleaved real form) and every TMEM column is a finished visibility
-// component: the epilogue converts and stores, with no lane exchange.
-//
-// Exact 8-bit input: int8 is exact in fp16, products are exact in fp32, and
-// every partial sum of an accumulator is an integer bounded by the sum of
-// |products| so far: at most 2 m^2 per sample, m = max |x| of the channel.
-// The converters record m per channel; a chunk of S samples with
-// 2 m^2 S <= 2^24 is exact in fp32 in any summation order (S >= 512 for any
-// int8 data, the whole integration for typical 4-6 bit signal levels).  Each
-// chunk is drained into int32 and added into the output (stored for the
-// first chunk).  Float input accumulates in fp32 over the whole integration.
-//
-// Float input (Sec. 5 leaves its precision open): each (channel, input) gets
-// a power-of-two scale 2^e from a pre-pass over the integration (max
-// component of g x), so y 2^-e spans the operand format's range and the
-// epilogue multiplies by 2^(e_a + e_b) exactly.  Three operand formats:
-//   FP16   one fp16 plane pair, 4 MMAs per 16 samples;
-//   HI/LO  y 2^-e = h + l with h = fp16(.) and l = fp16(. - h); the ring
-//          holds H and L tiles and each 64-sample block runs three steps
-//          (H H^T, L H^T, H L^T; the l l^T term is dropped), 3x the MMAs;
-//   FP8    e4m3 planes (kind::f8f6f4, K = 32), half the operand bytes.
-// Optionally (FP64 block sums) the fp32 accumulator is drained every
-// T_blk samples into a float64 running sum; the output is its rounding.
-//
-// Blocks (Sec. 4.2): 128 x 128 blocks of V on or below the block diagonal,
-// g = by(by+1)/2 + bx; block edges fall on station boundaries (128 inputs =
-// 128/P stations).  Diagonal blocks load one pair of planes for both
-// operands and store only their lower station triangle (Sec. 4.4).
-//
-// Operand formation (Sec. 4.1 input order, Sec. 5 8-bit samples): converter
-// warps form each channel's planes once into a ring of channel slots in
-// global memory that stays in L2; the blocks of a channel read it back with
-// bulk copies.  The ring holds operand tiles exactly as the MMA reads them:
-// per (slot, plane, 64-sample K-block, 128-input block) one 16 KiB tile in
-// the no-swizzle K-major canonical layout [8-sample chunk][128 inputs][8],
-// so a stage is four contiguous 16 KiB copies and a converter lane writing
-// one input's 16-byte chunk next to its neighbours' fills whole lines.
-// 8-bit input arrives by TMA in 128-row x 64-sample boxes (other types and
-// row counts by direct loads); lane l converts inputs l and l + 32 of a
-// 64-input half block; each converter warp works through its own stream of
-// units.  Ring protocol:
-//   ready[slot] counts converted units (128 rows x 64 samples); channel c
-//     (generation c / slots of slot c % slots) is complete at
-//     ready >= (gen + 1) * units_per_channel;
-//   done[slot] counts blocks whose operands have landed in shared memory;
-//     slot s may take channel c once done >= gen(c) * blocks_per_channel.
-// Dependencies point only to lower channels and all CTAs are co-resident,
-// so the ring cannot deadlock; every wait is bounded regardless.
-//
-// CTA roles (persistent, one CTA per SM, channel-major items):
-//   warp 0      producer: 3 stages x (Ar, Ai, Br, Bi) 64-sample tiles (bulk copies)
-//   warp 1      MMA issuer; owns TMEM (2 sets x {D_re, D_im} x 128 columns)
-//   warps 2..5  epilogue
-//   warps 6..9  converters
-#include <cuda.h>
-#include <cuda_fp16.h>
-#include <cuda_fp8.h>
-
-#include <algorithm>
-#include <cstring>
-#include <type_traits>
-
-#include "xc_launch.h"
-#include "xc_ptx.cuh"
+// xc_planar.cu -- host side of the planar tensor-core X-engine (the kernel
+// template is xc_planar_kernel.cuh): the single-CTA instantiations, the
+// float scale pre-pass, the kernel parameter block, the ring geometry and
+// the launch (single CTAs, or CTA pairs from xc_planar_pair.cu).
+#include "xc_planar_kernel.cuh"
 
 namespace xc {
+
+// The CTA-pair and 128 x 256 instantiations live in xc_planar_pair.cu and
+// xc_planar_wide.cu (compiled in parallel with this file).
+const void* planar_pair_select(int in_dtype, int fmt, bool multi);
+const void* planar_wide_select(int in_dtype, int fmt, bool multi);
+
+static_assert(kShape128 == kPlanar128 && kShapePair == kPlanarPair && kShapeWide == kPlanarWide,
+              "tile shape codes");
+
 namespace {
-
-constexpr int kBlk = 128;      // complex inputs per block side
-constexpr int kBK = 64;        // samples per stage
-constexpr int kStages = 3;
-constexpr int kNumEpiWarps = 4;
-constexpr int kNumConvWarps = 4;
-constexpr int kThreads = 32 * (2 + kNumEpiWarps + kNumConvWarps);
-constexpr int kTileBytes = kBlk * kBK * 2;  // 16 KiB: one plane tile
-constexpr int kStageBytes = 4 * kTileBytes;
-constexpr uint32_t kTmemCols = 512;         // 2 sets x (D_re, D_im) x 128
-constexpr int kUnitRows = 128;  // converter unit: 128 real rows (64 inputs) x kUnitT samples
-constexpr int kUnitT = kPlanarUnitT;
-static_assert(kUnitT == 32 || kUnitT == 64, "a unit covers a whole or half 64-sample K-block");
-constexpr uint32_t kChunkStride = kBlk * 16;  // bytes between 8-sample chunks of a tile (K)
-constexpr uint32_t kGroupStride = 8 * 16;     // bytes between 8-input groups of a tile (M/N)
-constexpr int kConvBufBytes = kUnitRows * kUnitT;  // int8 staging per converter warp
-
-constexpr int kConvOff = kStages * kStageBytes;
-constexpr int kBarOff = kConvOff + kNumConvWarps * kConvBufBytes;
-constexpr int kNumBars = 2 * kStages + 5 + kNumConvWarps;
-constexpr int kSmemBytes = kBarOff + kNumBars * 8 + 16 + 1024;
-static_assert(kSmemBytes <= 232448, "shared memory budget");
-
-// Operand formats: tile size (log2 bytes), 16-byte K chunks per tile and
-// MMA steps per 64-sample block (ring K-tiles per block: fmt_kt()).
-enum : int { kFmtF16 = 0, kFmtHiLo = 1, kFmtF8 = 2 };
-template <int FMT>
-struct FmtT {
-  static constexpr int kTileShift = FMT == kFmtF8 ? 13 : 14;
-  static constexpr int kTile = 1 << kTileShift;
-  static constexpr int kChunks = FMT == kFmtF8 ? 4 : 8;
-  static constexpr int kSteps = FMT == kFmtHiLo ? 3 : 1;
-};
-
-struct Params {
-  Geometry g;
-  int n;               // complex inputs per channel = N * P
-  const void* in;
-  void* out;
-  int accumulate;
-  int ntiles;          // lower blocks per channel
-  long long nitems;    // ntiles * F
-  int nkb;             // Tp / 64
-  int is_int;          // 8-bit input: exact chunks from the channel's max |x|
-  unsigned* amax;      // [F] max |x| per channel (8-bit input), zeroed by the host
-  const float2* gains; // [n] complex gains applied to float input (y = g x), or NULL
-  const unsigned* in_amax;  // [F][n] max component of g x (float bits), float input
-  double* acc64;       // FP64 block sums: running visibility sums (output layout), or NULL
-  int f_chunk_kb;      // float input: K-blocks per fp32 accumulation chunk
-  uint8_t* ring;       // tiles [slots][2][nkt][nib][chunks][128][16 B]
-  int nkt;             // K-tiles per plane per input block of a slot (nkb or 2 nkb)
-  int nib;             // 128-input blocks per channel
-  int ring_slots;
-  unsigned* ready;
-  unsigned* done;
-  int row_units;       // 64-input half blocks per channel = 2 * nib
-  int units_per_chan;  // row_units * Tp / 64
-  int tma_in;          // 8-bit input staged by TMA (else direct loads)
-  unsigned long long timeout_ns;
-  int* status;
-  int test_no_publish;  // test hook: converted units are never published
-  // Small arrays: `pack` consecutive channels form one virtual channel of
-  // pack * Nr stations (g, n, F above are the virtual geometry; the input
-  // [T][F][n] is the same memory as [T][F / pack][pack * n]).  The epilogue
-  // keeps only each real channel's own block and stores it at real indices.
-  int pack;
-  int Nr;              // real stations per channel
-  int64_t NBr;         // real baselines per channel
-  int gain_n;          // real inputs per channel (gains are indexed a mod gain_n)
-};
-
-// One launch over up to kMaxSub subarrays (Sec. 4.2's channel-major raster
-// extended across subarrays): items and converter units are numbered
-// subarray by subarray; item_base / unit_base are their prefix sums.  Each
-// subarray has its own ring region and counters.
-struct Batch {
-  CUtensorMap maps[kMaxSub];  // 8-bit input of each subarray (read when tma_in)
-  Params sub[kMaxSub];
-  long long item_base[kMaxSub + 1];
-  long long unit_base[kMaxSub + 1];
-  int nsub;
-};
-static_assert(sizeof(Batch) <= kBatchArgBytes && alignof(Batch) <= 128, "batch parameter block");
-
-// Subarray holding global index i, starting the search at cursor s (every
-// role walks its items and units in increasing order).  Single-subarray
-// launches (MULTI = false) index subarray 0 at compile time.
-// End of a prefix-sum table (compile-time index for single launches).
-template <bool MULTI>
-__device__ __forceinline__ long long table_end(const long long* base, int nsub) {
-  if constexpr (!MULTI) {
-    return base[1];
-  } else {
-    return base[nsub];
-  }
-}
-
-template <bool MULTI>
-__device__ __forceinline__ int advance_sub(const long long* base, int nsub, long long i, int s) {
-  if constexpr (!MULTI) {
-    return 0;
-  } else {
-    while (s + 1 < nsub && i >= base[s + 1]) ++s;
-    return s;
-  }
-}
-
-// ------------------------------------------------------------ global sync
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-__device__ __noinline__ bool wait_counter(const unsigned* p, unsigned target, const Params& prm,
-                                          volatile int* abort_flag) {
-  if (ld_acquire(p) >= target) return true;
-  const uint64_t t0 = ptx::globaltimer();
-  for (uint32_t it = 1;; ++it) {
-    __nanosleep(64);
-    if (ld_acquire(p) >= target) return true;
-    if ((it & 15u) == 0) {
-      if (*abort_flag) return false;
-      if (*reinterpret_cast<volatile int*>(prm.status) != 0) {
-        *abort_flag = 1;
-        return false;
-      }
-      if (ptx::globaltimer() - t0 > prm.timeout_ns) {
-        *abort_flag = 1;
-        atomicOr(prm.status, kStatusTimeout);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void item_coords(long long it, int ntiles, int* f, int* bx, int* by) {
-  *f = static_cast<int>(it / ntiles);
-  int64_t x, y;
-  tri_coords(it % ntiles, &x, &y);
-  *bx = static_cast<int>(x);
-  *by = static_cast<int>(y);
-}
-
-// K-blocks per exact fp32 accumulation chunk for channel f (all K-blocks for
-// float input).  Called after the channel is known to be fully converted.
-__device__ __forceinline__ int chunk_kblocks(const Params& p, int f) {
-  if (!p.is_int) return p.f_chunk_kb;
-  const unsigned m = *reinterpret_cast<volatile const unsigned*>(p.amax + f);
-  if (m == 0) return p.nkb;
-  const unsigned long long per_block = 2ull * m * m * kBK;  // |partial| growth per K-block
-  const unsigned long long kb = (1ull << 24) / per_block;
-  return static_cast<int>(kb < 1 ? 1 : (kb > static_cast<unsigned long long>(p.nkb) ? p.nkb : kb));
-}
-
-// Wait (bounded) until channel f is fully converted into its ring slot.
-__device__ __forceinline__ bool channel_ready(const Params& p, int f, volatile int* abort_flag) {
-  const unsigned gen = static_cast<unsigned>(f / p.ring_slots);
-  return wait_counter(p.ready + f % p.ring_slots, (gen + 1) * static_cast<unsigned>(p.units_per_chan),
-                      p, abort_flag);
-}
-
-// -------------------------------------------------------------- converter
-
-// fp16x2 of (component j of sample a, component j of sample b), 8-bit input.
-__device__ __forceinline__ uint32_t pair_i8(uint32_t a, uint32_t b, uint32_t j) {
-  // Byte j of a into byte 0 and byte j of b into byte 2; 0x6400 | (x ^ 0x80)
-  // is the fp16 value 1152 + x, so subtracting 1152 gives x exactly.
-  uint32_t d = __byte_perm(a, b, j | ((j + 4u) << 8));
-  d = (d & 0x00FF00FFu) ^ 0x64806480u;
-  __half2 h = *reinterpret_cast<__half2*>(&d);
-  h = __hsub2(h, __half2(__float2half_rn(1152.f), __float2half_rn(1152.f)));
-  return *reinterpret_cast<uint32_t*>(&h);
-}
-
-// Byte address of tile (slot, plane, K-tile kt, ib) in the ring.
-template <int FMT>
-__device__ __forceinline__ uint8_t* ring_tile(const Params& p, int slot, int plane, int kt, int ib) {
-  return p.ring + ((((static_cast<int64_t>(slot) * 2 + plane) * p.nkt + kt) * p.nib + ib)
-                   << FmtT<FMT>::kTileShift);
-}
-
-// Power-of-two scale exponent e for an input whose largest component is
-// `bits` (fp32 bits): max |y| 2^-e lies in [2^14, 2^15) for the fp16 forms
-// and in (2^7, 448] for e4m3.  Zero or subnormal maxima are not scaled;
-// e is clamped to [-60, 60] so that 2^(e_a + e_b) is a normal float.
-template <int FMT>
-__device__ __forceinline__ int scale_exp(unsigned bits) {
-  const int E = static_cast<int>((bits >> 23) & 0xffu);
-  if (E == 0) return 0;
-  int e = E - 127 - (FMT == kFmtF8 ? 8 : 14);
-  if (FMT == kFmtF8 && (bits & 0x7fffffu) > 0x600000u) ++e;  // 256 (1 + m) > 448
-  return max(-60, min(60, e));
-}
-__device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }
-
-// A unit: 64 inputs (half block hb) x kUnitT samples (unit ku along K) of
-// channel c, units numbered channel-major with K fastest; it fills 8-sample
-// chunks cbase .. cbase + kUnitT/8 - 1 of the tiles of K-block kb.
-struct Unit {
-  int c, slot, hb, ku, kb, cbase;
-};
-
-__device__ __forceinline__ Unit unit_of(const Params& p, long long u) {
-  Unit x;
-  x.c = static_cast<int>(u / p.units_per_chan);
-  const int w = static_cast<int>(u % p.units_per_chan);
-  x.slot = x.c % p.ring_slots;
-  const int nku = p.nkb * (kBK / kUnitT);
-  x.hb = w / nku;
-  x.ku = w % nku;
-  x.kb = x.ku * kUnitT / kBK;
-  x.cbase = (x.ku * kUnitT % kBK) / 8;
-  return x;
-}
-
-// Before a warp first writes channel c into its slot: the slot's previous
-// channel (c - ring_slots) must have been read by all of its blocks.
-__device__ __forceinline__ bool claim_slot_warp(const Params& p, int c, int lane,
-                                                volatile int* abort_flag) {
-  const unsigned gen = static_cast<unsigned>(c / p.ring_slots);
-  bool ok = true;
-  if (gen > 0 && lane == 0)
-    ok = wait_counter(p.done + (c % p.ring_slots), gen * static_cast<unsigned>(p.ntiles), p, abort_flag);
-  // No proxy fence here: every bulk read of the slot's previous channel has
-  // completed (its data sat in shared memory before the MMA thread released
-  // done[slot]), so the generic writes that follow cannot reach it.
-  return __all_sync(0xffffffffu, ok);
-}
-
-// Would a claim of channel c's slot have to wait for the slot's previous
-// channel?  (Checked before a warp waits while it holds an unpublished unit.)
-__device__ __forceinline__ bool slot_busy(const Params& p, int c, int lane) {
-  const unsigned gen = static_cast<unsigned>(c / p.ring_slots);
-  bool busy = false;
-  if (gen > 0 && lane == 0)
-    busy = ld_acquire(p.done + (c % p.ring_slots)) < gen * static_cast<unsigned>(p.ntiles);
-  return __any_sync(0xffffffffu, busy);
-}
-
-// Publish one converted unit: every writing lane orders its generic stores
-// before later async-proxy (bulk copy) reads, then one release.
-__device__ __forceinline__ void publish_unit(const Params& p, int slot, int lane, unsigned n = 1) {
-  if (p.test_no_publish) {  // failure-detection test: every consumer wait runs out
-    __syncwarp();
-    return;
-  }
-  fence_proxy_async_global();
-  __syncwarp();
-  if (lane == 0) red_release_add(p.ready + slot, n);
-}
-
-// Converter warps take their units in runs of kUnitRun consecutive units
-// (the same channel except at channel ends): one slot claim and one publish
-// (fence + release of the whole count) per run instead of per unit.  Warp gw
-// of nw takes runs gw, gw + nw, gw + 2 nw, ... of the global unit list.
-constexpr int kUnitRun = 2;
-__device__ __forceinline__ long long first_unit(long long gw) { return gw * kUnitRun; }
-__device__ __forceinline__ long long next_unit(long long u, long long nw) {
-  return (u % kUnitRun != kUnitRun - 1) ? u + 1 : u + 1 + (nw - 1) * kUnitRun;
-}
-
-// Complex sample (re, im) of input a at sample t, channel c, as fp32.
-template <int DT>
-__device__ __forceinline__ float2 load_cx(const Params& p, int c, int a, int t) {
-  const int64_t idx = (static_cast<int64_t>(t) * p.g.F + c) * p.n + a;
-  if constexpr (DT == 0) {
-    const char2 v = static_cast<const char2*>(p.in)[idx];
-    return make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
-  } else if constexpr (DT == 1) {
-    return __half22float2(static_cast<const __half2*>(p.in)[idx]);
-  } else {
-    return static_cast<const float2*>(p.in)[idx];
-  }
-}
-
-// fp16x2 bits of (a, b).
-__device__ __forceinline__ uint32_t h2bits(float a, float b) {
-  __half2 q = __floats2half2_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&q);
-}
-// fp16x2 bits of the residuals (a - fp16(a), b - fp16(b)) given h = fp16x2(a, b).
-__device__ __forceinline__ uint32_t lo2bits(float a, float b, uint32_t h) {
-  const __half2 hh = *reinterpret_cast<const __half2*>(&h);
-  return h2bits(a - __low2float(hh), b - __high2float(hh));
-}
-// Four e4m3 bytes (a, b, c, d), a in the low byte, rounded to nearest with
-// saturation to +-448.
-__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
-  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-  return (lo & 0xffffu) | (hi << 16);
-}
-
-// Direct-load converter (any input type and row count), independent warps:
-// lane l loads the complex samples of inputs l and l + 32 of the half block,
-// 16 samples (32 loads) in flight at a time, applies the gains and the
-// input's power-of-two scale (float input) and writes 16-byte chunks: per
-// (input, plane) two fp16 chunks (8 samples each; HI/LO: two more into the
-// L tile) or one e4m3 chunk (16 samples).
-template <int DT, int FMT, bool MULTI>
-__device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int* abort_flag) {
-  const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
-  const long long stride = static_cast<long long>(gridDim.x) * kNumConvWarps;
-  int sb = 0, claimed = -1, claimed_sb = -1;
-  for (long long u = static_cast<long long>(blockIdx.x) * kNumConvWarps + cw; u < total; u += stride) {
-    sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
-    const Params& p = bt.sub[sb];
-    const Unit x = unit_of(p, u - bt.unit_base[sb]);
-    if (x.c != claimed || sb != claimed_sb) {
-      if (!claim_slot_warp(p, x.c, lane, abort_flag)) return;
-      claimed = x.c;
-      claimed_sb = sb;
-    }
-    const int ib = x.hb >> 1;
-    uint8_t* tre = ring_tile<FMT>(p, x.slot, 0, x.kb, ib);
-    uint8_t* tim = ring_tile<FMT>(p, x.slot, 1, x.kb, ib);
-    const int a0 = x.hb * 64 + lane, a1 = a0 + 32;
-    const int row0 = (x.hb & 1) * 64 + lane;
-    // y = g x 2^-e (float input; gains are not defined for 8-bit input).
-    float2 g0 = make_float2(1.f, 0.f), g1 = make_float2(1.f, 0.f);
-    if (DT != 0) {
-      if (p.gains) {
-        g0 = a0 < p.n ? p.gains[a0 % p.gain_n] : make_float2(0.f, 0.f);
-        g1 = a1 < p.n ? p.gains[a1 % p.gain_n] : make_float2(0.f, 0.f);
-      }
-      if (p.in_amax) {
-        const unsigned* am = p.in_amax + static_cast<int64_t>(x.c) * p.n;
-        const float s0 = a0 < p.n ? exp2i(-scale_exp<FMT>(am[a0])) : 0.f;
-        const float s1 = a1 < p.n ? exp2i(-scale_exp<FMT>(am[a1])) : 0.f;
-        g0 = make_float2(g0.x * s0, g0.y * s0);  // exact: s is a power of two
-        g1 = make_float2(g1.x * s1, g1.y * s1);
-      }
-    }
-    const bool apply = DT != 0 && (p.gains || p.in_amax);
-    bool unit_over_16 = false;
-#pragma unroll 1
-    for (int g = 0; g < kUnitT / 16; ++g) {
-      float2 v0[16], v1[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int t = x.ku * kUnitT + g * 16 + i;
-        v0[i] = (a0 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a0, t) : make_float2(0.f, 0.f);
-        v1[i] = (a1 < p.n && t < p.g.T) ? load_cx<DT>(p, x.c, a1, t) : make_float2(0.f, 0.f);
-      }
-      if constexpr (DT == 0 && FMT == kFmtF8) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          unit_over_16 |= fmaxf(fmaxf(fabsf(v0[i].x), fabsf(v0[i].y)),
-                                fmaxf(fabsf(v1[i].x), fabsf(v1[i].y))) > 16.f;
-      }
-      if (apply) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          v0[i] = make_float2(g0.x * v0[i].x - g0.y * v0[i].y, g0.x * v0[i].y + g0.y * v0[i].x);
-          v1[i] = make_float2(g1.x * v1[i].x - g1.y * v1[i].y, g1.x * v1[i].y + g1.y * v1[i].x);
-        }
-      }
-      if constexpr (FMT == kFmtF8) {
-        const uint32_t off = (x.cbase / 2 + g) * kChunkStride + row0 * 16;
-        uint32_t r0[4], i0[4], r1[4], i1[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float2* A = v0 + 4 * k;
-          const float2* B = v1 + 4 * k;
-          r0[k] = e4m3x4(A[0].x, A[1].x, A[2].x, A[3].x);
-          i0[k] = e4m3x4(A[0].y, A[1].y, A[2].y, A[3].y);
-          r1[k] = e4m3x4(B[0].x, B[1].x, B[2].x, B[3].x);
-          i1[k] = e4m3x4(B[0].y, B[1].y, B[2].y, B[3].y);
-        }
-        *reinterpret_cast<uint4*>(tre + off) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
-        *reinterpret_cast<uint4*>(tim + off) = make_uint4(i0[0], i0[1], i0[2], i0[3]);
-        *reinterpret_cast<uint4*>(tre + off + 32 * 16) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
-        *reinterpret_cast<uint4*>(tim + off + 32 * 16) = make_uint4(i1[0], i1[1], i1[2], i1[3]);
-      } else {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t off = (x.cbase + 2 * g + h) * kChunkStride + row0 * 16;
-          uint32_t r0[4], i0[4], r1[4], i1[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float2 a = v0[8 * h + 2 * k], b = v0[8 * h + 2 * k + 1];
-            const float2 c = v1[8 * h + 2 * k], d = v1[8 * h + 2 * k + 1];
-            r0[k] = h2bits(a.x, b.x);
-            i0[k] = h2bits(a.y, b.y);
-            r1[k] = h2bits(c.x, d.x);
-            i1[k] = h2bits(c.y, d.y);
-          }
-          *reinterpret_cast<uint4*>(tre + off) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
-          *reinterpret_cast<uint4*>(tim + off) = make_uint4(i0[0], i0[1], i0[2], i0[3]);
-          *reinterpret_cast<uint4*>(tre + off + 32 * 16) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
-          *reinterpret_cast<uint4*>(tim + off + 32 * 16) = make_uint4(i1[0], i1[1], i1[2], i1[3]);
-          if constexpr (FMT == kFmtHiLo) {
-            // Residual tile of the same K-block: K-tile nkb + kb.
-            const int64_t lo_off = static_cast<int64_t>(p.nkb) * p.nib << FmtT<FMT>::kTileShift;
-            uint32_t l0[4], m0[4], l1[4], m1[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const float2 a = v0[8 * h + 2 * k], b = v0[8 * h + 2 * k + 1];
-              const float2 c = v1[8 * h + 2 * k], d = v1[8 * h + 2 * k + 1];
-              l0[k] = lo2bits(a.x, b.x, r0[k]);
-              m0[k] = lo2bits(a.y, b.y, i0[k]);
-              l1[k] = lo2bits(c.x, d.x, r1[k]);
-              m1[k] = lo2bits(c.y, d.y, i1[k]);
-            }
-            *reinterpret_cast<uint4*>(tre + lo_off + off) = make_uint4(l0[0], l0[1], l0[2], l0[3]);
-            *reinterpret_cast<uint4*>(tim + lo_off + off) = make_uint4(m0[0], m0[1], m0[2], m0[3]);
-            *reinterpret_cast<uint4*>(tre + lo_off + off + 32 * 16) =
-                make_uint4(l1[0], l1[1], l1[2], l1[3]);
-            *reinterpret_cast<uint4*>(tim + lo_off + off + 32 * 16) =
-                make_uint4(m1[0], m1[1], m1[2], m1[3]);
-          }
-        }
-      }
-    }
-    if (DT == 0 && lane == 0) atomicMax(p.amax + x.c, 128u);  // no scan: worst case
-    if (DT == 0 && FMT == kFmtF8 && __any_sync(0xffffffffu, unit_over_16) && lane == 0)
-      atomicOr(p.status, kStatusRange);  // e4m3 is exact only for |x| <= 16
-    publish_unit(p, x.slot, lane);
-    if (*abort_flag) return;
-  }
-}
-
-// Bounded wait for the warp's TMA box still in flight (completing phase
-// `phase` of `bar`): a converter that gives up never leaves a copy landing in
-// shared memory after it has returned.
-__device__ __forceinline__ void drain_tma(uint32_t bar, uint32_t phase, bool pending,
-                                          unsigned long long timeout_ns) {
-  if (pending) {
-    const uint64_t t0 = ptx::globaltimer();
-    while (!ptx::mbar_try_wait(bar, phase) && ptx::globaltimer() - t0 < timeout_ns) {
-    }
-  }
-  __syncwarp();
-}
-
-// 8-bit converter with TMA-staged input.  Each converter warp is an
-// independent worker on its own stream of units (u = global warp id + k *
-// warps, channel-major), with an 8 KiB staging buffer ([64 samples][128
-// rows] int8 = 64 inputs x {re, im}) that always holds its next unit's box
-// in flight while the current one is converted.  A warp claims a slot for
-// itself and publishes each unit on its own: no barrier couples the warps.
-// A unit is published after the next unit's shared-memory reads, so its
-// stores have drained by the time the proxy fence waits for them; a warp
-// that would have to wait for a slot publishes first (a consumer of the
-// slot's previous channel may need that unit).
-template <int FMT, bool MULTI>
-__device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int cw, int lane,
-                              volatile int* abort_flag) {
-  static_assert(FMT == kFmtF16 || FMT == kFmtF8, "8-bit input: fp16 or e4m3 operands");
-  const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
-  const long long nw = static_cast<long long>(gridDim.x) * kNumConvWarps;
-  const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
-  int sb_issue = 0;
-  bool tma_pending = false;  // a box issued and not yet waited for
-  auto issue = [&](long long u) {
-    tma_pending = true;
-    sb_issue = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb_issue);
-    const Unit x = unit_of(bt.sub[sb_issue], u - bt.unit_base[sb_issue]);
-    if (lane == 0) {
-      ptx::mbar_arrive_expect_tx(bar, kConvBufBytes);
-      // The input streams through once: first in line for L2 replacement, so
-      // the operand ring it is converted into stays resident.
-      ptx::tma_load_3d_hint(buf, &bt.maps[sb_issue], bar, x.hb * kUnitRows, x.c, x.ku * kUnitT,
-                            ptx::l2_policy_evict_first());
-    }
-  };
-  const uint32_t* src = reinterpret_cast<const uint32_t*>(__cvta_shared_to_generic(static_cast<size_t>(buf)));
-  // Lane l converts inputs 2l and 2l + 1 of the half block: word l of each
-  // 128-byte sample row holds (re, im) of both.  Per 8-sample chunk and plane
-  // the lane writes tile rows 2l and 2l + 1 (32 contiguous bytes), so a warp
-  // store covers 1 KiB.
-  uint32_t phase = 0;
-  int sb = 0, claimed = -1, claimed_sb = -1;
-  // Converted units not yet published: their subarray, slot, channel, count.
-  const Params* pend = nullptr;
-  int pend_slot = 0, pend_c = -1, pend_sb = -1;
-  unsigned pend_n = 0;
-  long long u = first_unit(static_cast<long long>(blockIdx.x) * kNumConvWarps + cw);
-  if (u < total) issue(u);
-  for (; u < total; u = next_unit(u, nw)) {
-    sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
-    const Params& p = bt.sub[sb];
-    const Unit x = unit_of(p, u - bt.unit_base[sb]);
-    if (x.c != claimed || sb != claimed_sb) {
-      if (pend && slot_busy(p, x.c, lane)) {
-        publish_unit(*pend, pend_slot, lane, pend_n);
-        pend = nullptr;
-      }
-      if (!claim_slot_warp(p, x.c, lane, abort_flag)) {
-        drain_tma(bar, phase, tma_pending, wc.timeout_ns);
-        return;
-      }
-      claimed = x.c;
-      claimed_sb = sb;
-    }
-    const bool got = ptx::wait_bounded(bar, phase, wc);
-    if (!__all_sync(0xffffffffu, got)) {
-      drain_tma(bar, phase, tma_pending, wc.timeout_ns);
-      return;
-    }
-    tma_pending = false;
-    phase ^= 1u;
-    // Both inputs' kUnitT samples into registers, then refill the buffer.
-    uint32_t w[kUnitT];
-#pragma unroll
-    for (int t = 0; t < kUnitT; ++t) w[t] = src[t * (kUnitRows / 4) + lane];
-    __syncwarp();
-    ptx::fence_proxy_async_smem();
-    const long long un = next_unit(u, nw);
-    if (un < total) issue(un);
-    // A finished run (or the units of another channel) is published now: its
-    // stores have drained during this unit's shared-memory reads.
-    if (pend && (pend_n == kUnitRun || pend_c != x.c || pend_sb != sb)) {
-      publish_unit(*pend, pend_slot, lane, pend_n);
-      pend = nullptr;
-    }
-    const int ib = x.hb >> 1;
-    uint8_t* tre = ring_tile<FMT>(p, x.slot, 0, x.kb, ib);
-    uint8_t* tim = ring_tile<FMT>(p, x.slot, 1, x.kb, ib);
-    const int row = (x.hb & 1) * 64 + 2 * lane;  // tile rows 2l and 2l + 1
-    // Ring tiles are read back by every block of the channel: keep them in L2.
-    const uint64_t pol_last = ptx::l2_policy_evict_last();
-    unsigned m = 0;  // max |x| over the unit (zero-filled rows and samples contribute 0)
-    if constexpr (FMT == kFmtF16) {
-      // max |x| from the converted (exact) fp16 values.
-      __half2 mx[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) mx[q] = __float2half2_rn(0.f);
-      // Rows 2l and 2l + 1 of one plane: bytes j and j + 2 of the words.
-      auto store8 = [&](uint8_t* dst, const uint32_t* W, uint32_t j, __half2& mq) {
-        uint32_t v[8];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          v[k] = pair_i8(W[2 * k], W[2 * k + 1], j);
-          v[4 + k] = pair_i8(W[2 * k], W[2 * k + 1], j + 2);
-        }
-#pragma unroll
-        for (int k = 0; k < 8; k += 2)
-          mq = __hmax2(mq, __hmax2(__habs2(*reinterpret_cast<const __half2*>(&v[k])),
-                                   __habs2(*reinterpret_cast<const __half2*>(&v[k + 1]))));
-        ptx::st_global_v8_hint(dst, v, pol_last);
-      };
-#pragma unroll
-      for (int cc = 0; cc < kUnitT / 8; ++cc) {
-        const uint32_t off = (x.cbase + cc) * kChunkStride + row * 16;
-        store8(tre + off, w + 8 * cc, 0u, mx[0]);
-        store8(tim + off, w + 8 * cc, 1u, mx[1]);
-      }
-      const __half2 mm = __hmax2(mx[0], mx[1]);
-      m = static_cast<unsigned>(fmaxf(__low2float(mm), __high2float(mm)));
-    } else {
-      // e4m3 operands: exact for |x| <= 16 (a larger value sets the range
-      // status bit below).  16-sample chunks; rows 2l and 2l + 1 per store.
-      uint32_t mb = 0;  // per-byte |x| maximum
-#pragma unroll
-      for (int t = 0; t < kUnitT; ++t) mb = __vmaxu4(mb, __vabs4(w[t]));
-      m = max(max(mb & 0xffu, (mb >> 8) & 0xffu), max((mb >> 16) & 0xffu, mb >> 24));
-      auto cvt4 = [](uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t j) {
-        auto f = [j](uint32_t wv) {
-          return static_cast<float>(static_cast<int8_t>((wv >> (8 * j)) & 0xffu));
-        };
-        return e4m3x4(f(w0), f(w1), f(w2), f(w3));
-      };
-#pragma unroll
-      for (int cc = 0; cc < kUnitT / 16; ++cc) {
-        const uint32_t off = (x.cbase / 2 + cc) * kChunkStride + row * 16;
-        const uint32_t* W = w + 16 * cc;
-        uint32_t vr[8], vi[8];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          vr[k] = cvt4(W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3], 0);
-          vi[k] = cvt4(W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3], 1);
-          vr[4 + k] = cvt4(W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3], 2);
-          vi[4 + k] = cvt4(W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3], 3);
-        }
-        ptx::st_global_v8_hint(tre + off, vr, pol_last);
-        ptx::st_global_v8_hint(tim + off, vi, pol_last);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) {
-      atomicMax(p.amax + x.c, m);
-      if (FMT == kFmtF8 && m > 16) atomicOr(p.status, kStatusRange);
-    }
-    if (pend) {
-      ++pend_n;
-    } else {
-      pend = &p;
-      pend_slot = x.slot;
-      pend_c = x.c;
-      pend_sb = sb;
-      pend_n = 1;
-    }
-    if (*abort_flag) {
-      drain_tma(bar, phase, tma_pending, wc.timeout_ns);
-      return;
-    }
-  }
-  if (pend) publish_unit(*pend, pend_slot, lane, pend_n);
-}
-
-// Convert 16 samples of two inputs (v0: input a0, v1: input a1 = a0 + 32;
-// gains and scale already applied) into the tiles of one K-block: fp16 (two
-// 8-sample chunks from chunk8), hi/lo (the same in the H tiles plus the
-// residuals in the L tiles) or e4m3 (one 16-sample chunk).
-template <int FMT>
-__device__ __forceinline__ void store_group16(const Params& p, uint8_t* tre, uint8_t* tim, int row0,
-                                              int chunk8, const float2 (&v0)[16],
-                                              const float2 (&v1)[16], uint64_t pol) {
-  auto st = [&](uint8_t* dst, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    ptx::st_global_v4_hint(dst, a, b, c, d, pol);
-  };
-  if constexpr (FMT == kFmtF8) {
-    const uint32_t off = (chunk8 / 2) * kChunkStride + row0 * 16;
-    uint32_t r0[4], i0[4], r1[4], i1[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float2* A = v0 + 4 * k;
-      const float2* B = v1 + 4 * k;
-      r0[k] = e4m3x4(A[0].x, A[1].x, A[2].x, A[3].x);
-      i0[k] = e4m3x4(A[0].y, A[1].y, A[2].y, A[3].y);
-      r1[k] = e4m3x4(B[0].x, B[1].x, B[2].x, B[3].x);
-      i1[k] = e4m3x4(B[0].y, B[1].y, B[2].y, B[3].y);
-    }
-    st(tre + off, r0[0], r0[1], r0[2], r0[3]);
-    st(tim + off, i0[0], i0[1], i0[2], i0[3]);
-    st(tre + off + 32 * 16, r1[0], r1[1], r1[2], r1[3]);
-    st(tim + off + 32 * 16, i1[0], i1[1], i1[2], i1[3]);
-  } else {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t off = (chunk8 + h) * kChunkStride + row0 * 16;
-      uint32_t r0[4], i0[4], r1[4], i1[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float2 a = v0[8 * h + 2 * k], b = v0[8 * h + 2 * k + 1];
-        const float2 c = v1[8 * h + 2 * k], d = v1[8 * h + 2 * k + 1];
-        r0[k] = h2bits(a.x, b.x);
-        i0[k] = h2bits(a.y, b.y);
-        r1[k] = h2bits(c.x, d.x);
-        i1[k] = h2bits(c.y, d.y);
-      }
-      st(tre + off, r0[0], r0[1], r0[2], r0[3]);
-      st(tim + off, i0[0], i0[1], i0[2], i0[3]);
-      st(tre + off + 32 * 16, r1[0], r1[1], r1[2], r1[3]);
-      st(tim + off + 32 * 16, i1[0], i1[1], i1[2], i1[3]);
-      if constexpr (FMT == kFmtHiLo) {
-        // Residual tile of the same K-block: K-tile nkb + kb.
-        const int64_t lo_off = static_cast<int64_t>(p.nkb) * p.nib << FmtT<FMT>::kTileShift;
-        uint32_t l0[4], m0[4], l1[4], m1[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float2 a = v0[8 * h + 2 * k], b = v0[8 * h + 2 * k + 1];
-          const float2 c = v1[8 * h + 2 * k], d = v1[8 * h + 2 * k + 1];
-          l0[k] = lo2bits(a.x, b.x, r0[k]);
-          m0[k] = lo2bits(a.y, b.y, i0[k]);
-          l1[k] = lo2bits(c.x, d.x, r1[k]);
-          m1[k] = lo2bits(c.y, d.y, i1[k]);
-        }
-        st(tre + lo_off + off, l0[0], l0[1], l0[2], l0[3]);
-        st(tim + lo_off + off, m0[0], m0[1], m0[2], m0[3]);
-        st(tre + lo_off + off + 32 * 16, l1[0], l1[1], l1[2], l1[3]);
-        st(tim + lo_off + off + 32 * 16, m1[0], m1[1], m1[2], m1[3]);
-      }
-    }
-  }
-}
-
-// Float converter with TMA-staged input: boxes of 64 inputs x kFBox samples
-// (8 KiB: complex fp16, 32 samples, or complex fp32, 16 samples) pass
-// through the warp's one staging buffer, kUnitT / kFBox boxes per unit;
-// while one box is converted the next (of this unit or of the next) is in
-// flight.  Units are taken in runs and published as in converter_tma.
-template <int DT, int FMT, bool MULTI>
-__device__ void converter_tma_float(const Batch& bt, uint32_t buf, uint32_t bar, int cw, int lane,
-                                    volatile int* abort_flag) {
-  constexpr int kCx = DT == 1 ? 4 : 8;  // bytes per complex sample
-  constexpr int kFBox = kConvBufBytes / (64 * kCx);
-  constexpr int kBoxes = kUnitT / kFBox;
-  static_assert(kFBox % 16 == 0 && kUnitT % kFBox == 0, "boxes hold whole 16-sample groups");
-  const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
-  const long long nw = static_cast<long long>(gridDim.x) * kNumConvWarps;
-  const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
-  int sb_issue = 0;
-  bool tma_pending = false;  // a box issued and not yet waited for
-  auto issue = [&](long long u, int j) {
-    tma_pending = true;
-    sb_issue = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb_issue);
-    const Unit x = unit_of(bt.sub[sb_issue], u - bt.unit_base[sb_issue]);
-    if (lane == 0) {
-      ptx::mbar_arrive_expect_tx(bar, kConvBufBytes);
-      // Map elements: one complex fp16 (32-bit) or one fp32 component.
-      const int ex = DT == 1 ? x.hb * 64 : x.hb * 128;
-      ptx::tma_load_3d_hint(buf, &bt.maps[sb_issue], bar, ex, x.c, x.ku * kUnitT + j * kFBox,
-                            ptx::l2_policy_evict_first());
-    }
-  };
-  const uint8_t* src = reinterpret_cast<const uint8_t*>(__cvta_shared_to_generic(static_cast<size_t>(buf)));
-  const uint64_t pol_last = ptx::l2_policy_evict_last();
-  uint32_t phase = 0;
-  int sb = 0, claimed = -1, claimed_sb = -1;
-  const Params* pend = nullptr;
-  int pend_slot = 0, pend_c = -1, pend_sb = -1;
-  unsigned pend_n = 0;
-  long long u = first_unit(static_cast<long long>(blockIdx.x) * kNumConvWarps + cw);
-  if (u < total) issue(u, 0);
-  for (; u < total; u = next_unit(u, nw)) {
-    sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
-    const Params& p = bt.sub[sb];
-    const Unit x = unit_of(p, u - bt.unit_base[sb]);
-    if (x.c != claimed || sb != claimed_sb) {
-      if (pend && slot_busy(p, x.c, lane)) {
-        publish_unit(*pend, pend_slot, lane, pend_n);
-        pend = nullptr;
-      }
-      if (!claim_slot_warp(p, x.c, lane, abort_flag)) {
-        drain_tma(bar, phase, tma_pending, wc.timeout_ns);
-        return;
-      }
-      claimed = x.c;
-      claimed_sb = sb;
-    }
-    const int ib = x.hb >> 1;
-    uint8_t* tre = ring_tile<FMT>(p, x.slot, 0, x.kb, ib);
-    uint8_t* tim = ring_tile<FMT>(p, x.slot, 1, x.kb, ib);
-    const int a0 = x.hb * 64 + lane, a1 = a0 + 32;
-    const int row0 = (x.hb & 1) * 64 + lane;
-    // y = g x 2^-e.
-    float2 g0 = make_float2(1.f, 0.f), g1 = make_float2(1.f, 0.f);
-    if (p.gains) {
-      g0 = a0 < p.n ? p.gains[a0 % p.gain_n] : make_float2(0.f, 0.f);
-      g1 = a1 < p.n ? p.gains[a1 % p.gain_n] : make_float2(0.f, 0.f);
-    }
-    if (p.in_amax) {
-      const unsigned* am = p.in_amax + static_cast<int64_t>(x.c) * p.n;
-      const float s0 = a0 < p.n ? exp2i(-scale_exp<FMT>(am[a0])) : 0.f;
-      const float s1 = a1 < p.n ? exp2i(-scale_exp<FMT>(am[a1])) : 0.f;
-      g0 = make_float2(g0.x * s0, g0.y * s0);  // exact: s is a power of two
-      g1 = make_float2(g1.x * s1, g1.y * s1);
-    }
-#pragma unroll 1
-    for (int j = 0; j < kBoxes; ++j) {
-      const bool got = ptx::wait_bounded(bar, phase, wc);
-      if (!__all_sync(0xffffffffu, got)) {
-        drain_tma(bar, phase, tma_pending, wc.timeout_ns);
-        return;
-      }
-      tma_pending = false;
-      phase ^= 1u;
-      // Lane l: inputs l and l + 32 of the box's 64, every sample.
-      using Raw = typename std::conditional<DT == 1, uint32_t, float2>::type;
-      const Raw* box = reinterpret_cast<const Raw*>(src);
-      Raw w0[kFBox], w1[kFBox];
-#pragma unroll
-      for (int t = 0; t < kFBox; ++t) {
-        w0[t] = box[t * 64 + lane];
-        w1[t] = box[t * 64 + 32 + lane];
-      }
-      __syncwarp();
-      ptx::fence_proxy_async_smem();
-      if (j + 1 < kBoxes) {
-        issue(u, j + 1);
-      } else {
-        const long long un = next_unit(u, nw);
-        if (un < total) issue(un, 0);
-      }
-      if (j == 0 && pend && (pend_n == kUnitRun || pend_c != x.c || pend_sb != sb)) {
-        publish_unit(*pend, pend_slot, lane, pend_n);
-        pend = nullptr;
-      }
-#pragma unroll
-      for (int g16 = 0; g16 < kFBox / 16; ++g16) {
-        float2 v0[16], v1[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          float2 c0, c1;
-          if constexpr (DT == 1) {
-            c0 = __half22float2(*reinterpret_cast<const __half2*>(&w0[16 * g16 + i]));
-            c1 = __half22float2(*reinterpret_cast<const __half2*>(&w1[16 * g16 + i]));
-          } else {
-            c0 = w0[16 * g16 + i];
-            c1 = w1[16 * g16 + i];
-          }
-          v0[i] = make_float2(g0.x * c0.x - g0.y * c0.y, g0.x * c0.y + g0.y * c0.x);
-          v1[i] = make_float2(g1.x * c1.x - g1.y * c1.y, g1.x * c1.y + g1.y * c1.x);
-        }
-        store_group16<FMT>(p, tre, tim, row0, x.cbase + (j * kFBox + 16 * g16) / 8, v0, v1, pol_last);
-      }
-    }
-    if (pend) {
-      ++pend_n;
-    } else {
-      pend = &p;
-      pend_slot = x.slot;
-      pend_c = x.c;
-      pend_sb = sb;
-      pend_n = 1;
-    }
-    if (*abort_flag) {
-      drain_tma(bar, phase, tma_pending, wc.timeout_ns);
-      return;
-    }
-  }
-  if (pend) publish_unit(*pend, pend_slot, lane, pend_n);
-}
-
-// --------------------------------------------------------------- epilogue
-
-// Store one 32-column piece: values v_re[j], v_im[j] of V(a, b0 + j).
-template <bool IS_INT>
-__device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint32_t (&im)[32],
-                                            const Params& p, int f, int a, int b0, bool add) {
-  using T = typename std::conditional<IS_INT, int, float>::type;
-  const Geometry& g = p.g;
-  T* out = static_cast<T*>(p.out);
-  auto val = [&](uint32_t u) -> T {
-    if constexpr (IS_INT) {
-      return __float2int_rn(__uint_as_float(u));
-    } else {
-      return __uint_as_float(u);
-    }
-  };
-  // Two polarisations, overwrite, 32-byte aligned output: the lanes of a
-  // station's two rows (a, a ^ 1; both valid or both not, n being even)
-  // exchange halves so that each writes whole 32-byte baseline records.
-  const bool pairs = g.P == 2 && !add && (reinterpret_cast<uintptr_t>(out) & 31) == 0;
-  const bool valid = a < p.n;
-  if (!valid && !pairs) return;
-  // Real channel, row station and first column station (packed channels:
-  // columns of another channel of the pack fall outside 0 <= s2 <= s1).
-  int fr = f, s1 = a / g.P, s2_0 = b0 / g.P;
-  if (p.pack > 1) {
-    const int j = s1 / p.Nr;
-    s1 -= j * p.Nr;
-    s2_0 -= j * p.Nr;
-    fr = f * p.pack + j;
-  }
-  const int64_t krow = static_cast<int64_t>(fr) * p.NBr + static_cast<int64_t>(s1) * (s1 + 1) / 2;
-  if (pairs) {
-    const int p1 = a & 1;
-    uint32_t* o8 = reinterpret_cast<uint32_t*>(out + krow * 8);  // record of s2 at o8 + 8 s2
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      // This lane's products for column stations 2m (A) and 2m + 1 (B) of the piece.
-      uint32_t A[4], B[4], rec[8];
-      auto bits = [&](uint32_t u) -> uint32_t {  // the stored word: int32 value or fp32 bits
-        if constexpr (IS_INT) {
-          return static_cast<uint32_t>(val(u));
-        } else {
-          return u;
-        }
-      };
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        A[2 * q] = bits(re[4 * m + q]);
-        A[2 * q + 1] = bits(im[4 * m + q]);
-        B[2 * q] = bits(re[4 * m + 2 + q]);
-        B[2 * q + 1] = bits(im[4 * m + 2 + q]);
-      }
-      // Row p1 = 0 writes baseline 2m, row p1 = 1 baseline 2m + 1; each sends
-      // the partner the half it needs.
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t got = __shfl_xor_sync(0xffffffffu, p1 ? A[k] : B[k], 1);
-        rec[k] = p1 ? got : A[k];
-        rec[4 + k] = p1 ? B[k] : got;
-      }
-      const int s2 = s2_0 + 2 * m + p1;
-      if (valid && s2 >= 0 && s2 <= s1) ptx::st_global_v8(o8 + 8 * static_cast<int64_t>(s2), rec);
-    }
-  } else if (g.P == 2) {
-    const int p1 = a & 1;
-    using V4 = typename std::conditional<IS_INT, int4, float4>::type;
-    V4* o4 = reinterpret_cast<V4*>(out + (krow * 4 + p1 * 2) * 2);  // (p1,0),(p1,1) of s2 at o4[2 s2]
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      V4 old[8];
-      if (add) {
-        // Loads of a half first: independent of the stores that follow.
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int s2 = s2_0 + 8 * h + j;
-          if (s2 >= 0 && s2 <= s1) old[j] = o4[2 * s2];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int jj = 8 * h + j;
-        const int s2 = s2_0 + jj;
-        if (s2 >= 0 && s2 <= s1) {
-          V4 v;
-          v.x = val(re[2 * jj]);
-          v.y = val(im[2 * jj]);
-          v.z = val(re[2 * jj + 1]);
-          v.w = val(im[2 * jj + 1]);
-          if (add) {
-            v.x += old[j].x;
-            v.y += old[j].y;
-            v.z += old[j].z;
-            v.w += old[j].w;
-          }
-          o4[2 * s2] = v;
-        }
-      }
-    }
-  } else {
-    using V2 = typename std::conditional<IS_INT, int2, float2>::type;
-    V2* o2 = reinterpret_cast<V2*>(out + krow * 2);  // baseline s2 at o2[s2]
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      V2 old[8];
-      if (add) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int s2 = s2_0 + 8 * h + j;
-          if (s2 >= 0 && s2 <= s1) old[j] = o2[s2];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int jj = 8 * h + j;
-        const int s2 = s2_0 + jj;
-        if (s2 >= 0 && s2 <= s1) {
-          V2 v;
-          v.x = val(re[jj]);
-          v.y = val(im[jj]);
-          if (add) {
-            v.x += old[j].x;
-            v.y += old[j].y;
-          }
-          o2[s2] = v;
-        }
-      }
-    }
-  }
-}
-
-// Undo the operand scales of float input: V(a, b0 + j) *= 2^(e_a + e_b).
-template <int FMT>
-__device__ __forceinline__ void scale_piece(uint32_t (&re)[32], uint32_t (&im)[32], const Params& p,
-                                            int f, int a, int b0) {
-  const unsigned* am = p.in_amax + static_cast<int64_t>(f) * p.n;
-  const int ea = a < p.n ? scale_exp<FMT>(am[a]) : 0;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const int b = b0 + j;
-    const float sc = exp2i(ea + (b < p.n ? scale_exp<FMT>(am[b]) : 0));
-    re[j] = __float_as_uint(__uint_as_float(re[j]) * sc);
-    im[j] = __float_as_uint(__uint_as_float(im[j]) * sc);
-  }
-}
-
-// FP64 block sums: acc64 = (first chunk and not accumulating ? 0 : acc64) +
-// piece; the last chunk of the integration also stores its fp32 rounding.
-__device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const uint32_t (&im)[32],
-                                                const Params& p, int f, int a, int b0, bool first,
-                                                bool last) {
-  if (a >= p.n) return;
-  const int P = p.g.P;
-  int s1 = a / P, joff = 0, fr = f;
-  const int p1 = a - s1 * P;
-  if (p.pack > 1) {  // packed channels: real channel and stations
-    const int j = s1 / p.Nr;
-    joff = j * p.Nr;
-    s1 -= joff;
-    fr = f * p.pack + j;
-  }
-  const int64_t krow = static_cast<int64_t>(fr) * p.NBr + static_cast<int64_t>(s1) * (s1 + 1) / 2;
-  const bool load_old = !first || p.accumulate;
-  double2* ws = reinterpret_cast<double2*>(p.acc64);
-  float2* out = static_cast<float2*>(p.out);
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const int b = b0 + j;
-    const int s2v = b / P, p2 = b - s2v * P, s2 = s2v - joff;
-    if (s2 < 0 || s2 > s1) continue;
-    const int64_t idx = (krow + s2) * P * P + p1 * P + p2;
-    double2 v = make_double2(static_cast<double>(__uint_as_float(re[j])),
-                             static_cast<double>(__uint_as_float(im[j])));
-    if (load_old) {
-      const double2 o = ws[idx];
-      v.x += o.x;
-      v.y += o.y;
-    }
-    ws[idx] = v;
-    if (last) out[idx] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
-  }
-}
-
-// ------------------------------------------------------------------ kernel
-
-template <bool IS_INT, int DT, int FMT, bool MULTI>
-__global__ void __launch_bounds__(kThreads, 1)
-    planar_kernel(const __grid_constant__ Batch bt) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                             ~static_cast<uintptr_t>(1023));
-  const uint32_t sbase = ptx::smem_u32(smem);
-  const uint32_t bar0 = sbase + kBarOff;
-  auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
-  auto accf_bar = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
-  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * kStages + 2 + b); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
-  auto conv_bar = [&](int w) { return bar0 + 8u * (2 * kStages + 5 + w); };
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + kBarOff + kNumBars * 8);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
-
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      ptx::mbar_init(full_bar(s), 1);
-      ptx::mbar_init(empty_bar(s), 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      ptx::mbar_init(accf_bar(b), 1);
-      ptx::mbar_init(acce_bar(b), kNumEpiWarps);
-    }
-    ptx::mbar_init(drain_bar, 1);
-    for (int w = 0; w < kNumConvWarps; ++w) ptx::mbar_init(conv_bar(w), 1);
-    *abort_flag = 0;
-    ptx::fence_mbar_init();
-    ptx::fence_proxy_async_smem();
-  }
-  if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(tmem_holder), kTmemCols);
-    ptx::tmem_relinquish();
-  }
-  ptx::tc_fence_before();
-  __syncthreads();
-  ptx::tc_fence_after();
-  const uint32_t tmem = *tmem_holder;
-
-  // Hi/lo operands: 22-bit products lose accuracy in a long fp32 TMEM
-  // accumulation, so the MMA restarts its accumulator (buffer 0) every
-  // 64-sample K-block and the epilogue adds each block into a round-to-nearest
-  // fp32 running sum held in TMEM columns 256..511.
-  constexpr bool kTmemSum = FMT == kFmtHiLo;
-  const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
-  const long long nitems = table_end<MULTI>(bt.item_base, bt.nsub);
-
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      int issued_phase[kStages];
-      for (int s = 0; s < kStages; ++s) issued_phase[s] = -1;
-      bool ok = true;
-      int sb = 0, ready_chan = -1, ready_sb = -1;
-      for (long long it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
-        sb = advance_sub<MULTI>(bt.item_base, bt.nsub, it, sb);
-        const Params& p = bt.sub[sb];
-        int f, bx, by;
-        item_coords(it - bt.item_base[sb], p.ntiles, &f, &bx, &by);
-        const int slot = f % p.ring_slots;
-        if (f != ready_chan || sb != ready_sb) {
-          const unsigned gen = static_cast<unsigned>(f / p.ring_slots);
-          if (!wait_counter(p.ready + slot, (gen + 1) * static_cast<unsigned>(p.units_per_chan), p,
-                            abort_flag)) {
-            ok = false;
-            break;
-          }
-          ready_chan = f;
-          ready_sb = sb;
-        }
-        const bool diag = bx == by;
-        constexpr int TB = FmtT<FMT>::kTile;
-        const uint64_t pol_last = ptx::l2_policy_evict_last();  // tiles are shared by the channel's blocks
-        for (int st = 0; ok && st < p.nkb * FmtT<FMT>::kSteps; ++st) {
-          // Step st: K-block kb; HI/LO steps j = 0, 1, 2 take (H, H), (L, H), (H, L).
-          const int kb = st / FmtT<FMT>::kSteps, j = st - kb * FmtT<FMT>::kSteps;
-          const int kta = kb + (j == 1 ? p.nkb : 0);
-          const int ktb = kb + (j == 2 ? p.nkb : 0);
-          const bool same = diag && kta == ktb;
-          if (!ptx::wait_bounded(empty_bar(stage), phase ^ 1u, wc)) {
-            ok = false;
-            break;
-          }
-          const uint32_t dst = sbase + stage * kStageBytes;
-          const uint32_t fb = full_bar(stage);
-          ptx::mbar_arrive_expect_tx(fb, same ? 2 * TB : 4 * TB);
-          ptx::bulk_load_hint(dst, ring_tile<FMT>(p, slot, 0, kta, by), TB, fb, pol_last);
-          ptx::bulk_load_hint(dst + TB, ring_tile<FMT>(p, slot, 1, kta, by), TB, fb, pol_last);
-          if (!same) {
-            ptx::bulk_load_hint(dst + 2 * TB, ring_tile<FMT>(p, slot, 0, ktb, bx), TB, fb, pol_last);
-            ptx::bulk_load_hint(dst + 3 * TB, ring_tile<FMT>(p, slot, 1, ktb, bx), TB, fb, pol_last);
-          }
-          issued_phase[stage] = static_cast<int>(phase);
-          if (++stage == kStages) {
-            stage = 0;
-            phase ^= 1u;
-          }
-        }
-      }
-      if (!ok) {
-        for (int s = 0; s < kStages; ++s) {
-          if (issued_phase[s] < 0) continue;
-          const uint64_t t0 = ptx::globaltimer();
-          while (!ptx::mbar_try_wait(full_bar(s), static_cast<uint32_t>(issued_phase[s])) &&
-                 ptx::globaltimer() - t0 < wc.timeout_ns) {
-          }
-        }
-      }
-    }
-  } else if (warp == 1) {
-    // ---------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      uint32_t u = 0;
-      bool ok = true;
-      bool issued_any = false;
-      int sb = 0;
-      for (long long it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
-        sb = advance_sub<MULTI>(bt.item_base, bt.nsub, it, sb);
-        const Params& p = bt.sub[sb];
-        int f, bx, by;
-        item_coords(it - bt.item_base[sb], p.ntiles, &f, &bx, &by);
-        const bool diag = bx == by;
-        // Block shape: M = 128 rows; N trimmed to the block's valid columns
-        // (rounded up to 16), so ragged edge blocks skip the zero columns.
-        const int ncols = min(kBlk, p.n - bx * kBlk);
-        const uint32_t idesc = ptx::idesc_f16_f32(kBlk, (ncols + 15) & ~15);
-        const uint32_t idesc_negb = idesc | (1u << 14);
-        if (!channel_ready(p, f, abort_flag)) {
-          ok = false;
-          break;
-        }
-        const int chunk_kb = chunk_kblocks(p, f);
-        const int nchunks = (p.nkb + chunk_kb - 1) / chunk_kb;
-        for (int ch = 0; ok && ch < nchunks; ++ch) {
-          const int kb0 = ch * chunk_kb;
-          const int kb1 = min(p.nkb, kb0 + chunk_kb);
-          // Accumulation groups: the whole chunk, or one K-block per group when
-          // the epilogue sums 64-sample fp32 blocks in TMEM (buffer 0 only).
-          const int gstep = kTmemSum ? 1 : (kb1 - kb0);
-          for (int g0 = kb0; ok && g0 < kb1; g0 += gstep) {
-          const int g1 = min(kb1, g0 + gstep);
-          const uint32_t ab = kTmemSum ? 0u : (u & 1u);
-          const uint32_t ap = kTmemSum ? (u & 1u) : ((u >> 1) & 1u);
-          if (!ptx::wait_bounded(acce_bar(ab), ap ^ 1u, wc)) {
-            ok = false;
-            break;
-          }
-          ptx::tc_fence_after();
-          const uint32_t d_re = tmem + ab * 256;
-          const uint32_t d_im = d_re + 128;
-          constexpr int TB = FmtT<FMT>::kTile;
-          for (int st = g0 * FmtT<FMT>::kSteps; st < g1 * FmtT<FMT>::kSteps; ++st) {
-            if (!ptx::wait_bounded(full_bar(stage), phase, wc)) {
-              ok = false;
-              break;
-            }
-            ptx::tc_fence_after();
-            const bool same = diag && (FMT != kFmtHiLo || st % 3 == 0);
-            const uint32_t ar = sbase + stage * kStageBytes;
-            const uint32_t ai = ar + TB;
-            const uint32_t br = same ? ar : ar + 2 * TB;
-            const uint32_t bi = same ? ai : ar + 3 * TB;
-            // Descriptors of the stage's four tiles; K-step k adds its byte offset
-            // (16-byte units) to the address field, which cannot carry: every
-            // shared-memory address is below 256 KiB.
-            const uint64_t dar0 = ptx::interleave_kmajor_desc(ar, kChunkStride, kGroupStride);
-            const uint64_t dai0 = ptx::interleave_kmajor_desc(ai, kChunkStride, kGroupStride);
-            const uint64_t dbr0 = ptx::interleave_kmajor_desc(br, kChunkStride, kGroupStride);
-            const uint64_t dbi0 = ptx::interleave_kmajor_desc(bi, kChunkStride, kGroupStride);
-#pragma unroll
-            for (int k = 0; k < FmtT<FMT>::kChunks / 2; ++k) {
-              const uint32_t acc = (st > g0 * FmtT<FMT>::kSteps || k > 0) ? 1u : 0u;
-              // K-step k covers 16-byte chunks 2k and 2k + 1 (16 fp16 or 32 e4m3 samples).
-              const uint64_t kd = static_cast<uint64_t>(k * 2 * kChunkStride) >> 4;
-              const uint64_t dar = dar0 + kd, dai = dai0 + kd, dbr = dbr0 + kd, dbi = dbi0 + kd;
-              if constexpr (FMT == kFmtF8) {
-                ptx::mma_f8_ss(d_re, dar, dbr, idesc, acc);       // Re += Ar Br^T
-                ptx::mma_f8_ss(d_re, dai, dbi, idesc, 1u);        // Re += Ai Bi^T
-                ptx::mma_f8_ss(d_im, dai, dbr, idesc, acc);       // Im += Ai Br^T
-                ptx::mma_f8_ss(d_im, dar, dbi, idesc_negb, 1u);   // Im -= Ar Bi^T
-              } else {
-                ptx::mma_f16_ss(d_re, dar, dbr, idesc, acc);      // Re += Ar Br^T
-                ptx::mma_f16_ss(d_re, dai, dbi, idesc, 1u);       // Re += Ai Bi^T
-                ptx::mma_f16_ss(d_im, dai, dbr, idesc, acc);      // Im += Ai Br^T
-                ptx::mma_f16_ss(d_im, dar, dbi, idesc_negb, 1u);  // Im -= Ar Bi^T
-              }
-            }
-            issued_any = true;
-            ptx::mma_commit(empty_bar(stage));
-            if (++stage == kStages) {
-              stage = 0;
-              phase ^= 1u;
-            }
-          }
-          if (!ok) break;
-          ptx::mma_commit(accf_bar(ab));
-          ++u;
-          }
-        }
-        if (ok) red_release_add(p.done + (f % p.ring_slots), 1u);
-      }
-      if (!ok && issued_any) {
-        ptx::mma_commit(drain_bar);
-        const uint64_t t0 = ptx::globaltimer();
-        while (!ptx::mbar_try_wait(drain_bar, 0) && ptx::globaltimer() - t0 < wc.timeout_ns) {
-        }
-      }
-    }
-  } else if (warp < 2 + kNumEpiWarps) {
-    // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;
-    const uint32_t t_lanes = tmem + (static_cast<uint32_t>(q * 32) << 16);
-    uint32_t u = 0;
-    bool ok = true;
-    int sb = 0;
-    for (long long it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
-      sb = advance_sub<MULTI>(bt.item_base, bt.nsub, it, sb);
-      const Params& p = bt.sub[sb];
-      const int P = p.g.P;
-      int f, bx, by;
-      item_coords(it - bt.item_base[sb], p.ntiles, &f, &bx, &by);
-      const int a = by * kBlk + q * 32 + lane;  // this thread's row input
-      // Pieces piece0..last can reach the lower station triangle for this
-      // warp (packed channels: only from the first column of the lowest
-      // row's real channel on).
-      const int s1_hi = min(p.g.N - 1, (by * kBlk + q * 32 + 31) / P);
-      int last = -1;
-      for (int piece = 0; piece < kBlk / 32; ++piece)
-        if ((bx * kBlk + piece * 32) / P <= s1_hi) last = piece;
-      int piece0 = 0;
-      if (p.pack > 1) {
-        const int col0 = (by * kBlk + q * 32) / P / p.Nr * p.Nr * P;  // first column of that channel
-        piece0 = max(0, (col0 - bx * kBlk) / 32);
-        if (piece0 > last) last = -1;  // no row of this warp is valid
-      }
-      const bool rdy = channel_ready(p, f, abort_flag);
-      if (!__all_sync(0xffffffffu, rdy)) {
-        ok = false;
-        break;
-      }
-      const int chunk_kb = chunk_kblocks(p, f);
-      const int nchunks = (p.nkb + chunk_kb - 1) / chunk_kb;
-      for (int ch = 0; ok && ch < nchunks; ++ch) {
-        const int kb0 = ch * chunk_kb;
-        const int kb1 = min(p.nkb, kb0 + chunk_kb);
-        const int gstep = kTmemSum ? 1 : (kb1 - kb0);
-        const bool add = p.accumulate || ch > 0;
-        const bool first = ch == 0, last_chunk = ch == nchunks - 1;
-        for (int g0 = kb0; g0 < kb1; g0 += gstep) {
-          // TMEM running sum: the first group of a chunk starts it, the last
-          // one is stored; groups in between only add into it.
-          const bool gfirst = g0 == kb0, glast = g0 + gstep >= kb1;
-          const uint32_t ab = kTmemSum ? 0u : (u & 1u);
-          const uint32_t ap = kTmemSum ? (u & 1u) : ((u >> 1) & 1u);
-          const bool got = ptx::wait_bounded(accf_bar(ab), ap, wc);
-          if (!__all_sync(0xffffffffu, got)) {
-            ok = false;
-            break;
-          }
-          ptx::tc_fence_after();
-          if (last < 0) {
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
-          }
-#pragma unroll 1
-          for (int piece = piece0; piece <= last; ++piece) {
-            uint32_t vr[32], vi[32];
-            ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + piece * 32, vr);
-            ptx::tmem_ld_32x32b_x32(t_lanes + ab * 256 + 128 + piece * 32, vi);
-            if constexpr (kTmemSum) {
-              if (!gfirst) {
-                uint32_t sr[32], si[32];
-                ptx::tmem_ld_32x32b_x32(t_lanes + 256 + piece * 32, sr);
-                ptx::tmem_ld_32x32b_x32(t_lanes + 384 + piece * 32, si);
-                ptx::tmem_wait_ld();
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  vr[j] = __float_as_uint(__uint_as_float(vr[j]) + __uint_as_float(sr[j]));
-                  vi[j] = __float_as_uint(__uint_as_float(vi[j]) + __uint_as_float(si[j]));
-                }
-              }
-            }
-            ptx::tmem_wait_ld();
-            if (piece == last) {
-              ptx::tc_fence_before();
-              __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(acce_bar(ab));
-            }
-            if (kTmemSum && !glast) {
-              ptx::tmem_st_32x32b_x32(t_lanes + 256 + piece * 32, vr);
-              ptx::tmem_st_32x32b_x32(t_lanes + 384 + piece * 32, vi);
-              continue;
-            }
-            const int b0 = bx * kBlk + piece * 32;
-            if constexpr (IS_INT) {
-              store_piece<true>(vr, vi, p, f, a, b0, add);
-            } else {
-              if (p.in_amax) scale_piece<FMT>(vr, vi, p, f, a, b0);
-              if (p.acc64) {
-                store_piece_f64(vr, vi, p, f, a, b0, first, last_chunk);
-              } else {
-                store_piece<false>(vr, vi, p, f, a, b0, add);
-              }
-            }
-          }
-          if (kTmemSum && !glast) ptx::tmem_wait_st();
-          ++u;
-        }
-      }
-    }
-  } else {
-    // ---------------------------------------------------------- converters
-    const int cw = warp - (2 + kNumEpiWarps);
-    if constexpr (DT == 0) {
-      if (bt.sub[0].tma_in) {  // set for every subarray or for none
-        converter_tma<FMT, MULTI>(bt, sbase + kConvOff + cw * kConvBufBytes, conv_bar(cw), cw, lane,
-                                  abort_flag);
-      } else {
-        converter_direct<DT, FMT, MULTI>(bt, cw, lane, abort_flag);
-      }
-    } else {
-      if (bt.sub[0].tma_in) {
-        converter_tma_float<DT, FMT, MULTI>(bt, sbase + kConvOff + cw * kConvBufBytes, conv_bar(cw),
-                                            cw, lane, abort_flag);
-      } else {
-        converter_direct<DT, FMT, MULTI>(bt, cw, lane, abort_flag);
-      }
-    }
-  }
-
-  // ------------------------------------------------------------- teardown
-  ptx::tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, kTmemCols);
-  }
-}
 
 template <bool IS_INT, int DT, int FMT, bool MULTI = false>
 const void* kernel_of() {
@@ -1484,7 +73,7 @@ int fmt_kt(int fmt) { return fmt == kFmtHiLo ? 2 : 1; }
 int fmt_tile_bytes(int fmt) { return fmt == kFmtF8 ? (1 << 13) : (1 << 14); }
 
 // Kernel parameters of one subarray.
-Params sub_params(const XeLaunch& L) {
+Params sub_params(const XeLaunch& L, int shape) {
   Params p;
   p.g = L.g;
   p.n = L.g.N * L.g.P;
@@ -1493,7 +82,8 @@ Params sub_params(const XeLaunch& L) {
   p.accumulate = L.accumulate;
   p.nib = (p.n + kBlk - 1) / kBlk;
   p.ntiles = p.nib * (p.nib + 1) / 2;
-  p.nitems = static_cast<long long>(p.ntiles) * L.g.F;
+  p.ipc = shape != kShape128 ? pair_items(p.nib) : p.ntiles;
+  p.nitems = static_cast<long long>(p.ipc) * L.g.F;
   p.nkb = L.g.Tp / kBK;
   p.is_int = L.in_dtype == 0 ? 1 : 0;
   const int fmt = p.is_int ? (L.fmt == kFmtF8 ? kFmtF8 : kFmtF16) : L.fmt;
@@ -1561,8 +151,17 @@ int planar_ring_slots(const Geometry& g, int grid, int fmt) {
   return static_cast<int>(std::min<int64_t>(n, g.F));
 }
 
+int planar_default_shape(const Geometry& g, int fmt) {
+  // 128 x 128 measured fastest for the Large-N geometry (the larger shapes
+  // move fewer operand bytes per MAC but put more channels in flight than
+  // the L2-resident ring can run ahead of); the batch tuner tries all three.
+  (void)g;
+  (void)fmt;
+  return kShape128;
+}
+
 cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps, int nsub,
-                           PlanarKernel* k) {
+                           PlanarKernel* k, int shape) {
   if (nsub < 1 || nsub > kMaxSub || !subs || !k) return cudaErrorInvalidValue;
   const int dt = subs[0].in_dtype;
   // 8-bit input: fp16 operands, or e4m3 when asked for (exact for |x| <= 16).
@@ -1577,7 +176,7 @@ cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps,
   for (int i = 0; i < nsub; ++i) {
     if (subs[i].in_dtype != dt || fmt_of(subs[i]) != fmt) return cudaErrorInvalidValue;
     if (subs[i].ring_slots < 1 || subs[i].ring_slots > kMaxRingSlots) return cudaErrorInvalidValue;
-    b->sub[i] = sub_params(subs[i]);
+    b->sub[i] = sub_params(subs[i], shape);
     if (maps && maps[i]) {
       b->maps[i] = *maps[i];
     } else {
@@ -1588,12 +187,42 @@ cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps,
                           (b->sub[i].nkb > 0 ? static_cast<long long>(subs[i].g.F) * b->sub[i].units_per_chan : 0);
   }
   for (int i = 0; i < nsub; ++i) b->sub[i].tma_in = all_tma ? 1 : 0;
-  k->func = select_kernel(dt, fmt, nsub > 1);
+  const bool pair = shape == kShapePair;
+  switch (shape) {
+    case kShape128: k->func = select_kernel(dt, fmt, nsub > 1); break;
+    case kShapePair: k->func = planar_pair_select(dt, fmt, nsub > 1); break;
+    case kShapeWide: k->func = planar_wide_select(dt, fmt, nsub > 1); break;
+    default: k->func = nullptr;
+  }
   if (!k->func) return cudaErrorInvalidValue;
-  k->grid = static_cast<int>(std::min<long long>(b->item_base[nsub], subs[0].grid));
   k->block = kThreads;
-  k->smem = kSmemBytes;
-  return cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  k->smem = shape == kShapePair ? Cfg<kShapePair>::kSmemBytes
+                                : (shape == kShapeWide ? Cfg<kShapeWide>::kSmemBytes : Cfg<kShape128>::kSmemBytes);
+  k->shape = shape;
+  cudaError_t e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, k->smem);
+  if (e != cudaSuccess) return e;
+  // Every CTA must be resident at once: the operand ring couples them.
+  const long long items = b->item_base[nsub];
+  if (pair) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(std::max(2, subs[0].grid & ~1)));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = static_cast<size_t>(k->smem);
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, k->func, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    const long long ncl = std::min<long long>({static_cast<long long>(clusters), subs[0].grid / 2, items});
+    k->grid = static_cast<int>(2 * ncl);
+  } else {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, kThreads, static_cast<size_t>(k->smem));
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long resident = static_cast<long long>(per_sm) * subs[0].grid;
+    k->grid = static_cast<int>(std::min<long long>({items, static_cast<long long>(subs[0].grid), resident}));
+  }
+  return cudaSuccess;
 }
 
 cudaError_t planar_setup(const XeLaunch* subs, int nsub, cudaStream_t s) {
@@ -1628,10 +257,10 @@ cudaError_t planar_launch(PlanarKernel& k, cudaStream_t s) {
   return cudaLaunchKernel(k.func, dim3(k.grid), dim3(k.block), args, static_cast<size_t>(k.smem), s);
 }
 
-cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, cudaStream_t s) {
+cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, int shape, cudaStream_t s) {
   static thread_local PlanarKernel k;
   const CUtensorMap* maps[1] = {in_map};
-  cudaError_t e = planar_prepare(&L, maps, 1, &k);
+  cudaError_t e = planar_prepare(&L, maps, 1, &k, shape);
   if (e == cudaSuccess && k.grid > 0) e = planar_setup(&L, 1, s);
   if (e == cudaSuccess) e = planar_launch(k, s);
   return e;

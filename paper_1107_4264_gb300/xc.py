@@ -26,7 +26,8 @@ XC_ERR_TIMEOUT = 6
 XC_ERR_OOM = 7
 XC_ERR_NO_DEVICE = 8
 XC_OPT_ENGINE, XC_OPT_ACCUMULATE, XC_OPT_TIMEOUT_MS, XC_OPT_PROFILE = 1, 2, 3, 4
-XC_OPT_PRECISION, XC_OPT_FP64_BLOCK = 5, 6
+XC_OPT_PRECISION, XC_OPT_FP64_BLOCK, XC_OPT_TILE = 5, 6, 7
+XC_TILE_AUTO, XC_TILE_128, XC_TILE_PAIR, XC_TILE_WIDE = 0, 1, 2, 3
 XC_OPT_TEST_NO_PUBLISH = 100
 XC_PREC_FP16, XC_PREC_HILO, XC_PREC_FP8 = 0, 1, 2
 (XC_ENGINE_TENSOR, XC_ENGINE_FP32, XC_ENGINE_TENSOR_2PASS, XC_ENGINE_TENSOR_1CTA,
@@ -240,7 +241,7 @@ class Correlator:
     def __init__(self, nstation: int, npol: int, nfreq: int, ntime: int, dtype: str = "int8",
                  engine: int = XC_ENGINE_TENSOR, accumulate: bool = False,
                  timeout_ms: Optional[int] = None, precision: int = XC_PREC_FP16,
-                 fp64_block: int = 0):
+                 fp64_block: int = 0, tile: int = XC_TILE_AUTO):
         import torch
         self._torch = torch
         self.nstation, self.npol, self.nfreq, self.ntime = nstation, npol, nfreq, ntime
@@ -254,6 +255,8 @@ class Correlator:
             self.set_option(XC_OPT_PRECISION, precision)
         if fp64_block:
             self.set_option(XC_OPT_FP64_BLOCK, fp64_block)
+        if tile != XC_TILE_AUTO:
+            self.set_option(XC_OPT_TILE, tile)
 
     @property
     def in_shape(self):

@@ -19,9 +19,15 @@ from paper_1107_4264_gb300 import synth, xc
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = [("tensor", xc.XC_ENGINE_TENSOR), ("fp32", xc.XC_ENGINE_FP32),
-           ("tensor_2pass", xc.XC_ENGINE_TENSOR_2PASS), ("tensor_1cta", xc.XC_ENGINE_TENSOR_1CTA),
-           ("tensor_pair", xc.XC_ENGINE_TENSOR_PAIR)]
+# (name, engine, tile shape of the planar tensor-core engine)
+ENGINES = [("tensor", xc.XC_ENGINE_TENSOR, xc.XC_TILE_AUTO),
+           ("tensor_128", xc.XC_ENGINE_TENSOR, xc.XC_TILE_128),
+           ("tensor_pair", xc.XC_ENGINE_TENSOR, xc.XC_TILE_PAIR),
+           ("tensor_wide", xc.XC_ENGINE_TENSOR, xc.XC_TILE_WIDE),
+           ("fp32", xc.XC_ENGINE_FP32, xc.XC_TILE_AUTO),
+           ("tensor_2pass", xc.XC_ENGINE_TENSOR_2PASS, xc.XC_TILE_AUTO),
+           ("interleaved_1cta", xc.XC_ENGINE_TENSOR_1CTA, xc.XC_TILE_AUTO),
+           ("interleaved_pair", xc.XC_ENGINE_TENSOR_PAIR, xc.XC_TILE_AUTO)]
 
 
 @pytest.fixture(scope="module")
@@ -32,9 +38,9 @@ def dev():
     return torch.device("cuda:0")
 
 
-def run_engine(x_cpu, engine, dev, dtype="int8", accumulate=False, out=None):
+def run_engine(x_cpu, engine, dev, dtype="int8", accumulate=False, out=None, tile=xc.XC_TILE_AUTO):
     T, F, N, P, _ = x_cpu.shape
-    eng = xc.Correlator(N, P, F, T, dtype, engine=engine, accumulate=accumulate)
+    eng = xc.Correlator(N, P, F, T, dtype, engine=engine, accumulate=accumulate, tile=tile)
     try:
         res = eng.correlate(x_cpu.to(dev).contiguous(), out=out, sync=True)
         return res.cpu()
@@ -68,11 +74,11 @@ INT_CASES = [
 ]
 
 
-@pytest.mark.parametrize("engine_name,engine", ENGINES, ids=[e[0] for e in ENGINES])
+@pytest.mark.parametrize("engine_name,engine,tile", ENGINES, ids=[e[0] for e in ENGINES])
 @pytest.mark.parametrize("x", INT_CASES)
-def test_int8_bit_exact(x, engine_name, engine, dev):
+def test_int8_bit_exact(x, engine_name, engine, tile, dev):
     want = oracle.correlate_i8(x.numpy())
-    got = run_engine(x, engine, dev).numpy().astype(np.int64)
+    got = run_engine(x, engine, dev, tile=tile).numpy().astype(np.int64)
     assert got.shape == want.shape
     mism = np.argwhere(got != want)
     assert mism.size == 0, "first mismatches %s: got %s want %s" % (
@@ -87,17 +93,17 @@ def test_adversarial_sign_pattern(dev):
     x = torch.where(((t // 3 + a) % 2) == 0, torch.tensor(127), torch.tensor(-128)).to(torch.int8)
     x = x.expand(T, F, N, P, 2).contiguous()
     want = oracle.correlate_i8(x.numpy())
-    for _, engine in ENGINES:
-        got = run_engine(x, engine, dev).numpy().astype(np.int64)
+    for _, engine, tile in ENGINES:
+        got = run_engine(x, engine, dev, tile=tile).numpy().astype(np.int64)
         np.testing.assert_array_equal(got, want)
 
 
-@pytest.mark.parametrize("engine_name,engine", ENGINES, ids=[e[0] for e in ENGINES])
-def test_accumulate_mode(engine_name, engine, dev):
+@pytest.mark.parametrize("engine_name,engine,tile", ENGINES, ids=[e[0] for e in ENGINES])
+def test_accumulate_mode(engine_name, engine, tile, dev):
     x1 = synth.uniform_int8((300, 3, 50, 2, 2), -128, 127, 21)
     x2 = synth.uniform_int8((300, 3, 50, 2, 2), -128, 127, 22)
     want = oracle.correlate_i8(x1.numpy()) + oracle.correlate_i8(x2.numpy())
-    eng = xc.Correlator(50, 2, 3, 300, "int8", engine=engine, accumulate=True)
+    eng = xc.Correlator(50, 2, 3, 300, "int8", engine=engine, accumulate=True, tile=tile)
     try:
         out = eng.new_output(device=dev)
         eng.correlate(x1.to(dev), out=out)
@@ -145,8 +151,8 @@ def test_large_n_sampled_channels(dev):
     chans = sorted(set([0, w.nfreq - 1] + rng.choice(w.nfreq, 4, replace=False).tolist()))
     xs = x[:, chans].cpu().numpy()
     want = oracle.correlate_i8(xs)
-    for _, engine in ENGINES:
-        eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "int8", engine=engine)
+    for _, engine, tile in ENGINES:
+        eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "int8", engine=engine, tile=tile)
         try:
             out = eng.correlate(x, sync=True)
             got = out[chans].cpu().numpy().astype(np.int64)
@@ -181,13 +187,13 @@ def frob_and_maxnorm(got, want, N, P):
 # (P = 1) takes the direct-load converter for both.
 @pytest.mark.parametrize("N,P", [(70, 2), (35, 2), (37, 1)], ids=["n140", "n70", "n37"])
 @pytest.mark.parametrize("dtype", ["float32", "float16"])
-@pytest.mark.parametrize("engine_name,engine", ENGINES, ids=[e[0] for e in ENGINES])
-def test_float_input_within_tolerance(dtype, engine_name, engine, N, P, dev):
+@pytest.mark.parametrize("engine_name,engine,tile", ENGINES, ids=[e[0] for e in ENGINES])
+def test_float_input_within_tolerance(dtype, engine_name, engine, tile, N, P, dev):
     T, F = 700, 3
     x = synth.sky_voltages(T, F, N, P, noise_sigma=0.7, nsrc=3, src_amp=1.0, seed=31)
     xt = x.to(torch.float16 if dtype == "float16" else torch.float32)
     want = oracle.correlate_f64(xt.to(torch.float64).numpy())
-    got = run_engine(xt, engine, dev, dtype=dtype).numpy().astype(np.float64)
+    got = run_engine(xt, engine, dev, dtype=dtype, tile=tile).numpy().astype(np.float64)
     frob, mx = frob_and_maxnorm(got, want, N, P)
     # fp16 operands (tensor path, unit round-off 2^-11) / fp32 accumulation
     assert frob <= 1e-3, frob
