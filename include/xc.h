@@ -120,8 +120,12 @@ xc_status xc_correlate(xc_handle* h, const void* in, void* out, void* stream);
  *   grad_out: device fp32, layout of `out`; in: the forward's input
  *   (re-read, nothing of the forward is stored); grad_in: device fp32,
  *   layout of `in`.  The gain gradient is kept for xc_get_grad_gains.
- *   FP32 arithmetic.  Allocates an F*n*n complex workspace on first use.
- *   Needs XC_CF32 input (XC_ERR_UNSUPPORTED otherwise).
+ *   Arithmetic: with the default XC_ENGINE_TENSOR, a tcgen05 complex GEMM on
+ *   split hi/lo fp16 operands (per-channel power-of-two scales, three MMAs
+ *   per step: about 22 significant bits) with fp32 accumulation; with
+ *   XC_ENGINE_FP32, FP32 on the CUDA cores.  Allocates an F*n*n complex
+ *   workspace (and, on the tensor cores, the hi/lo operand tiles) on first
+ *   use.  Needs XC_CF32 input (XC_ERR_UNSUPPORTED otherwise).
  */
 xc_status xc_correlate_backward(xc_handle* h, const void* grad_out, const void* in, void* grad_in,
                                 void* stream);
@@ -290,7 +294,8 @@ void xc_tri_coords(int64_t g, int64_t* bx, int64_t* by);
  * Channels the tensor-core engine correlates together in one 128-input block
  * for these sizes (see xc_create): k, the largest divisor of nfreq with
  * k * nstation * npol <= 128, when nstation * npol <= 64; else 1.  Host-side,
- * no device work; returns 0 for sizes <= 0.
+ * no device work; returns 0 for sizes xc_create rejects (a size <= 0, npol
+ * not 1 or 2, more than 2^30 rows).
  */
 int xc_channels_packed(int nstation, int npol, int nfreq);
 
@@ -304,28 +309,35 @@ int xc_channels_packed(int nstation, int npol, int nfreq);
  * an application whose device memory is entirely held by another allocator,
  * or a plug-in whose host forbids allocation inside its processing callback.
  * xc_create allocates the operand workspace, so those callers use this call
- * instead: it computes exactly what xc_correlate computes (tensor-core
- * engine, out overwritten) and allocates nothing, neither device nor pinned
- * memory.
+ * instead: it runs the same tensor-core kernel as xc_correlate (default tile
+ * shape, FP16 operands with the same per-input power-of-two scaling for float
+ * input, the same exact chunks for 8-bit input), so its visibilities are
+ * identical to xc_correlate's, and it allocates nothing, neither device nor
+ * host memory.
  *
  * Its scratch is a static device array of XC_NOALLOC_SCRATCH_BYTES that
- * every GPU loading the library holds until the process exits.  The band is
- * processed in groups of channels whose fp16 operands (2*P*N rows x T
- * rounded up to 64 samples x 2 bytes per channel) fit that array; a size
- * where one channel alone does not fit is rejected with
- * XC_ERR_UNSUPPORTED (message in xc_last_error_message()).
+ * every GPU loading the library holds until the process exits.  It holds the
+ * kernel's counters, the scale pre-pass maxima (nfreq*npol*nstation words for
+ * float input) and as many operand-ring channel slots as fit; one slot is
+ * 2*P*N rows (rounded up to 128) x ntime (rounded up to 64) x 2 bytes.  A
+ * size where not even one slot fits is rejected with XC_ERR_UNSUPPORTED
+ * (message in xc_last_error_message()).
  *
  *   sizes, in_dtype, in, out: as for xc_create / xc_correlate.
  *   status: optional caller-owned device int; a kernel whose bounded wait
  *           gives up ORs 1 into it (the caller zeroes it).  NULL: not reported.
  *   stream: cudaStream_t as void*; the call is stream-ordered and returns
  *           once the work is queued.
- * The first call on each device does a one-time set-up (device query and the
- * device address of the static scratch, with that device current); make that
- * first call before any stream capture begins.  Every call on a device shares
- * the one scratch array, so calls whose work overlaps on the GPU (different
- * streams, or different host threads, without ordering between them) race
- * and corrupt each other's results: order them.
+ * The first call on each device does a one-time set-up with that device
+ * current: it looks up the device address of the static scratch, and with
+ * CUDA's lazy module loading (the default) that also loads the library's
+ * device code and creates its 64 MiB array.  Make that first call at
+ * start-up, before any stream capture and outside any section that must not
+ * allocate (or set CUDA_MODULE_LOADING=EAGER so the load happens when the
+ * context is created).  A failed set-up is retried by the next call.  Every
+ * call on a device shares the one scratch array, so calls whose work overlaps
+ * on the GPU (different streams, or different host threads, without ordering
+ * between them) race and corrupt each other's results: order them.
  */
 #define XC_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 xc_status xc_correlate_noalloc(int nstation, int npol, int nfreq, int ntime, xc_dtype in_dtype,
@@ -405,23 +417,58 @@ xc_status xc_channelize_pfb(const void* in, xc_dtype in_dtype, int nstation, int
  *   in host memory, read during the call.  Stream-ordered; one graph launch
  *   per call.  Calls on one handle must be ordered with each other (they
  *   share the rings and counters).
- * xc_batch_tune: times each candidate schedule (work-list order: as given,
- *   largest subarray first, smallest first; x operand-ring depth: 1x, 2x) on
- *   the given buffers with `reps` timed launches each (after one warm-up),
- *   keeps the fastest for later calls and writes the mean milliseconds of
- *   every candidate to ms[XC_BATCH_CANDIDATES] and the winner to *best
- *   (either may be NULL).  Synchronises `stream`.
+ * xc_batch_tune: times each candidate schedule on the given buffers with
+ *   `reps` timed launches each (after one warm-up), keeps the fastest for
+ *   later calls, and writes the mean milliseconds of every candidate to
+ *   ms[XC_BATCH_CANDIDATES] (-1 for candidates not timed) and the winner to
+ *   *best (either may be NULL).  Candidate c (the tile shapes of XC_OPT_TILE
+ *   and the launch's schedule; every candidate computes the same result):
+ *     c % 3        work-list order: as given, largest subarray first,
+ *                  smallest first;
+ *     (c / 3) % 2  operand-ring depth: 1x, 2x;
+ *     (c / 6) % 2  channel packing of subarrays with nstation*npol <= 64
+ *                  (see xc_create): on, off (only tried when some subarray
+ *                  packs);
+ *     c / 12       tile shape: 128 x 128, CTA pair, 128 x 256.
+ *   With a tuning file set (xc_batch_set_cache) that holds this batch's
+ *   choice, the choice is applied without timing (ms[c] gets its recorded
+ *   time); otherwise the winner is appended to the file.  Synchronises
+ *   `stream`.
+ * xc_batch_set_cache: names a tuning file (NULL or "" for none) for this
+ *   handle's xc_batch_tune; lines are "<key>\t<candidate>\t<ms>", the last
+ *   line of a key counts, and the file is meant for one GPU model.
+ * xc_batch_cache_key: the key of a batch (the library version, npol, input
+ *   type and every subarray's nstation:nfreq:ntime in order) into buf;
+ *   returns its length, or -1 if it does not fit or an argument is bad.
+ * xc_batch_cache_lookup: the candidate a tuning file records for a key, or
+ *   -1 (no file, no such line).  Host-side helpers, no device work.
  */
 #define XC_BATCH_MAX_SUB 8
-#define XC_BATCH_CANDIDATES 6
+#define XC_BATCH_CANDIDATES 36
 xc_handle* xc_batch_create(int nsub, const int* nstation, const int* nfreq, const int* ntime,
                            int npol, xc_dtype in_dtype);
 xc_status xc_batch_correlate(xc_handle* h, const void* const* in, void* const* out, void* stream);
 xc_status xc_batch_tune(xc_handle* h, const void* const* in, void* const* out, void* stream,
                         int reps, double* ms, int* best);
+xc_status xc_batch_set_cache(xc_handle* h, const char* path);
+int xc_batch_cache_key(int nsub, const int* nstation, const int* nfreq, const int* ntime, int npol,
+                       xc_dtype in_dtype, char* buf, size_t len);
+int xc_batch_cache_lookup(const char* path, const char* key);
 
 /* Library version string. */
 const char* xc_version(void);
+
+/*
+ * Diagnostics (not in the paper): the FP32 CUDA-core peak that the plain
+ * FP32 X-engine's fraction of peak is quoted against, measured rather than
+ * computed from a nominal clock.  Launches, on `stream`, 4 CTAs of 512
+ * threads per SM of the current device, each thread running 8 independent
+ * fused multiply-add chains for 16 * iterations rounds; *flops receives the
+ * floating-point operations launched (2 per FFMA).  The caller times the
+ * launch (CUDA events on `stream`).  sink: device float[4 * SM count],
+ * written only in a case that cannot occur (it keeps the chains live).
+ */
+xc_status xc_fp32_peak_probe(long long iterations, void* sink, void* stream, long long* flops);
 
 #ifdef __cplusplus
 }

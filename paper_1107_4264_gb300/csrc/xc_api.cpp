@@ -79,6 +79,7 @@ struct BatchSub {
   xc::Geometry g{};
   xc::Geometry pg{};   // planar engine's geometry: `pack` channels per virtual channel
   int pack = 1;
+  int slots_unpacked = 0;  // ring depth 1x without channel packing (pack > 1 only)
   size_t in_bytes = 0, out_bytes = 0;
   void* ring = nullptr;
   int slots_base = 0;  // ring depth 1x (xc::planar_ring_slots)
@@ -93,6 +94,8 @@ struct BatchState {
   unsigned* ctr_all = nullptr;
   int order[XC_BATCH_MAX_SUB];
   int depth = 1;
+  bool packing = true;  // small subarrays' channels packed into one block (see planar_geometry)
+  char cache_path[1024] = "";  // xc_batch_set_cache
   int shape = xc::kPlanar128;  // tile shape (xc::kPlanar*), tuned by xc_batch_tune
   int shape_default = xc::kPlanar128;
   cudaStream_t cap_stream = nullptr;
@@ -164,9 +167,6 @@ struct xc_handle {
 namespace {
 
 xc_status encode_operand_map(CUtensorMap* map, void* base, int64_t R, int64_t Tp, int64_t n);
-xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g,
-                           xc_dtype dtype = XC_CI8);
-bool input_map_possible(xc_dtype dtype, const xc::Geometry& g);
 void batch_drop_graph(BatchState* b);
 
 // Planar tile shape for an XC_TILE_* option value (-1: not available).
@@ -283,8 +283,8 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     // Input in TMA boxes when its rows are 16-byte strided.
     CUtensorMap in_map;
     const CUtensorMap* im = nullptr;
-    if (input_map_possible(h->dtype, h->pg)) {
-      if (encode_input_map(&in_map, in, h->pg, h->dtype) != XC_OK) return t_status;
+    if (xc::input_map_possible(h->dtype, h->pg)) {
+      if (xc::encode_input_map(&in_map, in, h->pg, h->dtype) != XC_OK) return t_status;
       im = &in_map;
     }
     if (tm) tm->nkern = 1;
@@ -352,13 +352,33 @@ xc_status encode_operand_map(CUtensorMap* map, void* base, int64_t R, int64_t Tp
   return XC_OK;
 }
 
+// Full fp16 operand copy for the two-pass engine, allocated on first use.
+xc_status ensure_two_pass_workspace(xc_handle* h) {
+  if (h->ws) return XC_OK;
+  const size_t bytes = static_cast<size_t>(h->g.F) * h->g.R * h->g.Tp * 2;
+  cudaError_t e = cudaMalloc(&h->ws, bytes);
+  if (e != cudaSuccess) {
+    h->ws = nullptr;
+    return cuda_fail(e, "two-pass workspace allocation");
+  }
+  xc_status st = encode_operand_map(&h->tmap, h->ws, h->g.R, h->g.Tp, h->g.F);
+  if (st != XC_OK) {
+    cudaFree(h->ws);
+    h->ws = nullptr;
+  }
+  return st;
+}
+
+}  // namespace
+
+namespace xc {
 // Input [T][F][n] (complex) as a 3-D tensor {row elements, F, T} for the
 // planar converters' TMA boxes of 8 KiB (zero fill past the row and T):
 //   8-bit: {R = 2n bytes}, boxes of 128 x 1 x kPlanarUnitT;
 //   fp16:  {n} 32-bit complex elements, boxes of 64 x 1 x 32;
 //   fp32:  {2n} fp32 components, boxes of 128 x 1 x 16.
 // A row must be a multiple of 16 bytes (TMA global strides).
-bool input_map_possible(xc_dtype dtype, const xc::Geometry& g) {
+bool input_map_possible(xc_dtype dtype, const Geometry& g) {
   const int64_t n = static_cast<int64_t>(g.N) * g.P;
   switch (dtype) {
     case XC_CI8: return g.R % 16 == 0;
@@ -368,9 +388,9 @@ bool input_map_possible(xc_dtype dtype, const xc::Geometry& g) {
   return false;
 }
 
-xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry& g, xc_dtype dtype) {
+xc_status encode_input_map(CUtensorMap* map, const void* in, const Geometry& g, xc_dtype dtype) {
   EncodeTiledFn enc = tensor_map_encoder();
-  if (!enc) return fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  if (!enc) return record_error(XC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
   const cuuint64_t n = static_cast<cuuint64_t>(g.N) * g.P;
   cuuint64_t row = 0, esize = 1;
   cuuint32_t box_x = 0, box_t = 0;
@@ -400,30 +420,10 @@ xc_status encode_input_map(CUtensorMap* map, const void* in, const xc::Geometry&
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS)
-    return fail(XC_ERR_CUDA, "cuTensorMapEncodeTiled (input) failed (%d)", static_cast<int>(cr));
+    return record_error(XC_ERR_CUDA, "cuTensorMapEncodeTiled (input) failed (%d)", static_cast<int>(cr));
   return XC_OK;
 }
 
-// Full fp16 operand copy for the two-pass engine, allocated on first use.
-xc_status ensure_two_pass_workspace(xc_handle* h) {
-  if (h->ws) return XC_OK;
-  const size_t bytes = static_cast<size_t>(h->g.F) * h->g.R * h->g.Tp * 2;
-  cudaError_t e = cudaMalloc(&h->ws, bytes);
-  if (e != cudaSuccess) {
-    h->ws = nullptr;
-    return cuda_fail(e, "two-pass workspace allocation");
-  }
-  xc_status st = encode_operand_map(&h->tmap, h->ws, h->g.R, h->g.Tp, h->g.F);
-  if (st != XC_OK) {
-    cudaFree(h->ws);
-    h->ws = nullptr;
-  }
-  return st;
-}
-
-}  // namespace
-
-namespace xc {
 xc_status record_error(xc_status s, const char* fmt, ...) {
   t_status = s;
   if (s == XC_OK) {
@@ -459,18 +459,36 @@ const char* xc_status_string(xc_status s) {
   return "XC_ERR_UNKNOWN";
 }
 
-const char* xc_version(void) { return "xc 0.1 (sm_103a)"; }
+const char* xc_version(void) { return "xc 0.2 (sm_103a)"; }
+
+xc_status xc_fp32_peak_probe(long long iterations, void* sink, void* stream, long long* flops) {
+  if (iterations <= 0 || !sink || !flops) return fail(XC_ERR_INVALID_ARG, "bad probe arguments");
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(XC_ERR_NO_DEVICE, "no usable CUDA device");
+  }
+  const long long f = xc::launch_ffma_probe(iterations, static_cast<float*>(sink), sms,
+                                            static_cast<cudaStream_t>(stream));
+  if (f < 0) return cuda_fail(cudaErrorLaunchFailure, "FFMA probe launch");
+  *flops = f;
+  return succeed();
+}
 
 int64_t xc_tri_index(int64_t bx, int64_t by) { return xc::tri_index(bx, by); }
 
 int xc_channels_packed(int nstation, int npol, int nfreq) {
-  if (nstation <= 0 || npol <= 0 || nfreq <= 0) return 0;
+  // The sizes xc_create accepts (npol 1 or 2; rows 2 P N within its limit).
+  if (nstation <= 0 || nfreq <= 0 || (npol != 1 && npol != 2)) return 0;
+  const int64_t R = 2LL * npol * nstation;
+  if (R > (1LL << 30)) return 0;
   xc::Geometry g{};
   g.N = nstation;
   g.P = npol;
   g.F = nfreq;
   g.T = 1;
-  g.R = 2 * npol * nstation;
+  g.R = static_cast<int>(R);
   g.Tp = 64;
   g.NB = static_cast<int64_t>(nstation) * (nstation + 1) / 2;
   int pack = 1;
@@ -937,23 +955,77 @@ xc_status xc_channelize_pfb(const void* in, xc_dtype in_dtype, int nstation, int
 
 namespace {
 
+// Tuning file lines: "<key>\t<candidate>\t<ms>"; the last line with the key
+// wins.  Returns the candidate, or -1 (no file, no line, unreadable).
+int cache_lookup_ms(const char* path, const char* key, double* ms) {
+  if (!path || !path[0] || !key) return -1;
+  FILE* fh = fopen(path, "r");
+  if (!fh) return -1;
+  const size_t klen = strlen(key);
+  char line[2048];
+  int found = -1;
+  while (fgets(line, sizeof(line), fh)) {
+    if (strncmp(line, key, klen) != 0 || line[klen] != '\t') continue;
+    int c = -1;
+    double m = 0.0;
+    if (sscanf(line + klen + 1, "%d\t%lf", &c, &m) >= 1 && c >= 0 && c < XC_BATCH_CANDIDATES) {
+      found = c;
+      *ms = m;
+    }
+  }
+  fclose(fh);
+  return found;
+}
+
+// The tuning key of a batch handle (its subarrays in creation order).
+void batch_key(const BatchState* b, xc_dtype dtype, char* buf, size_t len) {
+  int N[XC_BATCH_MAX_SUB], F[XC_BATCH_MAX_SUB], T[XC_BATCH_MAX_SUB];
+  for (int i = 0; i < b->nsub; ++i) {
+    N[i] = b->sub[i].g.N;
+    F[i] = b->sub[i].g.F;
+    T[i] = b->sub[i].g.T;
+  }
+  if (xc_batch_cache_key(b->nsub, N, F, T, b->sub[0].g.P, dtype, buf, len) < 0) buf[0] = '\0';
+}
+
 // Work of subarray i in MMA block-steps: blocks per channel x channels x K-blocks.
 double batch_work(const BatchSub& b) {
   const double nib = std::ceil((static_cast<double>(b.pg.N) * b.pg.P) / 128);
   return nib * (nib + 1) / 2 * b.pg.F * (b.pg.Tp / 64);
 }
 
-// Candidate c: work-list order (c % 3: as given, largest first, smallest
-// first) and ring depth (1 + c / 3).
-void batch_schedule(BatchState* b, int c, int* order, int* depth) {
-  for (int i = 0; i < b->nsub; ++i) order[i] = i;
+// Candidate c of xc_batch_tune (XC_BATCH_CANDIDATES = 36):
+//   c % 3          work-list order: as given, largest first, smallest first;
+//   (c / 3) % 2    operand-ring depth: 1x, 2x;
+//   (c / 6) % 2    channel packing of small subarrays: on, off;
+//   c / 12         tile shape: 128 x 128, CTA pair, 128 x 256.
+struct Schedule {
+  int order[XC_BATCH_MAX_SUB];
+  int depth;
+  bool packing;
+  int shape;
+};
+
+Schedule batch_schedule(const BatchState* b, int c) {
+  Schedule sc;
+  for (int i = 0; i < b->nsub; ++i) sc.order[i] = i;
   const int kind = c % 3;
   if (kind != 0)
-    std::stable_sort(order, order + b->nsub, [&](int x, int y) {
+    std::stable_sort(sc.order, sc.order + b->nsub, [&](int x, int y) {
       const double wx = batch_work(b->sub[x]), wy = batch_work(b->sub[y]);
       return kind == 1 ? wx > wy : wx < wy;
     });
-  *depth = 1 + c / 3;
+  sc.depth = 1 + (c / 3) % 2;
+  sc.packing = (c / 6) % 2 == 0;
+  sc.shape = c / 12 == 0 ? xc::kPlanar128 : (c / 12 == 1 ? xc::kPlanarPair : xc::kPlanarWide);
+  return sc;
+}
+
+// The candidate index of a schedule (the inverse of batch_schedule for the
+// order kinds it produces).
+int batch_candidate(int order_kind, int depth, bool packing, int shape) {
+  const int sh = shape == xc::kPlanar128 ? 0 : (shape == xc::kPlanarPair ? 1 : 2);
+  return sh * 12 + (packing ? 0 : 6) + (depth - 1) * 3 + order_kind;
 }
 
 void batch_drop_graph(BatchState* b) {
@@ -967,7 +1039,7 @@ void batch_drop_graph(BatchState* b) {
 // Launch descriptions of the subarrays in work-list order, their input
 // maps, and the kernel parameter block in b->k.
 xc_status batch_prepare(xc_handle* h, const void* const* in, void* const* out,
-                        const int* order, int depth, int shape, xc::XeLaunch* L) {
+                        const int* order, int depth, bool packing, int shape, xc::XeLaunch* L) {
   BatchState* b = h->batch;
   if (!in || !out) return fail(XC_ERR_INVALID_ARG, "NULL pointer array");
   CUtensorMap maps[XC_BATCH_MAX_SUB];
@@ -980,14 +1052,16 @@ xc_status batch_prepare(xc_handle* h, const void* const* in, void* const* out,
       return fail(XC_ERR_ALIGNMENT, "subarray %d: buffers must be 16-byte aligned", i);
     xc::XeLaunch& X = L[j];
     X = xc::XeLaunch{};
-    X.g = s.pg;
-    X.pack = s.pack;
+    const bool packed = packing || s.pack == 1;
+    const xc::Geometry& pg = packed ? s.pg : s.g;
+    X.g = pg;
+    X.pack = packed ? s.pack : 1;
     X.in = in[i];
     X.in_dtype = static_cast<int>(h->dtype);
     X.out = out[i];
     X.accumulate = h->accumulate;
     X.ring = s.ring;
-    X.ring_slots = std::min(s.max_slots, s.slots_base * depth);
+    X.ring_slots = std::min(s.max_slots, (packed ? s.slots_base : s.slots_unpacked) * depth);
     X.counters = s.counters;
     X.amax = s.amax;
     X.gains = nullptr;
@@ -995,14 +1069,24 @@ xc_status batch_prepare(xc_handle* h, const void* const* in, void* const* out,
     X.timeout_ns = h->timeout_ns;
     X.status = h->d_status;
     mp[j] = nullptr;
-    if (h->dtype == XC_CI8 && s.pg.R % 16 == 0) {
-      if (encode_input_map(&maps[j], in[i], s.pg) != XC_OK) return t_status;
+    if (h->dtype == XC_CI8 && pg.R % 16 == 0) {
+      if (xc::encode_input_map(&maps[j], in[i], pg, XC_CI8) != XC_OK) return t_status;
       mp[j] = &maps[j];
     }
   }
   cudaError_t e = xc::planar_prepare(L, mp, b->nsub, &b->k, shape);
   if (e != cudaSuccess) return cuda_fail(e, "batch launch preparation");
   return XC_OK;
+}
+
+// Make a schedule the handle's own (later xc_batch_correlate calls capture
+// a new graph: ring depths, memset sizes and the kernel may change).
+void apply_schedule(BatchState* b, const Schedule& sc) {
+  for (int i = 0; i < b->nsub; ++i) b->order[i] = sc.order[i];
+  b->depth = sc.depth;
+  b->packing = sc.packing;
+  b->shape = sc.shape;
+  batch_drop_graph(b);
 }
 
 }  // namespace
@@ -1063,6 +1147,11 @@ xc_handle* xc_batch_create(int nsub, const int* nstation, const int* nfreq, cons
     s.max_slots = static_cast<int>(std::min<int64_t>(
         {static_cast<int64_t>(xc::kMaxRingSlots), static_cast<int64_t>(s.pg.F), 2ll * s.slots_base, cap2}));
     s.max_slots = std::max(s.max_slots, s.slots_base);
+    if (s.pack > 1) {
+      // Unpacked, the same channel slot size (one 128-input block) serves
+      // pack times as many channels.
+      s.slots_unpacked = std::min(s.max_slots, xc::planar_ring_slots(s.g, h->num_sms, XC_PREC_FP16));
+    }
     ring_off[i] = ring_total;
     ring_total += static_cast<size_t>(s.max_slots) * slot_bytes;
     in_total += s.in_bytes;
@@ -1104,7 +1193,7 @@ xc_status xc_batch_correlate(xc_handle* h, const void* const* in, void* const* o
   BatchState* b = h->batch;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   xc::XeLaunch L[XC_BATCH_MAX_SUB];
-  xc_status st = batch_prepare(h, in, out, b->order, b->depth, b->shape, L);
+  xc_status st = batch_prepare(h, in, out, b->order, b->depth, b->packing, b->shape, L);
   if (st != XC_OK) return st;
   if (b->k.grid <= 0) return succeed();
   cudaError_t e = cudaSuccess;
@@ -1166,6 +1255,23 @@ xc_status xc_batch_tune(xc_handle* h, const void* const* in, void* const* out, v
   if (!h || !h->batch) return fail(XC_ERR_INVALID_ARG, "not a batch handle");
   if (reps < 1 || reps > 1000) return fail(XC_ERR_INVALID_ARG, "reps must be in [1, 1000]");
   BatchState* b = h->batch;
+  if (ms)
+    for (int c = 0; c < XC_BATCH_CANDIDATES; ++c) ms[c] = -1.0;
+  // A tuning file that already holds this batch's choice: no timing.
+  char key[512] = "";
+  if (b->cache_path[0]) {
+    batch_key(b, h->dtype, key, sizeof(key));
+    double cms = 0.0;
+    const int c = cache_lookup_ms(b->cache_path, key, &cms);
+    if (c >= 0 && c < XC_BATCH_CANDIDATES) {
+      apply_schedule(b, batch_schedule(b, c));
+      if (best) *best = c;
+      if (ms) ms[c] = cms;
+      return succeed();
+    }
+  }
+  bool any_pack = false;
+  for (int i = 0; i < b->nsub; ++i) any_pack = any_pack || b->sub[i].pack > 1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
@@ -1175,11 +1281,14 @@ xc_status xc_batch_tune(xc_handle* h, const void* const* in, void* const* out, v
   int best_c = -1;
   xc_status st = XC_OK;
   for (int c = 0; c < XC_BATCH_CANDIDATES && st == XC_OK; ++c) {
-    int order[XC_BATCH_MAX_SUB], depth = 1;
-    batch_schedule(b, c, order, &depth);
+    const Schedule sc = batch_schedule(b, c);
+    if (!sc.packing && !any_pack) continue;  // the same launch as its packed twin
     xc::XeLaunch L[XC_BATCH_MAX_SUB];
-    st = batch_prepare(h, in, out, order, depth, b->shape, L);
-    if (st != XC_OK) break;
+    if (batch_prepare(h, in, out, sc.order, sc.depth, sc.packing, sc.shape, L) != XC_OK) {
+      if (t_status == XC_ERR_CUDA) continue;  // a shape this device cannot launch: not a candidate
+      st = t_status;
+      break;
+    }
     float t = 0.f;
     for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
       if (r == 1) e = cudaEventRecord(e0, s);
@@ -1203,13 +1312,42 @@ xc_status xc_batch_tune(xc_handle* h, const void* const* in, void* const* out, v
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != XC_OK) return st;
+  if (best_c < 0) return fail(XC_ERR_CUDA, "no tuning candidate could be launched");
   // The device status word tells whether any candidate gave up on a wait.
   st = xc_synchronize(h, stream);
   if (st != XC_OK) return st;
-  batch_schedule(b, best_c, b->order, &b->depth);
-  batch_drop_graph(b);  // ring depths (memset sizes) may change: capture again
+  apply_schedule(b, batch_schedule(b, best_c));
   if (best) *best = best_c;
+  if (b->cache_path[0]) {
+    if (FILE* fh = fopen(b->cache_path, "a")) {
+      fprintf(fh, "%s\t%d\t%.6f\n", key, best_c, best_ms);
+      fclose(fh);
+    }
+  }
   return succeed();
+}
+
+xc_status xc_batch_set_cache(xc_handle* h, const char* path) {
+  if (!h || !h->batch) return fail(XC_ERR_INVALID_ARG, "not a batch handle");
+  if (path && strlen(path) >= sizeof(h->batch->cache_path))
+    return fail(XC_ERR_INVALID_ARG, "cache path longer than %zu bytes", sizeof(h->batch->cache_path) - 1);
+  snprintf(h->batch->cache_path, sizeof(h->batch->cache_path), "%s", path ? path : "");
+  return succeed();
+}
+
+int xc_batch_cache_key(int nsub, const int* nstation, const int* nfreq, const int* ntime, int npol,
+                       xc_dtype in_dtype, char* buf, size_t len) {
+  if (nsub < 1 || nsub > XC_BATCH_MAX_SUB || !nstation || !nfreq || !ntime || !buf || len == 0)
+    return -1;
+  int k = snprintf(buf, len, "%s|npol=%d|dtype=%d|", xc_version(), npol, static_cast<int>(in_dtype));
+  for (int i = 0; i < nsub && k >= 0 && static_cast<size_t>(k) < len; ++i)
+    k += snprintf(buf + k, len - k, "%s%d:%d:%d", i ? "," : "", nstation[i], nfreq[i], ntime[i]);
+  return (k < 0 || static_cast<size_t>(k) >= len) ? -1 : k;
+}
+
+int xc_batch_cache_lookup(const char* path, const char* key) {
+  double ms = 0.0;
+  return cache_lookup_ms(path, key, &ms);
 }
 
 }  // extern "C"

@@ -272,4 +272,33 @@ cudaError_t launch_fp32_xengine(const void* in, int in_dtype, void* out, const G
   return cudaGetLastError();
 }
 
+// FP32 CUDA-core peak probe: every thread runs 8 independent fused
+// multiply-add chains (enough to hide the FFMA latency at 16 warps per SM)
+// for `iters` rounds, 2 flops per FFMA.  The result is folded into `sink` so
+// that no chain can be removed.
+__global__ void __launch_bounds__(512) ffma_probe_kernel(long long iters, float* sink) {
+  float a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = static_cast<float>(threadIdx.x + i) * 1e-3f;
+  const float b = 0.999f, c = 1e-4f;
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = fmaf(a[i], b, c);
+    }
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t += a[i];
+  if (t == 123.456f) sink[blockIdx.x] = t;  // never true for these inputs; keeps the chains live
+}
+
+long long launch_ffma_probe(long long iters, float* sink, int num_sms, cudaStream_t s) {
+  const int blocks = num_sms * 4;
+  ffma_probe_kernel<<<blocks, 512, 0, s>>>(iters, sink);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  return 2LL * 8 * 16 * iters * 512 * blocks;
+}
+
 }  // namespace xc

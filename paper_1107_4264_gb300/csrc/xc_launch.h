@@ -116,6 +116,10 @@ int xengine_ring_slots(const Geometry& g);
 cudaError_t launch_fp32_xengine(const void* in, int in_dtype, void* out, const Geometry& g,
                                 int accumulate, const void* gains, cudaStream_t s);
 
+// FP32 peak probe (xc_fp32_peak_probe): returns the flops launched, -1 on a
+// launch error; `sink` is a device float array of 4 * num_sms elements.
+long long launch_ffma_probe(long long iters, float* sink, int num_sms, cudaStream_t s);
+
 // Adjoint of the float forward: H_f = G_f + G_f^H into `h_ws` ([F][n][n]
 // cf32), grad_in = conj(g) H_f (g x) (cf32, layout of the input) and
 // grad_g = sum conj(x) H_f (g x) (cf32 [n], may be NULL).
@@ -130,6 +134,13 @@ size_t adjoint_tc_workspace_bytes(const Geometry& g);
 cudaError_t launch_adjoint_tc(const void* grad_out, const void* in, const void* gains, void* grad_in,
                               float* grad_g, void* h_ws, void* tc_ws, const Geometry& g,
                               unsigned long long timeout_ns, int* status, cudaStream_t s);
+
+// The planar converters' TMA view of the input [T][F][n] (complex) of a
+// (virtual) geometry: 8-bit rows in 128 x 1 x kPlanarUnitT boxes, fp16 as
+// 32-bit complex elements in 64 x 1 x 32 boxes, fp32 components in
+// 128 x 1 x 16 boxes.  Possible when a row is a multiple of 16 bytes.
+bool input_map_possible(xc_dtype dtype, const Geometry& g);
+xc_status encode_input_map(CUtensorMap* map, const void* in, const Geometry& g, xc_dtype dtype);
 
 // Record `s` and a printf-style message as this thread's last error
 // (xc_last_error / xc_last_error_message); returns s.

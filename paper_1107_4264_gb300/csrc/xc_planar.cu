@@ -254,7 +254,23 @@ cudaError_t planar_setup(const XeLaunch* subs, int nsub, cudaStream_t s) {
 cudaError_t planar_launch(PlanarKernel& k, cudaStream_t s) {
   if (k.grid <= 0) return cudaSuccess;
   void* args[1] = {k.args};
-  return cudaLaunchKernel(k.func, dim3(k.grid), dim3(k.block), args, static_cast<size_t>(k.smem), s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(k.grid));
+  cfg.blockDim = dim3(static_cast<unsigned>(k.block));
+  cfg.dynamicSmemBytes = static_cast<size_t>(k.smem);
+  cfg.stream = s;
+  // The persistent CTAs wait on each other through the operand ring, so all
+  // of them must be resident at once.  A cooperative launch guarantees that
+  // or fails up front (cudaErrorCooperativeLaunchTooLarge, e.g. when part of
+  // the GPU's SMs are held by another context), instead of a kernel whose
+  // waits run out.  CTA-pair kernels rely on the cluster occupancy query of
+  // planar_prepare instead.
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = k.shape == kShapePair ? 0 : 1;
+  return cudaLaunchKernelExC(&cfg, k.func, args);
 }
 
 cudaError_t launch_planar(const CUtensorMap* in_map, const XeLaunch& L, int shape, cudaStream_t s) {

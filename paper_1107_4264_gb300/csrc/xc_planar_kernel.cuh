@@ -1137,8 +1137,11 @@ __device__ __forceinline__ void scale_piece(uint32_t (&re)[32], uint32_t (&im)[3
 __device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const uint32_t (&im)[32],
                                                 const Params& p, int f, int a, int b0, bool first,
                                                 bool last) {
-  if (a >= p.n) return;
   const int P = p.g.P;
+  // Every lane of the warp joins the pairs path's exchanges; rows past n
+  // (the ragged last block) only skip their memory accesses.
+  const bool valid = a < p.n;
+  if (!valid && !(P == 2 && p.pack == 1)) return;
   int s1 = a / P, joff = 0, fr = f;
   const int p1 = a - s1 * P;
   if (p.pack > 1) {  // packed channels: real channel and stations
@@ -1151,6 +1154,60 @@ __device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const 
   const bool load_old = !first || p.accumulate;
   double2* ws = reinterpret_cast<double2*>(p.acc64);
   float2* out = static_cast<float2*>(p.out);
+  if (P == 2 && p.pack == 1) {
+    // As the int32 store's pairs path: the lanes of a station's two
+    // polarisation rows (a, a ^ 1) exchange halves so that each holds one
+    // whole baseline record {(0,0), (0,1), (1,0), (1,1)}: the p1 = 0 lane the
+    // record of column station 2m, the p1 = 1 lane that of 2m + 1.  A lane
+    // then moves 64 contiguous bytes of running sums (and 32 of output), and
+    // a lane pair 128 contiguous bytes of one baseline row.
+    const int s2_0 = b0 / 2;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      float own[4], got[4];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float r0 = __uint_as_float(re[4 * m + q]), i0 = __uint_as_float(im[4 * m + q]);
+        const float r1 = __uint_as_float(re[4 * m + 2 + q]), i1 = __uint_as_float(im[4 * m + 2 + q]);
+        own[2 * q] = p1 ? r1 : r0;
+        own[2 * q + 1] = p1 ? i1 : i0;
+        got[2 * q] = __shfl_xor_sync(0xffffffffu, p1 ? r0 : r1, 1);
+        got[2 * q + 1] = __shfl_xor_sync(0xffffffffu, p1 ? i0 : i1, 1);
+      }
+      // Products (p1', p2) of the record: row p1' = 0 from the p1 = 0 lane.
+      double2 v[4];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float* r0 = p1 ? got : own;  // row 0 of the record
+        const float* r1 = p1 ? own : got;  // row 1
+        v[q] = make_double2(r0[2 * q], r0[2 * q + 1]);
+        v[2 + q] = make_double2(r1[2 * q], r1[2 * q + 1]);
+      }
+      const int s2 = s2_0 + 2 * m + p1;
+      if (!valid || s2 > s1) continue;
+      double2* w4 = ws + (krow + s2) * 4;
+      if (load_old) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double2 o = w4[k];
+          v[k].x += o.x;
+          v[k].y += o.y;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w4[k] = v[k];
+      if (last) {
+        uint32_t rec[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          rec[2 * k] = __float_as_uint(static_cast<float>(v[k].x));
+          rec[2 * k + 1] = __float_as_uint(static_cast<float>(v[k].y));
+        }
+        ptx::st_global_v8(out + (krow + s2) * 4, rec);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const int b = b0 + j;

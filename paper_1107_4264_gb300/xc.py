@@ -34,7 +34,7 @@ XC_PREC_FP16, XC_PREC_HILO, XC_PREC_FP8 = 0, 1, 2
  XC_ENGINE_TENSOR_PAIR) = 0, 1, 2, 3, 4
 XC_CI8_MAX_NTIME = 66572
 XC_BATCH_MAX_SUB = 8
-XC_BATCH_CANDIDATES = 6
+XC_BATCH_CANDIDATES = 36
 
 # Symbols declared in include/xc.h (checked by the tests against the header).
 EXPORTS = [
@@ -43,7 +43,8 @@ EXPORTS = [
     "xc_correlate_stream", "xc_input_bytes", "xc_output_bytes", "xc_tri_index", "xc_tri_coords",
     "xc_version", "xc_kernel_times", "xc_correlate_noalloc", "xc_set_gains", "xc_get_grad_gains",
     "xc_batch_create", "xc_batch_correlate", "xc_batch_tune", "xc_channelize",
-    "xc_channelize_pfb", "xc_channels_packed",
+    "xc_channelize_pfb", "xc_channels_packed", "xc_fp32_peak_probe", "xc_batch_set_cache",
+    "xc_batch_cache_key", "xc_batch_cache_lookup",
 ]
 
 _lib: Optional[ctypes.CDLL] = None
@@ -86,6 +87,11 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "xc_channelize": ([vp, i32, i32, i32, i32, i32, ctypes.c_float, vp, i32, vp], i32),
         "xc_channelize_pfb": ([vp, i32, i32, i32, i32, i32, vp, i32, ctypes.c_float, vp, i32, vp], i32),
         "xc_channels_packed": ([i32, i32, i32], i32),
+        "xc_fp32_peak_probe": ([ctypes.c_longlong, vp, vp, ctypes.POINTER(ctypes.c_longlong)], i32),
+        "xc_batch_set_cache": ([vp, ctypes.c_char_p], i32),
+        "xc_batch_cache_key": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), i32, i32,
+                                ctypes.c_char_p, sz], i32),
+        "xc_batch_cache_lookup": ([ctypes.c_char_p, ctypes.c_char_p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +229,14 @@ def xc_channelize_pfb(in_ptr: int, in_dtype: int, nstation: int, npol: int, ncha
 
 def xc_version() -> str:
     return load().xc_version().decode()
+
+
+def xc_fp32_peak_probe(iterations: int, sink_ptr: int, stream: int = 0) -> int:
+    """Launch the FP32 FFMA peak probe; returns the flops launched (time it with
+    CUDA events on `stream`)."""
+    flops = ctypes.c_longlong(0)
+    _check(load().xc_fp32_peak_probe(iterations, sink_ptr, stream, ctypes.byref(flops)))
+    return flops.value
 
 
 # ------------------------------------------------------ torch convenience
@@ -441,6 +455,24 @@ def xc_batch_tune(h: int, in_ptrs, out_ptrs, stream: int = 0, reps: int = 3):
     return list(ms), best.value
 
 
+def xc_batch_set_cache(h: int, path: Optional[str]) -> int:
+    return load().xc_batch_set_cache(h, path.encode() if path else None)
+
+
+def xc_batch_cache_key(nstation, nfreq, ntime, npol: int, in_dtype: int) -> str:
+    n = len(nstation)
+    arr = ctypes.c_int * n
+    buf = ctypes.create_string_buffer(512)
+    k = load().xc_batch_cache_key(n, arr(*nstation), arr(*nfreq), arr(*ntime), npol, in_dtype, buf, 512)
+    if k < 0:
+        raise ValueError("bad batch key arguments")
+    return buf.value.decode()
+
+
+def xc_batch_cache_lookup(path: str, key: str) -> int:
+    return load().xc_batch_cache_lookup(path.encode(), key.encode())
+
+
 class BatchCorrelator:
     """Subarrays ``[(nstation, nfreq, ntime), ...]`` (8-bit input, one npol)
     correlated by one persistent launch replayed from a CUDA graph."""
@@ -488,6 +520,10 @@ class BatchCorrelator:
         if sync:
             _check(xc_synchronize(self.h, s))
         return outs
+
+    def set_cache(self, path: Optional[str]) -> None:
+        """Tuning file for tune(): a recorded choice is applied without timing."""
+        _check(xc_batch_set_cache(self.h, path))
 
     def tune(self, xs, outs, reps: int = 3, stream=None):
         self._check_bufs(xs, outs)

@@ -123,6 +123,12 @@ def test_channels_packed_rule(lib):
     assert lib.xc_channels_packed(16, 2, 1024) == 4
     assert lib.xc_channels_packed(256, 2, 1024) == 1
     assert lib.xc_channels_packed(0, 2, 8) == 0
+    # sizes xc_create rejects give 0: npol outside {1, 2}, more than 2^30 rows
+    for P in (0, 3, 4, -1):
+        assert lib.xc_channels_packed(16, P, 8) == 0, P
+    assert lib.xc_channels_packed(2 ** 28, 2, 8) == 1  # 2^30 rows: accepted
+    assert lib.xc_channels_packed(2 ** 28 + 1, 2, 8) == 0
+    assert lib.xc_channels_packed(2 ** 31 - 1, 2, 8) == 0  # 2 P N would overflow int
 
 
 def test_tri_map_round_trip_exhaustive(lib):

@@ -61,16 +61,57 @@ def test_batch_graph_replay_new_buffers_and_accumulate(dev):
 
 
 def test_batch_tune_then_exact(dev):
+    """The tuner times tile shape x packing x ring depth x order; the launch
+    it keeps is bit-exact, and so is every forced candidate."""
     xs = [x.to(dev) for x in inputs(SMALL, 2, 700)]
     bc = xc.BatchCorrelator(SMALL, npol=2)
     try:
         outs = bc.new_outputs()
         ms, best = bc.tune(xs, outs, reps=2)
         assert 0 <= best < xc.XC_BATCH_CANDIDATES
-        assert all(m > 0 for m in ms)
+        timed = [c for c, m in enumerate(ms) if m > 0]
+        # every shape, both depths and all orders; packing only if a subarray packs
+        assert {c // 12 for c in timed} == {0, 1, 2}
+        assert {(c // 3) % 2 for c in timed} == {0, 1} and {c % 3 for c in timed} == {0, 1, 2}
+        assert ms[best] == min(ms[c] for c in timed)
         outs = bc.correlate(xs, sync=True)
-        for x, o in zip(xs, outs):
-            np.testing.assert_array_equal(o.cpu().numpy(), oracle.correlate_i8(x.cpu().numpy()))
+        want = [oracle.correlate_i8(x.cpu().numpy()) for x in xs]
+        for w, o in zip(want, outs):
+            np.testing.assert_array_equal(o.cpu().numpy(), w)
+        # each tile shape forced in turn, through the captured graph
+        for tile in (xc.XC_TILE_128, xc.XC_TILE_PAIR, xc.XC_TILE_WIDE):
+            bc.set_option(xc.XC_OPT_TILE, tile)
+            outs = bc.correlate(xs, sync=True)
+            for w, o in zip(want, outs):
+                np.testing.assert_array_equal(o.cpu().numpy(), w)
+    finally:
+        bc.close()
+
+
+def test_batch_tuning_file(dev, tmp_path):
+    """A tuning file records the winner; a second handle for the same batch
+    applies it without timing anything, and stays exact."""
+    path = str(tmp_path / "tune.txt")
+    xs = [x.to(dev) for x in inputs(SMALL, 2, 300)]
+    want = [oracle.correlate_i8(x.cpu().numpy()) for x in xs]
+    bc = xc.BatchCorrelator(SMALL, npol=2)
+    try:
+        bc.set_cache(path)
+        ms, best = bc.tune(xs, bc.new_outputs(), reps=1)
+    finally:
+        bc.close()
+    key = xc.xc_batch_cache_key([s[0] for s in SMALL], [s[1] for s in SMALL], [s[2] for s in SMALL], 2,
+                                xc.XC_CI8)
+    assert xc.xc_batch_cache_lookup(path, key) == best
+    bc = xc.BatchCorrelator(SMALL, npol=2)
+    try:
+        bc.set_cache(path)
+        ms2, best2 = bc.tune(xs, bc.new_outputs(), reps=1)
+        assert best2 == best
+        assert [c for c, m in enumerate(ms2) if m >= 0] == [best]  # nothing else timed
+        outs = bc.correlate(xs, sync=True)
+        for w, o in zip(want, outs):
+            np.testing.assert_array_equal(o.cpu().numpy(), w)
     finally:
         bc.close()
 
@@ -108,9 +149,9 @@ def _slice_check(x, out, N, c, lo, hi):
 
 def test_batched_workload(dev):
     """The six-subarray workload (N = 32 ... 1024, 1.606e13 useful ops) in one
-    launch: sampled channels against the oracle (whole channels for the
-    smaller subarrays, station slices for N = 1024), every subarray against
-    the single-subarray engine in full."""
+    launch: sampled whole channels against the oracle (two per subarray up to
+    N = 384, one for N = 1024), every subarray against the single-subarray
+    engine in full."""
     subs = [(w.nstation, w.nfreq, w.ntime) for w in synth.BATCHED]
     xs = [synth.int8_sky(w, device=dev) for w in synth.BATCHED]
     bc = xc.BatchCorrelator(subs, npol=2)
@@ -123,9 +164,16 @@ def test_batched_workload(dev):
                 want = oracle.correlate_i8(x[:, chans].cpu().numpy())
                 np.testing.assert_array_equal(o[chans].cpu().numpy(), want)
             else:
+                # One whole channel of the N = 1024 subarray.  The oracle runs
+                # in parallel over channels, so the channel's T samples are
+                # cut into 16 time ranges presented as 16 channels; their
+                # integer partial sums add up exactly.
                 c = int(rng.integers(F))
+                xc_ = x[:, c].cpu().numpy()  # [T][N][P][2]
+                parts = xc_.reshape(16, T // 16, N, 2, 2).transpose(1, 0, 2, 3, 4)
+                want = oracle.correlate_i8(np.ascontiguousarray(parts)).sum(axis=0)
+                np.testing.assert_array_equal(o[c].cpu().numpy().astype(np.int64), want)
                 _slice_check(x, o, N, c, 0, 48)
-                _slice_check(x, o, N, c, N - 48, N)
             eng = xc.Correlator(N, 2, F, T, "int8")
             try:
                 single = eng.correlate(x, sync=True)

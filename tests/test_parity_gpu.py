@@ -166,6 +166,44 @@ def test_large_n_sampled_channels(dev):
         del out
 
 
+def test_large_n_streamed_depth(dev):
+    """The benchmark's workload as a user runs it: 10 Large-N integrations
+    (N=256 x 2 pols, F=1024, T=1000) streamed from pinned host memory through
+    xc_correlate_stream (Algorithm 1 of Sec. 5, dump mode: one output per
+    integration, each copied back to pinned host memory).  The operand ring
+    wraps 34 times per integration.  Checked bit-exactly against the oracle:
+    every channel of integration 0 and 64 seeded channels of each of
+    integrations 1..9 (1600 channels, 1.7e12 useful ops on the host), and
+    the device outputs equal the copies that came back."""
+    w = synth.LARGE_N
+    nint = 10
+    host_in = torch.empty((nint,) + w.shape, dtype=torch.int8, pin_memory=True)
+    for i in range(nint):
+        host_in[i].copy_(synth.large_n_input(w, i, device=dev))
+    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "int8")
+    try:
+        out = eng.new_output(nint, device=dev)
+        host_out = torch.empty((nint,) + w.out_shape, dtype=torch.int32, pin_memory=True)
+        eng.correlate_stream(host_in, nint, out, host_out=host_out)
+        eng.synchronize()
+        for i in (0, nint - 1):
+            assert torch.equal(out[i].cpu(), host_out[i])
+    finally:
+        eng.close()
+    del out
+    x0 = host_in[0].numpy()
+    for c0 in range(0, w.nfreq, 128):
+        want = oracle.correlate_i8(np.ascontiguousarray(x0[:, c0:c0 + 128]))
+        got = host_out[0, c0:c0 + 128].numpy().astype(np.int64)
+        assert np.array_equal(got, want), "integration 0, channels %d..%d" % (c0, c0 + 127)
+    rng = np.random.default_rng(w.seed + 99)
+    for i in range(1, nint):
+        chans = sorted(rng.choice(w.nfreq, size=64, replace=False).tolist())
+        want = oracle.correlate_i8(np.ascontiguousarray(host_in[i].numpy()[:, chans]))
+        got = host_out[i].numpy()[chans].astype(np.int64)
+        assert np.array_equal(got, want), "integration %d" % i
+
+
 def frob_and_maxnorm(got, want, N, P):
     """Per-channel Frobenius relative error and max |dV_ab| / sqrt(V_aa V_bb)."""
     g = got[..., 0] + 1j * got[..., 1]

@@ -171,24 +171,36 @@ def test_precision_options_validated(dev):
         eng.close()
 
 
-@pytest.mark.parametrize("prec", list(PRECS))
-def test_precision_workload_sampled(prec, dev):
+@pytest.fixture(scope="module")
+def precision_workload(dev):
     """Precision workload at full size (N=512 x 2 pols, F=480, T=2048, fp16
-    input, random gains): errors of two sampled channels against the oracle."""
+    input, random gains) and the FP64 oracle on 32 seeded channels."""
     w = synth.PRECISION
     x, g = synth.precision_input(w, device=dev)
     x16 = x.to(torch.float16)
     del x
-    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "float16", precision=PRECS[prec])
+    rng = np.random.default_rng(w.seed + 3)
+    chans = sorted(rng.choice(w.nfreq, size=32, replace=False).tolist())
+    want = oracle.correlate_f64(x16[:, chans].cpu().double().numpy(), gains=g)
+    return w, x16, g, chans, want
+
+
+@pytest.mark.parametrize("prec,fp64_block", [("fp16", 0), ("hilo", 0), ("fp8", 0), ("fp16", 1024)],
+                         ids=["fp16", "hilo", "fp8", "fp16_fp64_blocks"])
+def test_precision_workload_sampled(prec, fp64_block, precision_workload, dev):
+    """Each precision form on the full precision workload, in the launch the
+    benchmark times: errors of 32 seeded channels against the FP64 oracle."""
+    w, x16, g, chans, want = precision_workload
+    eng = xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "float16", precision=PRECS[prec],
+                        fp64_block=fp64_block)
     try:
         eng.set_gains(torch.from_numpy(g).float().to(dev))
         out = eng.correlate(x16, sync=True)
-        chans = [3, 401]
         got = out[chans].cpu().double().numpy()
-        xs = x16[:, chans].cpu().double().numpy()
     finally:
         eng.close()
-    want = oracle.correlate_f64(xs, gains=g)
     frob, mx = frob_and_maxnorm(got, want, w.nstation, w.npol)
-    print(f"\nprecision workload {prec}: frobenius {frob:.3e} max-norm {mx:.3e}")
+    print(f"\nprecision workload {prec} (fp64 blocks {fp64_block}): frobenius {frob:.3e} max-norm {mx:.3e}")
     assert frob <= FROB_TOL[prec], frob
+    if prec == "fp16":
+        assert mx <= 1e-3, mx
