@@ -1152,6 +1152,9 @@ __device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const 
   }
   const int64_t krow = static_cast<int64_t>(fr) * p.NBr + static_cast<int64_t>(s1) * (s1 + 1) / 2;
   const bool load_old = !first || p.accumulate;
+  // The running sum outlives this drain unless it is the integration's last
+  // one and calls do not accumulate.
+  const bool keep = !last || p.accumulate;
   double2* ws = reinterpret_cast<double2*>(p.acc64);
   float2* out = static_cast<float2*>(p.out);
   if (P == 2 && p.pack == 1) {
@@ -1162,48 +1165,68 @@ __device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const 
     // then moves 64 contiguous bytes of running sums (and 32 of output), and
     // a lane pair 128 contiguous bytes of one baseline row.
     const int s2_0 = b0 / 2;
+    // Groups of MG records: the running sums of a group are loaded before
+    // any of its stores (the compiler cannot move a load above a store to
+    // the same buffer), so their memory latencies overlap.
+    constexpr int MG = 2;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      float own[4], got[4];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float r0 = __uint_as_float(re[4 * m + q]), i0 = __uint_as_float(im[4 * m + q]);
-        const float r1 = __uint_as_float(re[4 * m + 2 + q]), i1 = __uint_as_float(im[4 * m + 2 + q]);
-        own[2 * q] = p1 ? r1 : r0;
-        own[2 * q + 1] = p1 ? i1 : i0;
-        got[2 * q] = __shfl_xor_sync(0xffffffffu, p1 ? r0 : r1, 1);
-        got[2 * q + 1] = __shfl_xor_sync(0xffffffffu, p1 ? i0 : i1, 1);
-      }
-      // Products (p1', p2) of the record: row p1' = 0 from the p1 = 0 lane.
-      double2 v[4];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float* r0 = p1 ? got : own;  // row 0 of the record
-        const float* r1 = p1 ? own : got;  // row 1
-        v[q] = make_double2(r0[2 * q], r0[2 * q + 1]);
-        v[2 + q] = make_double2(r1[2 * q], r1[2 * q + 1]);
-      }
-      const int s2 = s2_0 + 2 * m + p1;
-      if (!valid || s2 > s1) continue;
-      double2* w4 = ws + (krow + s2) * 4;
+    for (int h = 0; h < 8 / MG; ++h) {
+      double2 old[MG][4];
       if (load_old) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const double2 o = w4[k];
-          v[k].x += o.x;
-          v[k].y += o.y;
+        for (int mm = 0; mm < MG; ++mm) {
+          const int s2 = s2_0 + 2 * (MG * h + mm) + p1;
+          const bool ok = valid && s2 <= s1;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            old[mm][k] = ok ? ws[(krow + s2) * 4 + k] : make_double2(0.0, 0.0);
         }
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) w4[k] = v[k];
-      if (last) {
-        uint32_t rec[8];
+      for (int mm = 0; mm < MG; ++mm) {
+        const int m = MG * h + mm;
+        float own[4], got[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          rec[2 * k] = __float_as_uint(static_cast<float>(v[k].x));
-          rec[2 * k + 1] = __float_as_uint(static_cast<float>(v[k].y));
+        for (int q = 0; q < 2; ++q) {
+          const float r0 = __uint_as_float(re[4 * m + q]), i0 = __uint_as_float(im[4 * m + q]);
+          const float r1 = __uint_as_float(re[4 * m + 2 + q]), i1 = __uint_as_float(im[4 * m + 2 + q]);
+          own[2 * q] = p1 ? r1 : r0;
+          own[2 * q + 1] = p1 ? i1 : i0;
+          got[2 * q] = __shfl_xor_sync(0xffffffffu, p1 ? r0 : r1, 1);
+          got[2 * q + 1] = __shfl_xor_sync(0xffffffffu, p1 ? i0 : i1, 1);
         }
-        ptx::st_global_v8(out + (krow + s2) * 4, rec);
+        // Products (p1', p2) of the record: row p1' = 0 from the p1 = 0 lane.
+        double2 v[4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float* r0 = p1 ? got : own;  // row 0 of the record
+          const float* r1 = p1 ? own : got;  // row 1
+          v[q] = make_double2(r0[2 * q], r0[2 * q + 1]);
+          v[2 + q] = make_double2(r1[2 * q], r1[2 * q + 1]);
+        }
+        const int s2 = s2_0 + 2 * m + p1;
+        if (!valid || s2 > s1) continue;
+        double2* w4 = ws + (krow + s2) * 4;
+        if (load_old) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            v[k].x += old[mm][k].x;
+            v[k].y += old[mm][k].y;
+          }
+        }
+        if (keep) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) w4[k] = v[k];
+        }
+        if (last) {
+          uint32_t rec[8];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            rec[2 * k] = __float_as_uint(static_cast<float>(v[k].x));
+            rec[2 * k + 1] = __float_as_uint(static_cast<float>(v[k].y));
+          }
+          ptx::st_global_v8(out + (krow + s2) * 4, rec);
+        }
       }
     }
     return;
@@ -1221,7 +1244,7 @@ __device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const 
       v.x += o.x;
       v.y += o.y;
     }
-    ws[idx] = v;
+    if (!last || p.accumulate) ws[idx] = v;
     if (last) out[idx] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
   }
 }
@@ -1338,7 +1361,7 @@ __device__ __forceinline__ void store_piece_f64_tr(const uint32_t (&re)[32], con
       v.x += o.x;
       v.y += o.y;
     }
-    ws[idx] = v;
+    if (!last || p.accumulate) ws[idx] = v;
     if (last) out[idx] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
   }
 }
@@ -1765,13 +1788,42 @@ __device__ __forceinline__ void planar_body(const Batch& bt) {
         const int kb1 = min(p.nkb, kb0 + chunk_kb);
         const int gstep = kTmemSum ? 1 : (kb1 - kb0);
         const bool add = p.accumulate || ch > 0;
-        const bool first = ch == 0, last_chunk = ch == nchunks - 1;
+        const bool last_chunk = ch == nchunks - 1;
+        // FP64 block sums: chunks pair off, (0, 1), (2, 3), ...  The first
+        // chunk of a pair stays in its TMEM accumulator (`hold`); the second's
+        // drain adds it in fp32 (a correctly rounded sum of the two partials,
+        // what an fp64 add rounded back would give) and updates the float64
+        // running sum once per pair: half the passes over it, none at all for
+        // an integration of two chunks.  Needs the two accumulator sets.
+        const bool f64pair = !IS_INT && !kOneSet && p.acc64 != nullptr;
+        const bool hold = f64pair && (ch % 2 == 0) && ch + 1 < nchunks;
+        const bool paired = f64pair && (ch % 2 == 1);
+        const bool first = f64pair ? ch < 2 : ch == 0;
         for (int g0 = kb0; g0 < kb1; g0 += gstep) {
           // TMEM running sum: the first group of a chunk starts it, the last
           // one is stored; groups in between only add into it.
           const bool gfirst = g0 == kb0, glast = g0 + gstep >= kb1;
           const uint32_t ab = kOneSet ? 0u : (u & 1u);
           const uint32_t ap = kOneSet ? (u & 1u) : ((u >> 1) & 1u);
+          if constexpr (!IS_INT) {
+            // FP64 block sums: while the MMAs run, bring into L2 the running
+            // sums this drain will read: each lane of a row's pair prefetches
+            // half of the row's records in the block (one bulk request).
+            if (p.acc64 && !hold && (!first || p.accumulate) && glast && P == 2 && p.pack == 1 && a < p.n) {
+              const int s1 = a / 2;
+              const int64_t krow = static_cast<int64_t>(f) * p.NBr + static_cast<int64_t>(s1) * (s1 + 1) / 2;
+              for (int j = 0; j < nblk; ++j) {
+                const int b = cb[j];
+                if (b > k.a) continue;  // mirrored blocks write other rows
+                const int lo = b * (kBlk / 2), hi = min(b * (kBlk / 2) + kBlk / 2 - 1, s1);
+                const int half = (hi - lo + 2) / 2;
+                const int from = lo + (a & 1) * half, cnt = min(half, hi - from + 1);
+                if (cnt > 0)
+                  ptx::bulk_prefetch_l2(reinterpret_cast<const double2*>(p.acc64) + (krow + from) * 4,
+                                        static_cast<uint32_t>(cnt) * 64u);
+              }
+            }
+          }
           const bool got = ptx::wait_bounded(accf_bar(ab), ap, wc);
           if (!__all_sync(0xffffffffu, got)) {
             ok = false;
@@ -1783,6 +1835,36 @@ __device__ __forceinline__ void planar_body(const Batch& bt) {
           // its ring slot.  (Released here, off the MMA thread's path.)
           if (last_chunk && glast && q == 0 && lane == 0 && leader)
             red_release_add(p.done + (f % p.ring_slots), 1u);
+          if (hold) {  // drained with the next chunk
+            ++u;
+            continue;
+          }
+          if (paired) {
+            // Add the held chunk into this one inside TMEM and free it at
+            // once, so the next item's MMAs need not wait for the stores.
+            for (int j = 0; j < nblk; ++j) {
+              const uint32_t c_re = ab * 256, c_im = ab * 256 + 128;
+              const uint32_t h_re = (ab ^ 1u) * 256, h_im = (ab ^ 1u) * 256 + 128;
+#pragma unroll 1
+              for (int piece = first_p[j]; piece <= last_p[j]; ++piece) {
+                uint32_t vr[32], vi[32], sr[32], si[32];
+                ptx::tmem_ld_32x32b_x32(t_lanes + c_re + piece * 32, vr);
+                ptx::tmem_ld_32x32b_x32(t_lanes + c_im + piece * 32, vi);
+                ptx::tmem_ld_32x32b_x32(t_lanes + h_re + piece * 32, sr);
+                ptx::tmem_ld_32x32b_x32(t_lanes + h_im + piece * 32, si);
+                ptx::tmem_wait_ld();
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                  vr[jj] = __float_as_uint(__uint_as_float(vr[jj]) + __uint_as_float(sr[jj]));
+                  vi[jj] = __float_as_uint(__uint_as_float(vi[jj]) + __uint_as_float(si[jj]));
+                }
+                ptx::tmem_st_32x32b_x32(t_lanes + c_re + piece * 32, vr);
+                ptx::tmem_st_32x32b_x32(t_lanes + c_im + piece * 32, vi);
+              }
+            }
+            ptx::tmem_wait_st();
+            release_acc(ab ^ 1u);
+          }
           if (jlast < 0) release_acc(ab);
           for (int j = 0; j < nblk; ++j) {
             const int b = cb[j];
@@ -1795,17 +1877,17 @@ __device__ __forceinline__ void planar_body(const Batch& bt) {
               ptx::tmem_ld_32x32b_x32(t_lanes + c_re + piece * 32, vr);
               ptx::tmem_ld_32x32b_x32(t_lanes + c_im + piece * 32, vi);
               if constexpr (kTmemSum) {
-                if (!gfirst) {
-                  uint32_t sr[32], si[32];
-                  ptx::tmem_ld_32x32b_x32(t_lanes + 256 + piece * 32, sr);
-                  ptx::tmem_ld_32x32b_x32(t_lanes + 384 + piece * 32, si);
-                  ptx::tmem_wait_ld();
+               if (!gfirst) {
+                uint32_t sr[32], si[32];
+                ptx::tmem_ld_32x32b_x32(t_lanes + 256 + piece * 32, sr);
+                ptx::tmem_ld_32x32b_x32(t_lanes + 384 + piece * 32, si);
+                ptx::tmem_wait_ld();
 #pragma unroll
-                  for (int jj = 0; jj < 32; ++jj) {
-                    vr[jj] = __float_as_uint(__uint_as_float(vr[jj]) + __uint_as_float(sr[jj]));
-                    vi[jj] = __float_as_uint(__uint_as_float(vi[jj]) + __uint_as_float(si[jj]));
-                  }
+                for (int jj = 0; jj < 32; ++jj) {
+                  vr[jj] = __float_as_uint(__uint_as_float(vr[jj]) + __uint_as_float(sr[jj]));
+                  vi[jj] = __float_as_uint(__uint_as_float(vi[jj]) + __uint_as_float(si[jj]));
                 }
+               }
               }
               ptx::tmem_wait_ld();
               if (j == jlast && piece == last_p[j]) release_acc(ab);
@@ -1823,7 +1905,10 @@ __device__ __forceinline__ void planar_body(const Batch& bt) {
                   store_piece<true>(vr, vi, p, f, a, b0, add);
               } else {
                 if (p.in_amax) scale_piece<FMT>(vr, vi, p, f, a, b0);
-                if (p.acc64) {
+                // A drain that is both the first and the last of the running
+                // sum (one chunk, or one chunk pair, without accumulation
+                // across calls) only rounds to fp32: the plain store.
+                if (p.acc64 && !(first && last_chunk && !p.accumulate)) {
                   if (tr)
                     store_piece_f64_tr(vr, vi, p, f, a, b0, first, last_chunk);
                   else

@@ -325,6 +325,12 @@ __device__ __forceinline__ uint64_t interleave_kmajor_desc(uint32_t saddr, uint3
          (static_cast<uint64_t>(1) << 46);                  // descriptor version; layout 0
 }
 
+// Prefetch `bytes` contiguous bytes of global memory into L2 (16-byte
+// aligned address, size a multiple of 16); nothing waits for it.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Bulk copy (no tensor map) of `bytes` contiguous bytes global -> shared,
 // completing on `bar` (16-byte aligned addresses, size a multiple of 16).
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
