@@ -734,11 +734,19 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
 #pragma unroll
       for (int t = 0; t < kUnitT; ++t) mb = __vmaxu4(mb, __vabs4(w[t]));
       m = max(max(mb & 0xffu, (mb >> 8) & 0xffu), max((mb >> 16) & 0xffu, mb >> 24));
+      // Component j of four consecutive samples as four e4m3 bytes: the
+      // exact fp16 pair conversion of the fp16 path, then one fp16x2 ->
+      // e4m3x2 conversion per pair (exact for |x| <= 16).
       auto cvt4 = [](uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t j) {
-        auto f = [j](uint32_t wv) {
-          return static_cast<float>(static_cast<int8_t>((wv >> (8 * j)) & 0xffu));
-        };
-        return e4m3x4(f(w0), f(w1), f(w2), f(w3));
+        const uint32_t h01 = pair_i8(w0, w1, j), h23 = pair_i8(w2, w3, j);
+        __half2_raw r01, r23;
+        r01.x = static_cast<unsigned short>(h01 & 0xffffu);
+        r01.y = static_cast<unsigned short>(h01 >> 16);
+        r23.x = static_cast<unsigned short>(h23 & 0xffffu);
+        r23.y = static_cast<unsigned short>(h23 >> 16);
+        const uint32_t e01 = __nv_cvt_halfraw2_to_fp8x2(r01, __NV_SATFINITE, __NV_E4M3);
+        const uint32_t e23 = __nv_cvt_halfraw2_to_fp8x2(r23, __NV_SATFINITE, __NV_E4M3);
+        return (e01 & 0xffffu) | (e23 << 16);
       };
 #pragma unroll
       for (int cc = 0; cc < kUnitT / 16; ++cc) {
