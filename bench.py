@@ -121,6 +121,16 @@ def executed_ops(N, P, F, T, steps_per_block=1):
     return 8 * macs * ((T + 63) // 64 * 64) * fv * steps_per_block
 
 
+def small_executed_ops(N, P, F, T):
+    """Real operations the small-array engine's MMAs execute: per group of
+    m = 128 / W channels (W = 2 N P) and 64-sample stage, m MMAs of
+    128 x W x 64, over T padded to 64."""
+    from paper_1107_4264_gb300 import xc
+    m = xc.load().xc_small_engine_channels(N, P)
+    W = 2 * N * P
+    return 2 * 128 * W * m * ((T + 63) // 64 * 64) * ((F + m - 1) // m)
+
+
 def source_sha(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -626,10 +636,11 @@ def run_sweep(args):
     xc.load()
     dev = torch.device("cuda")
 
-    def measure(N, F, T, reps=10):
+    def measure(N, F, T, reps=10, tile=xc.XC_TILE_AUTO):
         x = synth.sky_voltages(T, F, N, 2, noise_sigma=3.0, nsrc=3, src_amp=1.5, seed=4242 + N + T,
                                device=dev, quantise_int8=True)
-        eng = xc.Correlator(N, 2, F, T, "int8")
+        small = tile == xc.XC_TILE_AUTO and xc.load().xc_small_engine_channels(N, 2) > 0
+        eng = xc.Correlator(N, 2, F, T, "int8", tile=tile)
         out = eng.new_output()
         for _ in range(2):
             eng.correlate(x, out=out)
@@ -643,9 +654,11 @@ def run_sweep(args):
         eng.close()
         ms = kms / max(nk, 1)
         useful = 8 * F * T * 4 * N * (N + 1) // 2
-        executed = executed_ops(N, 2, F, T)
+        executed = small_executed_ops(N, 2, F, T) if small else executed_ops(N, 2, F, T)
         in_b, out_b = T * F * N * 4, F * N * (N + 1) // 2 * 4 * 8
-        return {"N": N, "F": F, "T": T, "channels_packed": planar_pack(N, 2, F),
+        return {"N": N, "F": F, "T": T, "engine": "small" if small else "planar",
+                "channels_per_tile": xc.load().xc_small_engine_channels(N, 2) if small
+                else planar_pack(N, 2, F),
                 "kernel_ms": ms, "tops": useful / ms / 1e9,
                 "executed_tflops": executed / ms / 1e9, "useful_fraction": useful / executed,
                 "hbm_gbs_algorithmic": (in_b + out_b) / ms / 1e6}
@@ -655,10 +668,12 @@ def run_sweep(args):
         # Channel counts are multiples of 8, as channelised data usually is.
         F = max(8, min(65528, int(round(1.1e12 / (8 * 1000 * 4 * N * (N + 1) / 2))) // 8 * 8))
         by_n.append(measure(N, F, 1000))
+        if by_n[-1]["engine"] == "small":  # the planar engine on the same sizes
+            by_n.append(measure(N, F, 1000, tile=xc.XC_TILE_128))
     by_t = []
     for T in (125, 250, 500, 1000, 2000, 4000, 8000):
         by_t.append(measure(256, 1024000 // T, T))
-    print(json.dumps({"sweep": "planar_kernel<int8>, GB300, 1 GPU", "by_nstation": by_n,
+    print(json.dumps({"sweep": "small_kernel / planar_kernel <int8>, GB300, 1 GPU", "by_nstation": by_n,
                       "by_ntime_fixed_FT": by_t}))
     return 0
 

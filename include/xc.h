@@ -209,10 +209,26 @@ enum { XC_PREC_FP16 = 0, XC_PREC_HILO = 1, XC_PREC_FP8 = 2 };
  *     128 x 256 MMA per step (N = 256; one TMEM accumulator set): a quarter
  *     fewer shared-memory and L2 operand bytes per MAC than XC_TILE_128.  Not
  *     with XC_PREC_HILO (XC_ERR_UNSUPPORTED at the call).
- *   XC_TILE_AUTO: XC_TILE_128, the fastest shape measured on the Large-N
+ *   XC_TILE_SMALL: the small-array engine (8-bit input, fp16 operands,
+ *     W = 2 * nstation * npol in {16, 32, 64, 128}).  Each input is two real
+ *     rows (re, im) of a 128-row tile that holds 128 / W channels; per
+ *     16-sample step one 128 x W MMA per channel takes the whole tile as A
+ *     and the channel's own W rows as B, giving the real Gram matrix whose
+ *     2 x 2 sub-blocks form V (Sec. 4.4's diagonal blocks at twice the
+ *     planar density).  Operands are converted straight into shared memory:
+ *     no operand ring, one read of the input.  When the channel groups
+ *     (ceil(nfreq * W / 128)) are fewer than twice the SM count, T is split
+ *     across CTAs and partial sums are added with integer atomics into the
+ *     output, which the call zeroes first unless XC_OPT_ACCUMULATE is set.
+ *     XC_ERR_UNSUPPORTED at the call for other sizes, input types or
+ *     operand forms, and for batch handles.
+ *   XC_TILE_AUTO: XC_TILE_SMALL where it applies (see
+ *     xc_small_engine_channels; an input pointer that is not 16-byte aligned
+ *     and the XC_OPT_TEST_NO_PUBLISH hook keep the planar engine), else
+ *     XC_TILE_128, the fastest planar shape measured on the Large-N
  *     workload.  A batch handle takes the shape xc_batch_tune chose
  *     (XC_TILE_AUTO restores the default). */
-enum { XC_TILE_AUTO = 0, XC_TILE_128 = 1, XC_TILE_PAIR = 2, XC_TILE_WIDE = 3 };
+enum { XC_TILE_AUTO = 0, XC_TILE_128 = 1, XC_TILE_PAIR = 2, XC_TILE_WIDE = 3, XC_TILE_SMALL = 4 };
 /* Engines:
  *   XC_ENGINE_TENSOR (default): one fused persistent tcgen05 kernel in
  *     planar complex form (real and imaginary fp16 operand planes, four MMAs
@@ -298,6 +314,15 @@ void xc_tri_coords(int64_t g, int64_t* bx, int64_t* by);
  * not 1 or 2, more than 2^30 rows).
  */
 int xc_channels_packed(int nstation, int npol, int nfreq);
+
+/*
+ * Channels per 128-row tile of the small-array engine (XC_TILE_SMALL) for
+ * these sizes: 128 / (2 * nstation * npol) when that product is 16, 32, 64
+ * or 128, else 0 (the planar engine serves the sizes).  Host-side, no device
+ * work.  With XC_TILE_AUTO an 8-bit, fp16-operand handle of such sizes runs
+ * on the small-array engine, and xc_channels_packed does not apply to it.
+ */
+int xc_small_engine_channels(int nstation, int npol);
 
 /*
  * No-allocation X-engine (the paper has no counterpart; this is a service

@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libxc.so")
 
-SOURCES = ["xc_api.cpp", "xc_form.cu", "xc_tc.cu", "xc_fp32.cu", "xc_noalloc.cu", "xc_xengine.cu", "xc_xengine2.cu", "xc_planar.cu", "xc_planar_pair.cu", "xc_planar_wide.cu", "xc_adjoint.cu", "xc_adjoint_tc.cu", "xc_fengine.cu"]
+SOURCES = ["xc_api.cpp", "xc_form.cu", "xc_tc.cu", "xc_fp32.cu", "xc_noalloc.cu", "xc_xengine.cu", "xc_xengine2.cu", "xc_planar.cu", "xc_planar_pair.cu", "xc_planar_wide.cu", "xc_small.cu", "xc_adjoint.cu", "xc_adjoint_tc.cu", "xc_fengine.cu"]
 HEADERS = ["xc_internal.h", "xc_launch.h", "xc_ptx.cuh", "xc_convert.cuh", "xc_planar_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -239,6 +239,15 @@ xc_handle::Timed* next_timed(xc_handle* h, int nkern) {
   return t;
 }
 
+// The small-array engine serves XC_ENGINE_TENSOR handles with 8-bit input,
+// fp16 operands and 2 N P in {16, 32, 64, 128} (XC_TILE_AUTO or
+// XC_TILE_SMALL); the planar engine's test hook keeps a handle on that engine.
+bool use_small_engine(const xc_handle* h, const void* in) {
+  return h->dtype == XC_CI8 && h->precision == XC_PREC_FP16 && !h->test_no_publish &&
+         (h->tile == XC_TILE_AUTO || h->tile == XC_TILE_SMALL) && xc::small_tile_channels(h->g) > 0 &&
+         aligned16(in);
+}
+
 xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
   if (h->batch) return fail(XC_ERR_UNSUPPORTED, "batch handle: use xc_batch_correlate");
   cudaError_t e;
@@ -259,6 +268,28 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     if (tm) cudaEventRecord(tm->ev[1], s);
     return succeed();
   }
+  if (h->engine == XC_ENGINE_TENSOR && use_small_engine(h, in)) {
+    // Small arrays, 8-bit input: real-row tiles converted in shared memory.
+    xc::XeLaunch X;
+    X.g = h->g;
+    X.in = in;
+    X.in_dtype = 0;
+    X.out = out;
+    X.accumulate = h->accumulate;
+    X.grid = h->num_sms;
+    X.timeout_ns = h->timeout_ns;
+    X.status = h->d_status;
+    CUtensorMap in_map;
+    if (xc::encode_small_map(&in_map, in, h->g) != XC_OK) return t_status;
+    if (tm) tm->nkern = 1;
+    e = xc::launch_small(&in_map, X, s);
+    if (e != cudaSuccess) return cuda_fail(e, "small-array tensor-core X-engine launch");
+    if (tm) cudaEventRecord(tm->ev[1], s);
+    return succeed();
+  }
+  if (h->engine == XC_ENGINE_TENSOR && h->tile == XC_TILE_SMALL)
+    return fail(XC_ERR_UNSUPPORTED,
+                "XC_TILE_SMALL needs 8-bit input, fp16 operands and 2*nstation*npol in {16, 32, 64, 128}");
   if (h->engine == XC_ENGINE_TENSOR) {
     xc::XeLaunch X;
     X.g = h->pg;
@@ -424,6 +455,27 @@ xc_status encode_input_map(CUtensorMap* map, const void* in, const Geometry& g, 
   return XC_OK;
 }
 
+// 8-bit input [T][F][W bytes] for the small-array engine: boxes of one
+// channel group (128 / W channels) x 64 samples, zero-filled past F and T.
+xc_status encode_small_map(CUtensorMap* map, const void* in, const Geometry& g) {
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return record_error(XC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  const int m = small_tile_channels(g);
+  if (m == 0) return record_error(XC_ERR_UNSUPPORTED, "geometry not served by the small-array engine");
+  const cuuint64_t W = static_cast<cuuint64_t>(g.R);
+  const cuuint64_t dims[3] = {W, static_cast<cuuint64_t>(g.F), static_cast<cuuint64_t>(g.T)};
+  const cuuint64_t strides[2] = {W, W * static_cast<cuuint64_t>(g.F)};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(W), static_cast<cuuint32_t>(m), 64};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(in), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS)
+    return record_error(XC_ERR_CUDA, "cuTensorMapEncodeTiled (small-array input) failed (%d)",
+                        static_cast<int>(cr));
+  return XC_OK;
+}
+
 xc_status record_error(xc_status s, const char* fmt, ...) {
   t_status = s;
   if (s == XC_OK) {
@@ -477,6 +529,15 @@ xc_status xc_fp32_peak_probe(long long iterations, void* sink, void* stream, lon
 }
 
 int64_t xc_tri_index(int64_t bx, int64_t by) { return xc::tri_index(bx, by); }
+
+int xc_small_engine_channels(int nstation, int npol) {
+  if (nstation <= 0 || (npol != 1 && npol != 2) || nstation > 64) return 0;
+  xc::Geometry g{};
+  g.N = nstation;
+  g.P = npol;
+  g.R = 2 * nstation * npol;
+  return xc::small_tile_channels(g);
+}
 
 int xc_channels_packed(int nstation, int npol, int nfreq) {
   // The sizes xc_create accepts (npol 1 or 2; rows 2 P N within its limit).
@@ -669,8 +730,11 @@ xc_status xc_set_option(xc_handle* h, int key, long long value) {
       return succeed();
     }
     case XC_OPT_TILE:
-      if (value != XC_TILE_AUTO && value != XC_TILE_128 && value != XC_TILE_PAIR && value != XC_TILE_WIDE)
+      if (value != XC_TILE_AUTO && value != XC_TILE_128 && value != XC_TILE_PAIR && value != XC_TILE_WIDE &&
+          value != XC_TILE_SMALL)
         return fail(XC_ERR_INVALID_ARG, "unknown tile shape %lld", value);
+      if (value == XC_TILE_SMALL && h->batch)
+        return fail(XC_ERR_UNSUPPORTED, "batched launches run on the planar engine");
       if (h->batch) {
         h->batch->shape = value == XC_TILE_AUTO ? h->batch->shape_default
                                                 : planar_shape(static_cast<int>(value), h->pg, 0);

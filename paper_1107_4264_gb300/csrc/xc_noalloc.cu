@@ -11,9 +11,11 @@
 // static __device__ array, created with the library's device image and kept
 // by every GPU that loads the library until the process exits.
 //
-// The call runs the same planar tensor-core kernel as xc_correlate (same
-// tile shape, same operand formation and scaling, same exact chunks for 8-bit
-// input), so its visibilities are identical to xc_correlate's.  The scratch
+// The call runs the same tensor-core kernel as xc_correlate with default
+// options: the small-array engine for 8-bit input of the sizes it serves
+// (it needs no scratch), else the planar engine (same tile shape, same
+// operand formation and scaling, same exact chunks for 8-bit input), so its
+// visibilities are identical to xc_correlate's.  The planar scratch
 // holds, in order: the status word, the ring counters, the per-channel and
 // per-(channel, input) maxima of the scale pre-pass, and then as many
 // operand-ring channel slots as fit.  All work is queued on the caller's
@@ -115,6 +117,40 @@ extern "C" xc_status xc_correlate_noalloc(int nstation, int npol, int nfreq, int
   g.R = static_cast<int>(R);
   g.Tp = static_cast<int>(Tp);
   g.NB = static_cast<int64_t>(nstation) * (nstation + 1) / 2;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    (void)cudaGetLastError();
+    return record_error(XC_ERR_NO_DEVICE, "no usable current CUDA device");
+  }
+  DeviceSetup s;
+  const xc_status st0 = setup_device(dev, &s);
+  if (st0 != XC_OK) return st0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  // Small arrays with 8-bit input: the small-array engine, as xc_correlate
+  // runs them; it needs no scratch beyond the status word.
+  if (in_dtype == XC_CI8 && xc::small_tile_channels(g) > 0) {
+    xc::XeLaunch X;
+    X.g = g;
+    X.in = in;
+    X.in_dtype = 0;
+    X.out = out;
+    X.accumulate = 0;
+    X.grid = s.num_sms;
+    X.timeout_ns = 2000ull * 1000000ull;
+    X.status = status ? status : reinterpret_cast<int*>(s.scratch);
+    CUtensorMap in_map;
+    const xc_status se = xc::encode_small_map(&in_map, in, g);
+    if (se != XC_OK) return se;
+    const cudaError_t e = xc::launch_small(&in_map, X, st);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return record_error(XC_ERR_CUDA, "small-array tensor-core X-engine: %s", cudaGetErrorString(e));
+    }
+    return record_error(XC_OK, "");
+  }
+
   int pack = 1;
   const xc::Geometry pg = xc::planar_geometry(g, &pack);
   const int64_t n = static_cast<int64_t>(pg.N) * pg.P;
@@ -135,15 +171,6 @@ extern "C" xc_status xc_correlate_noalloc(int nstation, int npol, int nfreq, int
                         "%lld bytes of counters and scales",
                         XC_NOALLOC_SCRATCH_BYTES, static_cast<long long>(slot_bytes),
                         static_cast<long long>(off_ring));
-
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    (void)cudaGetLastError();
-    return record_error(XC_ERR_NO_DEVICE, "no usable current CUDA device");
-  }
-  DeviceSetup s;
-  const xc_status st0 = setup_device(dev, &s);
-  if (st0 != XC_OK) return st0;
 
   const int slots = static_cast<int>(
       std::min<int64_t>(xc::planar_ring_slots(pg, s.num_sms, XC_PREC_FP16), room / slot_bytes));
@@ -176,7 +203,6 @@ extern "C" xc_status xc_correlate_noalloc(int nstation, int npol, int nfreq, int
   // Kernel parameter block on the stack: nothing is allocated, host or device.
   xc::PlanarKernel k;
   const CUtensorMap* maps[1] = {im};
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = xc::planar_prepare(&X, maps, 1, &k, xc::planar_default_shape(pg, XC_PREC_FP16));
   if (e == cudaSuccess && k.grid > 0) e = xc::planar_setup(&X, 1, st);
   if (e == cudaSuccess) e = xc::planar_launch(k, st);

@@ -1,0 +1,498 @@
+// xc_small.cu -- tensor-core X-engine for small arrays: 8-bit input with
+// 2 N P in {16, 32, 64, 128} real rows per channel.
+//
+// The operation is Eq. (outer) of Sec. 2.1, V_f = sum_t x_f(t) x_f(t)^H per
+// channel, lower station triangle only (Sec. 4.2).  Sec. 4.4 computes whole
+// diagonal blocks and masks them; Sec. 6.1 raises F to keep a small array
+// busy; Sec. 8 leaves small N as future work.  On the planar engine a
+// 128 x 128 block holds 128 / n channels of n = N P inputs, and at most
+// n / 128 of each MMA pairs inputs of one channel.  This kernel instead
+// takes every input as two real rows (re, im: the interleaved order the
+// input already has) so that a 128-row operand tile holds m = 128 / (2 n)
+// channels at twice that density.  One 128 x 128 MMA per 16-sample step
+// (A = B = the tile) gives the real Gram matrix G = X X^T of the tile's
+// rows, with channel k's W x W block on the diagonal at rows and columns
+// k W .. k W + W - 1.  For inputs a, b with real rows (2a, 2a+1), (2b, 2b+1):
+//   Re V_ab = G[2a][2b] + G[2a+1][2b+1],  Im V_ab = G[2a+1][2b] - G[2a][2b+1].
+// The cross-channel blocks are computed and not read.  (One 128 x W MMA
+// per channel would skip them, but a tcgen05.mma costs about as long to
+// issue at N = 16 .. 64 as a 128 x 128 one takes to run, so m of them are
+// slower than the one full MMA.)
+//
+// No operand ring: a channel's operands are used by one CTA only, so each
+// CTA converts its 8-bit input straight into shared-memory operand tiles.
+// The kernel is then bound by the input stream from HBM (one read of
+// 2 n bytes per channel-sample) for every n it serves.
+//
+// Exactness (Sec. 5's 8-bit input): int8 samples are exact in fp16, their
+// products exact in fp32, and a fp32 sum of at most 1024 products of
+// magnitude <= 128^2 stays <= 2^24, so each 1024-sample chunk is exact in
+// fp32 and chunks add in int32.
+//
+// Roles of a persistent CTA (one per SM, 6 + kConvWarps warps):
+//   warp 0     TMA producer: [64 samples][m channels][2n bytes] int8 boxes;
+//   warp 1     TMEM owner and MMA issuer (one thread);
+//   warps 2-5  epilogue: TMEM -> V (int32) in the output layout;
+//   warps 6 .. converters: int8 box -> fp16 tile in the no-swizzle K-major
+//              canonical layout, whole stages in turn.
+// Work items are (channel group, segment of T); a CTA takes items in turn.
+// When there are too few channel groups to fill the GPU, T is split into
+// segments whose results are added to the (pre-zeroed) output with integer
+// atomics; integer addition is exact in any order.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "xc.h"
+#include "xc_internal.h"
+#include "xc_launch.h"
+#include "xc_ptx.cuh"
+
+namespace xc {
+namespace {
+
+constexpr int kRows = 128;                  // real rows per operand tile
+constexpr int kBK = 64;                     // samples per stage
+constexpr int kChunk = 1024;                // samples per exact fp32 chunk
+constexpr int kInStages = 10;               // int8 boxes (8 KiB) in flight
+constexpr int kOpStages = 8;                // fp16 operand tiles (16 KiB)
+constexpr int kInBytes = kRows * kBK;       // 8 KiB
+constexpr int kOpBytes = kRows * kBK * 2;   // 16 KiB
+constexpr uint32_t kCore = 128;             // one core matrix: 8 rows x 16 B
+constexpr uint32_t kSbo = (kBK / 8) * kCore;  // 1 KiB between 8-row groups
+constexpr int kConvWarp0 = 6;                // warps 0 .. 5: producer, MMA, epilogue
+constexpr int kConvWarps = 4;
+constexpr int kThreads = 32 * (kConvWarp0 + kConvWarps);
+constexpr uint32_t kTmemCols = 256;         // two accumulator buffers x 128 columns
+
+constexpr int kOpOff = 0;
+constexpr int kInOff = kOpOff + kOpStages * kOpBytes;
+constexpr int kBarOff = kInOff + kInStages * kInBytes;
+// in_full, in_empty per input stage; op_full, op_empty per operand stage;
+// accf, acce per accumulator buffer; one drain barrier.
+constexpr int kNumBars = 2 * kInStages + 2 * kOpStages + 5;
+constexpr int kMiscOff = kBarOff + kNumBars * 8;  // TMEM address, abort flag
+constexpr int kSmemBytes = kMiscOff + 16 + 1024;   // + slack to align the base to 1 KiB
+static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+struct SmallParams {
+  int N, P, F, T;
+  int ngroups;     // ceil(F / m)
+  int nseg;        // segments of T per channel group
+  int seg_len;     // samples per segment (a multiple of kChunk)
+  int64_t NB;      // baselines N (N + 1) / 2
+  int32_t* out;
+  int accumulate;  // add into out instead of overwriting it
+  int use_red;     // nseg > 1: every chunk is added with atomics (out pre-zeroed)
+  unsigned long long timeout_ns;
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t bar_in_full(uint32_t b, int s) { return b + 8u * s; }
+__device__ __forceinline__ uint32_t bar_in_empty(uint32_t b, int s) { return b + 8u * (kInStages + s); }
+__device__ __forceinline__ uint32_t bar_op_full(uint32_t b, int s) { return b + 8u * (2 * kInStages + s); }
+__device__ __forceinline__ uint32_t bar_op_empty(uint32_t b, int s) {
+  return b + 8u * (2 * kInStages + kOpStages + s);
+}
+__device__ __forceinline__ uint32_t bar_accf(uint32_t b, int ab) {
+  return b + 8u * (2 * kInStages + 2 * kOpStages + ab);
+}
+__device__ __forceinline__ uint32_t bar_acce(uint32_t b, int ab) {
+  return b + 8u * (2 * kInStages + 2 * kOpStages + 2 + ab);
+}
+__device__ __forceinline__ uint32_t bar_drain(uint32_t b) {
+  return b + 8u * (2 * kInStages + 2 * kOpStages + 4);
+}
+
+// Samples [t0, t1) of work item `it` (channel group it / nseg).
+struct Item {
+  int g, t0, t1;
+};
+__device__ __forceinline__ Item item_of(const SmallParams& p, int it) {
+  Item x;
+  x.g = it / p.nseg;
+  const int sg = it % p.nseg;
+  x.t0 = sg * p.seg_len;
+  x.t1 = min(p.T, x.t0 + p.seg_len);
+  return x;
+}
+
+// fp16x2 of (byte j of a, byte j of b) as signed 8-bit values: with byte x
+// placed under the fp16 pattern 0x6400 (1024) after flipping its sign bit,
+// the half is 1152 + x, and subtracting 1152 leaves x exactly.  The selector
+// j may differ between lanes.
+__device__ __forceinline__ uint32_t i8pair_to_h2(uint32_t a, uint32_t b, uint32_t j) {
+  uint32_t d = __byte_perm(a, b, j | ((j + 4u) << 8));
+  d = (d & 0x00FF00FFu) ^ 0x64806480u;
+  __half2 h = *reinterpret_cast<__half2*>(&d);
+  h = __hsub2(h, __half2(__float2half_rn(1152.f), __float2half_rn(1152.f)));
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+               : "memory");
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// Bounded wait of a whole warp (every lane polls; all give up together).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, const ptx::WaitCtl& wc) {
+  const bool got = ptx::wait_bounded(bar, parity, wc);
+  return __all_sync(0xffffffffu, got);
+}
+
+// One visibility (int32 re, im; 8-byte aligned): stored (mode 0), read-
+// modified-written (mode 1: later chunks of a segment, or accumulate) or
+// added with atomics (mode 2: T split into segments).
+__device__ __forceinline__ void put_vis(int32_t* dst, int re, int im, int mode) {
+  int2* d2 = reinterpret_cast<int2*>(dst);
+  if (mode == 0) {
+    *d2 = make_int2(re, im);
+  } else if (mode == 1) {
+    int2 v = *d2;
+    v.x += re;
+    v.y += im;
+    *d2 = v;
+  } else {
+    atomicAdd(dst, re);
+    atomicAdd(dst + 1, im);
+  }
+}
+
+// W = 2 N P real rows per channel; the tile holds kRows / W channels.
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1)
+    small_kernel(const __grid_constant__ CUtensorMap in_map, const SmallParams p) {
+  static_assert(W == 16 || W == 32 || W == 64 || W == 128, "a channel's rows divide the tile");
+  constexpr int kM = kRows / W;
+  constexpr int kPieces = W >= 32 ? W / 32 : 1;  // 32-column TMEM loads per channel block
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = ptx::smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  unsigned char* sgen = smem_raw + (sbase - raw);
+  const uint32_t bars = sbase + kBarOff;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sgen + kMiscOff);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sgen + kMiscOff + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = p.ngroups * p.nseg;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kInStages; ++s) {
+      ptx::mbar_init(bar_in_full(bars, s), 1);
+      ptx::mbar_init(bar_in_empty(bars, s), 1);
+    }
+    for (int s = 0; s < kOpStages; ++s) {
+      ptx::mbar_init(bar_op_full(bars, s), 1);
+      ptx::mbar_init(bar_op_empty(bars, s), 1);
+    }
+    for (int ab = 0; ab < 2; ++ab) {
+      ptx::mbar_init(bar_accf(bars, ab), 1);
+      ptx::mbar_init(bar_acce(bars, ab), 4);
+    }
+    ptx::mbar_init(bar_drain(bars), 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), kTmemCols);
+    ptx::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) ptx::prefetch_tmap(&in_map);
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const ptx::WaitCtl wc{p.timeout_ns, p.status, abort_flag};
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- producer
+    if (lane == 0) {
+      const uint64_t pol = ptx::l2_policy_evict_first();  // the input streams through once
+      int si = 0;
+      uint32_t ph = 0;
+      long long issued = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; ok && it < items; it += gridDim.x) {
+        const Item x = item_of(p, it);
+        for (int t = x.t0; t < x.t1; t += kBK) {
+          if (!ptx::wait_bounded(bar_in_empty(bars, si), ph ^ 1u, wc)) {
+            ok = false;
+            break;
+          }
+          // Past F or T the box is zero-filled; the transaction count is the whole box.
+          ptx::mbar_arrive_expect_tx(bar_in_full(bars, si), kInBytes);
+          ptx::tma_load_3d_hint(sbase + kInOff + si * kInBytes, &in_map, bar_in_full(bars, si), 0,
+                                x.g * kM, t, pol);
+          ++issued;
+          if (++si == kInStages) {
+            si = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      // No box may still be landing when the CTA exits (converters that gave
+      // up no longer wait for them): wait, bounded, for the last box of every
+      // stage.  Issue k used phase k / kInStages of stage k % kInStages.
+      for (long long k = max(0LL, issued - kInStages); k < issued; ++k) {
+        const int s = static_cast<int>(k % kInStages);
+        const uint32_t par = static_cast<uint32_t>((k / kInStages) & 1);
+        const uint64_t t0 = ptx::globaltimer();
+        while (!ptx::mbar_try_wait(bar_in_full(bars, s), par) && ptx::globaltimer() - t0 < p.timeout_ns) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_f16_f32(kRows, kRows);
+      int so = 0, ab = 0;
+      uint32_t oph = 0;
+      uint32_t usep = 0;  // bit ab: parity of buffer ab's use count
+      bool ok = true;
+      for (int it = blockIdx.x; ok && it < items; it += gridDim.x) {
+        const Item x = item_of(p, it);
+        for (int c0 = x.t0; ok && c0 < x.t1; c0 += kChunk) {
+          const int c1 = min(x.t1, c0 + kChunk);
+          // The epilogue has read this buffer's previous chunk.
+          if (!ptx::wait_bounded(bar_acce(bars, ab), ((usep >> ab) & 1u) ^ 1u, wc)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          for (int t = c0; t < c1; t += kBK) {
+            if (!ptx::wait_bounded(bar_op_full(bars, so), oph, wc)) {
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t tile = sbase + kOpOff + so * kOpBytes;
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              // A and B: all 128 rows (K step kk = chunks 2kk, 2kk + 1).  D
+              // holds every channel's block on its diagonal; the epilogue
+              // reads only those.
+              const uint64_t d = ptx::interleave_kmajor_desc(tile + kk * 2 * kCore, kCore, kSbo);
+              ptx::mma_f16_ss(tmem + static_cast<uint32_t>(ab * 128), d, d, idesc,
+                              (t > c0 || kk > 0) ? 1u : 0u);
+            }
+            ptx::mma_commit(bar_op_empty(bars, so));  // the tile may be refilled once read
+            if (++so == kOpStages) {
+              so = 0;
+              oph ^= 1u;
+            }
+          }
+          if (!ok) break;
+          ptx::mma_commit(bar_accf(bars, ab));
+          usep ^= 1u << ab;
+          ab ^= 1;
+        }
+      }
+      // Every MMA issued completes before TMEM is freed and the CTA exits.
+      ptx::mma_commit(bar_drain(bars));
+      const uint64_t t0 = ptx::globaltimer();
+      while (!ptx::mbar_try_wait(bar_drain(bars), 0u) && ptx::globaltimer() - t0 < p.timeout_ns) {
+      }
+    }
+  } else if (warp < kConvWarp0) {  // warps 2 .. 5
+    // --------------------------------------------------------- epilogue
+    // Warp w reads TMEM lanes 32 (w % 4) ..: tile row r is TMEM lane r.
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    const int k = r / W;           // channel of row r within the tile
+    const int a = (r % W) >> 1;    // input of the row (station a / P, polarisation a % P)
+    const int c = r & 1;           // 0: the row holds re(x_a), 1: im(x_a)
+    const int s1 = a / p.P, p1 = a % p.P;
+    const int PP = p.P * p.P;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
+    int ab = 0;
+    uint32_t usep = 0;  // bit ab: parity of buffer ab's use count
+    bool ok = true;
+    for (int it = blockIdx.x; ok && it < items; it += gridDim.x) {
+      const Item x = item_of(p, it);
+      const int ch = x.g * kM + k;
+      const bool chan_ok = ch < p.F;
+      int32_t* obase = p.out + static_cast<int64_t>(ch) * p.NB * PP * 2;
+      for (int c0 = x.t0; c0 < x.t1; c0 += kChunk) {
+        if (!warp_wait(bar_accf(bars, ab), (usep >> ab) & 1u, wc)) {
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const int mode = p.use_red ? 2 : ((c0 == x.t0 && !p.accumulate) ? 0 : 1);
+#pragma unroll 1
+        for (int pc = 0; pc < kPieces; ++pc) {
+          uint32_t v[32];
+          // Channel k's G columns; with W = 16 the piece holds the warp's two channels.
+          const uint32_t col = static_cast<uint32_t>(ab * 128 + (W >= 32 ? k * W + 32 * pc : 32 * q));
+          ptx::tmem_ld_32x32b_x32(lane_base + col, v);
+          ptx::tmem_wait_ld();
+          if (pc == kPieces - 1) {  // the buffer is free for the next chunk's MMAs
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(bar_acce(bars, ab));
+          }
+          constexpr int kJ = W >= 32 ? 8 : 4;  // input pairs (2j, 2j + 1) in the piece
+          const bool hi = W == 16 && lane >= 16;
+#pragma unroll
+          for (int jj = 0; jj < kJ; ++jj) {
+            // Columns 4j .. 4j+3 of the channel block: G[row][2b], G[row][2b+1]
+            // for b = 2j (d0, d1) and b = 2j + 1 (d2, d3).
+            const float d0 = __uint_as_float(hi ? v[16 + 4 * jj] : v[4 * jj]);
+            const float d1 = __uint_as_float(hi ? v[16 + 4 * jj + 1] : v[4 * jj + 1]);
+            const float d2 = __uint_as_float(hi ? v[16 + 4 * jj + 2] : v[4 * jj + 2]);
+            const float d3 = __uint_as_float(hi ? v[16 + 4 * jj + 3] : v[4 * jj + 3]);
+            // This lane produces V(a, b) for b = 2j + c; the partner row (lane ^ 1,
+            // same input, other component) sends its two columns for that b.
+            const float keep0 = c ? d2 : d0, keep1 = c ? d3 : d1;
+            const float send0 = c ? d0 : d2, send1 = c ? d1 : d3;
+            const float got0 = __shfl_xor_sync(0xffffffffu, send0, 1);
+            const float got1 = __shfl_xor_sync(0xffffffffu, send1, 1);
+            const int o0 = __float2int_rn(keep0), o1 = __float2int_rn(keep1);
+            const int g0 = __float2int_rn(got0), g1 = __float2int_rn(got1);
+            // c = 0: own (rr, ri), partner (ir, ii); c = 1: own (ir, ii), partner (rr, ri).
+            const int re = c ? g0 + o1 : o0 + g1;
+            const int im = c ? o0 - g1 : g0 - o1;
+            const int b = 2 * ((W >= 32 ? 8 * pc : 0) + jj) + c;
+            const int s2 = b / p.P, p2 = b % p.P;
+            if (chan_ok && s2 <= s1)
+              put_vis(obase + ((static_cast<int64_t>(s1) * (s1 + 1) / 2 + s2) * PP + p1 * p.P + p2) * 2,
+                      re, im, mode);
+          }
+        }
+        usep ^= 1u << ab;
+        ab ^= 1;
+      }
+    }
+  } else {
+    // ------------------------------------------------------- converters
+    // The CTA's stages (its items in turn, 64 samples each) are numbered
+    // k = 0, 1, ...; converter warp cw takes k = cw, cw + kConvWarps, ...
+    // whole, so kConvWarps stages are converted at once and each warp's
+    // latency overlaps the others'.  Stage k uses input slot k % kInStages and operand slot
+    // k % kOpStages, in phase k / (slot count).  The box ([64 samples][128
+    // bytes]: byte r of a sample is tile row r) becomes the fp16 tile: lane
+    // l reads byte word l (rows 4l .. 4l+3) of each sample and writes one
+    // 16-byte core-matrix row per tile row and 8-sample chunk.  Step s
+    // writes row 4l + ((s + l / 2) mod 4), so the 8 lanes of each
+    // quarter-warp cover the 8 rows of a core matrix, one shared-memory bank
+    // group each: the 16-byte stores do not conflict.
+    const int cw = warp - kConvWarp0;
+    uint32_t jsel[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) jsel[s] = static_cast<uint32_t>((s + (lane >> 1)) & 3);
+    // Cursor over the CTA's stages: item `it`, its samples [x.t0, x.t1), stage start t.
+    int it = blockIdx.x;
+    Item x = item_of(p, it < items ? it : 0);
+    int t = x.t0;
+    auto advance = [&]() {
+      t += kBK;
+      if (t >= x.t1) {
+        it += gridDim.x;
+        if (it < items) {
+          x = item_of(p, it);
+          t = x.t0;
+        }
+      }
+    };
+    for (int s = 0; s < cw && it < items; ++s) advance();
+    for (long long k = cw; it < items; k += kConvWarps) {
+      const int si = static_cast<int>(k % kInStages), so = static_cast<int>(k % kOpStages);
+      const uint32_t iph = static_cast<uint32_t>((k / kInStages) & 1);
+      const uint32_t oph = static_cast<uint32_t>((k / kOpStages) & 1);
+      if (!warp_wait(bar_in_full(bars, si), iph, wc) || !warp_wait(bar_op_empty(bars, so), oph ^ 1u, wc))
+        break;
+      const uint32_t src = sbase + kInOff + si * kInBytes + 4u * lane;
+      const uint32_t dst = sbase + kOpOff + so * kOpBytes;
+#pragma unroll 2
+      for (int cc = 0; cc < kBK / 8; ++cc) {
+        uint32_t w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) w[u] = lds32(src + static_cast<uint32_t>((8 * cc + u) * kRows));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t j = jsel[q];
+          const uint32_t row = 4u * lane + j;
+          sts128(dst + (row >> 3) * kSbo + cc * kCore + (row & 7u) * 16u, i8pair_to_h2(w[0], w[1], j),
+                 i8pair_to_h2(w[2], w[3], j), i8pair_to_h2(w[4], w[5], j), i8pair_to_h2(w[6], w[7], j));
+        }
+      }
+      // The tile's generic stores before the tensor core's reads; the box's
+      // reads are complete (their values were stored).
+      ptx::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        ptx::mbar_arrive(bar_in_empty(bars, si));
+        ptx::mbar_arrive(bar_op_full(bars, so));
+      }
+      for (int s = 0; s < kConvWarps && it < items; ++s) advance();
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+template <int W>
+cudaError_t launch_w(const CUtensorMap* map, const SmallParams& p, int grid, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(small_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  small_kernel<W><<<grid, kThreads, kSmemBytes, s>>>(*map, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int small_tile_channels(const Geometry& g) {
+  const int W = 2 * g.N * g.P;
+  return (W == 16 || W == 32 || W == 64 || W == 128) ? kRows / W : 0;
+}
+
+cudaError_t launch_small(const CUtensorMap* in_map, const XeLaunch& X, cudaStream_t s) {
+  const Geometry& g = X.g;
+  const int m = small_tile_channels(g);
+  if (m == 0 || X.in_dtype != 0 || !in_map) return cudaErrorInvalidValue;
+  SmallParams p;
+  p.N = g.N;
+  p.P = g.P;
+  p.F = g.F;
+  p.T = g.T;
+  p.NB = g.NB;
+  p.ngroups = (g.F + m - 1) / m;
+  // Split T only when the channel groups alone leave SMs idle.
+  const int nchunks = (g.T + kChunk - 1) / kChunk;
+  int nseg = 1;
+  if (p.ngroups < 2 * X.grid) nseg = std::min(nchunks, (2 * X.grid + p.ngroups - 1) / p.ngroups);
+  p.seg_len = (nchunks + nseg - 1) / nseg * kChunk;
+  p.nseg = (g.T + p.seg_len - 1) / p.seg_len;
+  p.out = static_cast<int32_t*>(X.out);
+  p.accumulate = X.accumulate;
+  p.use_red = p.nseg > 1 ? 1 : 0;
+  p.timeout_ns = X.timeout_ns;
+  p.status = X.status;
+  if (p.use_red && !X.accumulate) {
+    const size_t bytes = static_cast<size_t>(g.F) * static_cast<size_t>(g.NB) * g.P * g.P * 8;
+    const cudaError_t e = cudaMemsetAsync(X.out, 0, bytes, s);
+    if (e != cudaSuccess) return e;
+  }
+  const int items = p.ngroups * p.nseg;
+  const int grid = std::max(1, std::min(X.grid, items));
+  switch (2 * g.N * g.P) {
+    case 16: return launch_w<16>(in_map, p, grid, s);
+    case 32: return launch_w<32>(in_map, p, grid, s);
+    case 64: return launch_w<64>(in_map, p, grid, s);
+    default: return launch_w<128>(in_map, p, grid, s);
+  }
+}
+
+}  // namespace xc

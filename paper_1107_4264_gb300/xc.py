@@ -27,7 +27,7 @@ XC_ERR_OOM = 7
 XC_ERR_NO_DEVICE = 8
 XC_OPT_ENGINE, XC_OPT_ACCUMULATE, XC_OPT_TIMEOUT_MS, XC_OPT_PROFILE = 1, 2, 3, 4
 XC_OPT_PRECISION, XC_OPT_FP64_BLOCK, XC_OPT_TILE = 5, 6, 7
-XC_TILE_AUTO, XC_TILE_128, XC_TILE_PAIR, XC_TILE_WIDE = 0, 1, 2, 3
+XC_TILE_AUTO, XC_TILE_128, XC_TILE_PAIR, XC_TILE_WIDE, XC_TILE_SMALL = 0, 1, 2, 3, 4
 XC_OPT_TEST_NO_PUBLISH = 100
 XC_PREC_FP16, XC_PREC_HILO, XC_PREC_FP8 = 0, 1, 2
 (XC_ENGINE_TENSOR, XC_ENGINE_FP32, XC_ENGINE_TENSOR_2PASS, XC_ENGINE_TENSOR_1CTA,
@@ -43,7 +43,7 @@ EXPORTS = [
     "xc_correlate_stream", "xc_input_bytes", "xc_output_bytes", "xc_tri_index", "xc_tri_coords",
     "xc_version", "xc_kernel_times", "xc_correlate_noalloc", "xc_set_gains", "xc_get_grad_gains",
     "xc_batch_create", "xc_batch_correlate", "xc_batch_tune", "xc_channelize",
-    "xc_channelize_pfb", "xc_channels_packed", "xc_fp32_peak_probe", "xc_batch_set_cache",
+    "xc_channelize_pfb", "xc_channels_packed", "xc_small_engine_channels", "xc_fp32_peak_probe", "xc_batch_set_cache",
     "xc_batch_cache_key", "xc_batch_cache_lookup",
 ]
 
@@ -87,6 +87,7 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "xc_channelize": ([vp, i32, i32, i32, i32, i32, ctypes.c_float, vp, i32, vp], i32),
         "xc_channelize_pfb": ([vp, i32, i32, i32, i32, i32, vp, i32, ctypes.c_float, vp, i32, vp], i32),
         "xc_channels_packed": ([i32, i32, i32], i32),
+        "xc_small_engine_channels": ([i32, i32], i32),
         "xc_fp32_peak_probe": ([ctypes.c_longlong, vp, vp, ctypes.POINTER(ctypes.c_longlong)], i32),
         "xc_batch_set_cache": ([vp, ctypes.c_char_p], i32),
         "xc_batch_cache_key": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), i32, i32,

@@ -131,6 +131,18 @@ def test_channels_packed_rule(lib):
     assert lib.xc_channels_packed(2 ** 31 - 1, 2, 8) == 0  # 2 P N would overflow int
 
 
+def test_small_engine_channels_rule(lib):
+    """The small-array engine's reach: 128 / W channels per tile for
+    W = 2 N P in {16, 32, 64, 128}, else 0 (restated from its documentation)."""
+    for N in range(0, 80):
+        for P in (-1, 0, 1, 2, 3):
+            W = 2 * N * P
+            want = 128 // W if P in (1, 2) and W in (16, 32, 64, 128) else 0
+            assert lib.xc_small_engine_channels(N, P) == want, (N, P)
+    assert lib.xc_small_engine_channels(16, 2) == 2
+    assert lib.xc_small_engine_channels(2 ** 31 - 1, 2) == 0
+
+
 def test_tri_map_round_trip_exhaustive(lib):
     # every block of the lower triangle up to 4000 block rows (8e6 blocks)
     n = 4000

@@ -54,7 +54,9 @@ INT_CASES = [(16, 2, 12, 300), (10, 2, 12, 130), (7, 1, 10, 200), (5, 2, 7, 64),
                          ids=["N%d_P%d_F%d_T%d_k%d" % (c + (pack_of(c[0], c[1], c[2]),)) for c in INT_CASES])
 def test_packed_int8_bit_exact(N, P, F, T, dev):
     x = synth.uniform_int8((T, F, N, P, 2), -128, 127, 900 + N * F + T)
-    eng = xc.Correlator(N, P, F, T, "int8")
+    # XC_TILE_128: sizes the small-array engine serves would leave the planar
+    # engine (and its packing) under XC_TILE_AUTO.
+    eng = xc.Correlator(N, P, F, T, "int8", tile=xc.XC_TILE_128)
     try:
         got = eng.correlate(x.to(dev), sync=True).cpu().numpy()
     finally:
@@ -66,7 +68,7 @@ def test_packed_int8_accumulate(dev):
     N, P, F, T = 12, 2, 20, 256  # n = 24: pack 5
     xa = synth.uniform_int8((T, F, N, P, 2), -128, 127, 911)
     xb = synth.uniform_int8((T, F, N, P, 2), -128, 127, 912)
-    eng = xc.Correlator(N, P, F, T, "int8", accumulate=True)
+    eng = xc.Correlator(N, P, F, T, "int8", accumulate=True, tile=xc.XC_TILE_128)
     try:
         out = eng.new_output()
         out.zero_()
