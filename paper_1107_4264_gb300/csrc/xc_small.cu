@@ -65,7 +65,7 @@ constexpr int kOpBytes = kRows * kBK * 2;   // 16 KiB
 constexpr uint32_t kCore = 128;             // one core matrix: 8 rows x 16 B
 constexpr uint32_t kSbo = (kBK / 8) * kCore;  // 1 KiB between 8-row groups
 constexpr int kConvWarp0 = 6;                // warps 0 .. 5: producer, MMA, epilogue
-constexpr int kConvWarps = 4;
+constexpr int kConvWarps = 6;
 constexpr int kThreads = 32 * (kConvWarp0 + kConvWarps);
 constexpr uint32_t kTmemCols = 256;         // two accumulator buffers x 128 columns
 
