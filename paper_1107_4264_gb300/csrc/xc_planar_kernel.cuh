@@ -1056,7 +1056,8 @@ __device__ __forceinline__ void store_piece(const uint32_t (&re)[32], const uint
         rec[4 + k] = p1 ? B[k] : got;
       }
       const int s2 = s2_0 + 2 * m + p1;
-      if (valid && s2 >= 0 && s2 <= s1) ptx::st_global_v8(o8 + 8 * static_cast<int64_t>(s2), rec);
+      if (valid && s2 >= 0 && s2 <= s1)
+        ptx::st_global_v8_hint(o8 + 8 * static_cast<int64_t>(s2), rec, ptx::l2_policy_evict_first());
     }
   } else if (g.P == 2) {
     const int p1 = a & 1;
@@ -1233,7 +1234,7 @@ __device__ __forceinline__ void store_piece_f64(const uint32_t (&re)[32], const 
             rec[2 * k] = __float_as_uint(static_cast<float>(v[k].x));
             rec[2 * k + 1] = __float_as_uint(static_cast<float>(v[k].y));
           }
-          ptx::st_global_v8(out + (krow + s2) * 4, rec);
+          ptx::st_global_v8_hint(out + (krow + s2) * 4, rec, ptx::l2_policy_evict_first());
         }
       }
     }
@@ -1319,7 +1320,8 @@ __device__ __forceinline__ void store_piece_tr(const uint32_t (&re)[32], const u
       if (row_ok && sb < g.N) {
         const int64_t rec_idx =
             static_cast<int64_t>(f) * p.NBr + static_cast<int64_t>(sb) * (sb + 1) / 2 + sa;
-        ptx::st_global_v8(reinterpret_cast<uint32_t*>(out) + rec_idx * 8, rec);
+        ptx::st_global_v8_hint(reinterpret_cast<uint32_t*>(out) + rec_idx * 8, rec,
+                               ptx::l2_policy_evict_first());
       }
     }
     return;

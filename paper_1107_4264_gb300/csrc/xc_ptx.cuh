@@ -93,8 +93,9 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, uint
 }
 
 // L2 cache policies (createpolicy) for streamed data: evict_first lines are
-// the first candidates for replacement, so data read or written once does
-// not push longer-lived data (the operand ring) out of L2.
+// the first candidates for replacement, so data read or written once (the
+// input, the visibilities) does not push longer-lived data (the operand
+// ring) out of L2.
 __device__ __forceinline__ uint64_t l2_policy_evict_first() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
