@@ -58,8 +58,8 @@ namespace {
 constexpr int kRows = 128;                  // real rows per operand tile
 constexpr int kBK = 64;                     // samples per stage
 constexpr int kChunk = 1024;                // samples per exact fp32 chunk
-constexpr int kInStages = 10;               // int8 boxes (8 KiB) in flight
-constexpr int kOpStages = 8;                // fp16 operand tiles (16 KiB)
+constexpr int kInStages = 12;               // int8 boxes (8 KiB) in flight
+constexpr int kOpStages = 6;                // fp16 operand tiles (16 KiB)
 constexpr int kInBytes = kRows * kBK;       // 8 KiB
 constexpr int kOpBytes = kRows * kBK * 2;   // 16 KiB
 constexpr uint32_t kCore = 128;             // one core matrix: 8 rows x 16 B
@@ -67,6 +67,13 @@ constexpr uint32_t kSbo = (kBK / 8) * kCore;  // 1 KiB between 8-row groups
 constexpr int kConvWarp0 = 6;                // warps 0 .. 5: producer, MMA, epilogue
 constexpr int kConvWarps = 6;
 constexpr int kThreads = 32 * (kConvWarp0 + kConvWarps);
+// Converter warp cw takes stages cw, cw + kConvWarps, ...; with slot counts
+// that are multiples of kConvWarps every input and operand slot belongs to
+// one warp, which waits on its barriers phase by phase.  (A slot shared by
+// two warps lets one of them wait on a parity two phases old, which passes
+// too early: mbarrier waits test parity, not a phase count.)
+static_assert(kInStages % kConvWarps == 0 && kOpStages % kConvWarps == 0,
+              "each converter warp owns its input and operand slots");
 constexpr uint32_t kTmemCols = 256;         // two accumulator buffers x 128 columns
 
 constexpr int kOpOff = 0;
