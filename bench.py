@@ -80,6 +80,12 @@ def parse_args():
                     help="blocks (samples per stream / 1024) for --fengine (smaller for profiling)")
     ap.add_argument("--tile", choices=["auto", "128", "pair", "wide"], default="auto",
                     help="tile shape of the tensor-core engine (default: the library's choice)")
+    ap.add_argument("--smalln", type=int, default=0,
+                    help="time the small-array engine and the packed planar engine at this N "
+                         "(P=2, T=1000, F from --nfreq or the N sweep's choice) and exit")
+    ap.add_argument("--fp8-4bit", action="store_true",
+                    help="time the Large-N geometry with samples clipped to +-7 on the FP8 path "
+                         "(F from --nfreq) and exit")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the bench line: kernel TOPS over N (fixed work) and over T at "
                          "fixed F*T (output traffic), one JSON object")
@@ -270,15 +276,15 @@ def frob_and_maxnorm(got, want, N, P):
 
 def peak_of(peaks, measured, kind, long_region):
     """Peak in TFLOP/s for a tensor path of `kind` ("fp16" or "fp8"): the
-    burst (or, for a timed region over a second, sustained) rate measured in
-    this run, else the measured bf16 figure times the nominal ratio."""
-    m = measured.get("%s_dense_tflops" % ("fp8_e4m3" if kind == "fp8" else "fp16"), {})
-    key = "sustained" if long_region else "burst"
-    if key in m:
-        return m[key], "measured %s dense %s (%s, this run)" % (kind, key, m.get("how"))
+    pool's measured dense bf16 figure (MEASURED_PEAKS.json; burst, or for a
+    timed region over a second the sustained one) times the nominal
+    kind/bf16 ratio (1 for fp16, 2 for fp8).  The same kind's own rate
+    measured in this run is returned beside it, as context."""
     ratio = 2.0 if kind == "fp8" else 1.0
+    key = "sustained" if long_region else "burst"
     base = peaks["bf16_tflops_sustained" if long_region else "bf16_tflops"]
-    return base * ratio, "bf16 %s x nominal %s/bf16 ratio %.0f" % (key, kind, ratio)
+    m = measured.get("%s_dense_tflops" % ("fp8_e4m3" if kind == "fp8" else "fp16"), {})
+    return base * ratio, "bf16 %s of MEASURED_PEAKS.json x nominal %s/bf16 ratio %.0f" % (key, kind, ratio), m.get(key)
 
 
 # ------------------------------------------------------------- multi-rank
@@ -479,14 +485,14 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks, measured):
         (_, kms), (_, nk) = eng.kernel_times(reset=True)
         kms /= max(nk, 1)
         ex = executed_planar(w, steps)
-        peak, peak_src = peak_of(peaks, measured, "fp8" if peak_ratio == 2.0 else "fp16", False)
+        peak, peak_src, peak_run = peak_of(peaks, measured, "fp8" if peak_ratio == 2.0 else "fp16", False)
         samples["outs"][name] = out[err_chans].double().cpu().numpy()
         prec[name] = {"tops": w.useful_ops / (ms * 1e-3) / 1e12, "ms": ms,
                       "fp64_block": blk,
                       "kernel_ms_incl_scale_pass": kms,
                       "executed_tflops": ex / (kms * 1e-3) / 1e12,
                       "frac_of_peak": ex / (kms * 1e-3) / 1e12 / peak,
-                      "peak": peak, "peak_source": peak_src}
+                      "peak": peak, "peak_source": peak_src, "peak_measured_this_run": peak_run}
         if blk:
             prec[name]["note"] = ("fp32 blocks of %d samples summed in float64 in device memory "
                                   "(long-integration mode; 2 drains per 2048-sample integration)" % blk)
@@ -518,6 +524,7 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks, measured):
         "executed_tflops": ex / (kms * 1e-3) / 1e12,
         "frac_of_peak": ex / (kms * 1e-3) / 1e12 / peak_of(peaks, measured, "fp8", False)[0],
         "peak": peak_of(peaks, measured, "fp8", False)[0], "peak_source": peak_of(peaks, measured, "fp8", False)[1],
+        "peak_measured_this_run": peak_of(peaks, measured, "fp8", False)[2],
         "exact": "bit-exact vs the int64 oracle: tests/test_fp8_int8_gpu.py"}
     eng.close()
     del x4, out
@@ -618,6 +625,38 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks, measured):
                              "backward_ms": bms, "backward_ops": bwd_ops,
                              "backward_arithmetic": "tcgen05 complex GEMM (H_f diag(g)) x, fp16 hi/lo operands, fp32 accumulation"}
     eng.close()
+    del x, out, go, gx
+
+    # Small arrays (Sec. 6.1's small-N regime) at the N sweep's sizes, T = 1000:
+    # the small-array engine (XC_TILE_AUTO picks it) against the planar
+    # engine's packed channels (XC_TILE_128) on the same int8 sky data.  The
+    # small engine is bound by its single input read: in_gbs is that stream.
+    small = {}
+    for N, F in ((8, 65528), (16, 65528), (32, 65104)):
+        T = 1000
+        xs = synth.sky_voltages(T, F, N, 2, noise_sigma=3.0, nsrc=3, src_amp=1.5, seed=4242 + N + T,
+                                device=dev, quantise_int8=True)
+        useful = 8 * F * T * 4 * N * (N + 1) // 2
+        entry = {"F": F, "T": T, "useful_ops": useful}
+        for name, tile in (("small_engine", xc.XC_TILE_AUTO), ("planar_packed", xc.XC_TILE_128)):
+            eng = xc.Correlator(N, 2, F, T, "int8", tile=tile)
+            out = eng.new_output()
+            eng.correlate(xs, out=out, stream=stream)
+            eng.synchronize(stream)
+            eng.set_option(xc.XC_OPT_PROFILE, 1)
+            ms = timed(lambda: eng.correlate(xs, out=out, stream=stream), k) / k
+            eng.synchronize(stream)
+            (_, kms), (_, nk) = eng.kernel_times(reset=True)
+            kms /= max(nk, 1)
+            in_gbs = T * F * N * 4 / (kms * 1e-3) / 1e9
+            entry[name] = {"tops": useful / (ms * 1e-3) / 1e12, "ms": ms, "kernel_ms": kms,
+                           "in_gbs": in_gbs, "in_frac_of_hbm": in_gbs / peaks["hbm_gbs"]}
+            eng.close()
+            del out
+        small["N=%d" % N] = entry
+        del xs
+    res["small_n"] = {"workload": "int8 sky data, P=2, T=1000, F sized as in the N sweep", "points": small,
+                      "engine": "small_kernel<W> (W = 2 N P real rows per channel); planar_kernel for comparison"}
     return res
 
 
@@ -675,6 +714,58 @@ def run_sweep(args):
         by_t.append(measure(256, 1024000 // T, T))
     print(json.dumps({"sweep": "small_kernel / planar_kernel <int8>, GB300, 1 GPU", "by_nstation": by_n,
                       "by_ntime_fixed_FT": by_t}))
+    return 0
+
+
+def run_single(args):
+    """One engine on one workload, kernel time from live CUDA events (used
+    for the profiles' ncu captures of the small-array and FP8 kernels)."""
+    import torch
+
+    from paper_1107_4264_gb300 import build as engine_build
+    from paper_1107_4264_gb300 import synth, xc
+
+    engine_build.build()
+    xc.load()
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream(dev)
+    runs = []
+    if args.smalln:
+        N, T = args.smalln, 1000
+        F = args.nfreq or max(8, min(65528, int(round(1.1e12 / (8 * T * 4 * N * (N + 1) / 2))) // 8 * 8))
+        x = synth.sky_voltages(T, F, N, 2, noise_sigma=3.0, nsrc=3, src_amp=1.5, seed=4242 + N + T,
+                               device=dev, quantise_int8=True)
+        useful = 8 * F * T * 4 * N * (N + 1) // 2
+        for name, tile, prec in (("small_engine", xc.XC_TILE_AUTO, xc.XC_PREC_FP16),
+                                 ("planar_packed", xc.XC_TILE_128, xc.XC_PREC_FP16)):
+            runs.append((name, xc.Correlator(N, 2, F, T, "int8", tile=tile, precision=prec), x, useful))
+        what = {"N": N, "P": 2, "F": F, "T": T}
+    else:
+        w = synth.LARGE_N
+        if args.nfreq:
+            w = synth.Workload(w.name, w.nstation, w.npol, args.nfreq, w.ntime, w.seed)
+        x = synth.large_n_input(w, 0, device=dev).clamp_(-7, 7)
+        runs.append(("fp8_4bit", xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "int8",
+                                               precision=xc.XC_PREC_FP8), x, w.useful_ops))
+        runs.append(("fp16", xc.Correlator(w.nstation, w.npol, w.nfreq, w.ntime, "int8"), x, w.useful_ops))
+        what = {"N": w.nstation, "P": w.npol, "F": w.nfreq, "T": w.ntime, "samples": "clipped to +-7"}
+    res = {"mode": "single", "workload": what}
+    for name, eng, xx, useful in runs:
+        out = eng.new_output()
+        for _ in range(max(1, args.warmup)):
+            eng.correlate(xx, out=out, stream=stream)
+        eng.synchronize(stream)
+        eng.set_option(xc.XC_OPT_PROFILE, 1)
+        eng.kernel_times(reset=True)
+        for _ in range(args.steps):
+            eng.correlate(xx, out=out, stream=stream)
+        eng.synchronize(stream)
+        (_, kms), (_, nk) = eng.kernel_times(reset=True)
+        kms /= max(nk, 1)
+        res[name] = {"kernel_ms": kms, "useful_tops": useful / (kms * 1e-3) / 1e12}
+        eng.close()
+        del out
+    print(json.dumps(res))
     return 0
 
 
@@ -762,9 +853,8 @@ def run_xc(args):
     form_s = form_ms * 1e-3 / max(n_form, 1)
     achieved = ops_int / main_s / 1e12
     long_region = ms * 1e-3 > 1.0
-    peak, peak_note = peak_of(peaks, measured, "fp16", long_region)
-    if not measured:
-        peak_note += " (%s)" % peaks_kind
+    peak, peak_note, peak_run = peak_of(peaks, measured, "fp16", long_region)
+    peak_note += " (%s)" % peaks_kind
     executed = executed_ops(w.nstation, w.npol, w.nfreq, w.ntime)
     roofline = {
         "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -774,6 +864,8 @@ def run_xc(args):
         "kernel_ms": main_s * 1e3, "launches": n_main,
         "executed_tflops": executed / main_s / 1e12,
         "algorithmic_ops_per_launch": ops_int,
+        "fp16_peak_measured_this_run": peak_run,
+        "frac_of_fp16_measured_this_run": achieved / peak_run if peak_run else None,
     }
     gpu_launches = n_form + n_main
     if n_form:
@@ -974,6 +1066,8 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.smalln or args.fp8_4bit:
+        return run_single(args)
     if args.fengine:
         return run_fengine(args)
     return run_xc(args)
