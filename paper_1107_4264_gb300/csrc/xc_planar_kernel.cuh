@@ -1924,10 +1924,14 @@ __device__ __forceinline__ void planar_body(const Batch& bt) {
                   else
                     store_piece_f64(vr, vi, p, f, a, b0, first, last_chunk);
                 } else {
+                  // With block sums on, this drain holds the whole
+                  // integration: it overwrites `out` (a paired chunk's
+                  // ch > 0 must not make it add).
+                  const bool add_out = add && !p.acc64;
                   if (tr)
-                    store_piece_tr<false>(vr, vi, p, f, a, b0, add);
+                    store_piece_tr<false>(vr, vi, p, f, a, b0, add_out);
                   else
-                    store_piece<false>(vr, vi, p, f, a, b0, add);
+                    store_piece<false>(vr, vi, p, f, a, b0, add_out);
                 }
               }
             }

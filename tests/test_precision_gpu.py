@@ -124,6 +124,33 @@ def test_fp64_block_sums_long_integration(dev):
     assert e512 < e32 / 30 and e64 < e512
 
 
+@pytest.mark.parametrize("nblocks", [1, 2, 3, 4], ids=["one_block", "one_pair", "pair_plus_one", "two_pairs"])
+@pytest.mark.parametrize("P", [2, 1])
+def test_fp64_block_sums_overwrite_each_call(nblocks, P, dev):
+    """Without ACCUMULATE every call's result replaces `out`: the same handle
+    called twice into an output prefilled with garbage gives one
+    integration's visibilities.  Covers a single fp32 chunk, one chunk pair
+    (summed in TMEM and stored directly), a pair plus a single chunk and two
+    pairs (float64 running sum), both polarisation counts."""
+    blk, F, N = 128, 3, 40
+    T = blk * nblocks
+    x = synth.sky_voltages(T, F, N, P, noise_sigma=1.0, nsrc=2, src_amp=1.0, seed=81 + nblocks)
+    want = oracle.correlate_f64(x.double().numpy())
+    eng = xc.Correlator(N, P, F, T, "float32", fp64_block=blk)
+    try:
+        out = eng.new_output()
+        out.fill_(7.0)
+        xd = x.to(dev)
+        for _ in range(2):
+            eng.correlate(xd, out=out)
+        eng.synchronize()
+        got = out.cpu().double().numpy()
+    finally:
+        eng.close()
+    frob, mx = frob_and_maxnorm(got, want, N, P)
+    assert frob <= FROB_TOL["fp16"] and mx <= 1e-3, (frob, mx)
+
+
 def test_fp64_block_sums_accumulate_across_calls(dev):
     """ACCUMULATE with FP64 block sums continues the handle's float64 running
     sum: three calls equal one integration over the concatenated samples."""
