@@ -128,13 +128,14 @@ def executed_ops(N, P, F, T, steps_per_block=1):
 
 
 def small_executed_ops(N, P, F, T):
-    """Real operations the small-array engine's MMAs execute: per group of
-    m = 128 / W channels (W = 2 N P) and 64-sample stage, m MMAs of
-    128 x W x 64, over T padded to 64."""
+    """Real operations the small-array engine's MMAs execute: per channel
+    group (m = 128 / W channels, or one channel of two tiles at W = 2 N P =
+    256) and sample, one 128 x 128 MMA step (three at W = 256: the lower tile
+    blocks), over T padded to 64."""
     from paper_1107_4264_gb300 import xc
     m = xc.load().xc_small_engine_channels(N, P)
-    W = 2 * N * P
-    return 2 * 128 * W * m * ((T + 63) // 64 * 64) * ((F + m - 1) // m)
+    blocks = 3 if 2 * N * P == 256 else 1
+    return 2 * 128 * 128 * blocks * ((T + 63) // 64 * 64) * ((F + m - 1) // m)
 
 
 def source_sha(paths):
@@ -632,7 +633,7 @@ def measure_forms(args, torch, xc, synth, dev, stream, timed, peaks, measured):
     # engine's packed channels (XC_TILE_128) on the same int8 sky data.  The
     # small engine is bound by its single input read: in_gbs is that stream.
     small = {}
-    for N, F in ((8, 65528), (16, 65528), (32, 65104)):
+    for N, F in ((8, 65528), (16, 65528), (32, 65104), (64, 16520)):
         T = 1000
         xs = synth.sky_voltages(T, F, N, 2, noise_sigma=3.0, nsrc=3, src_amp=1.5, seed=4242 + N + T,
                                 device=dev, quantise_int8=True)

@@ -210,13 +210,14 @@ enum { XC_PREC_FP16 = 0, XC_PREC_HILO = 1, XC_PREC_FP8 = 2 };
  *     fewer shared-memory and L2 operand bytes per MAC than XC_TILE_128.  Not
  *     with XC_PREC_HILO (XC_ERR_UNSUPPORTED at the call).
  *   XC_TILE_SMALL: the small-array engine (8-bit input, fp16 operands,
- *     W = 2 * nstation * npol in {16, 32, 64, 128}).  Each input is two real
- *     rows (re, im) of a 128-row tile that holds 128 / W channels; per
- *     16-sample step one 128 x W MMA per channel takes the whole tile as A
- *     and the channel's own W rows as B, giving the real Gram matrix whose
- *     2 x 2 sub-blocks form V (Sec. 4.4's diagonal blocks at twice the
- *     planar density).  Operands are converted straight into shared memory:
- *     no operand ring, one read of the input.  When the channel groups
+ *     W = 2 * nstation * npol in {16, 32, 64, 128, 256}).  Each input is two
+ *     real rows (re, im) of 128-row tiles; a tile holds 128 / W channels
+ *     (W <= 128) or a channel spans two tiles (W = 256).  Per 16-sample step
+ *     128 x 128 MMAs form the real Gram matrix of the tile rows (one MMA, or
+ *     three for the lower tile blocks at W = 256), whose 2 x 2 sub-blocks
+ *     give V (Sec. 4.4's diagonal blocks at twice the planar density).
+ *     Operands are converted straight into shared memory: no operand ring,
+ *     one read of the input.  When the channel groups
  *     (ceil(nfreq * W / 128)) are fewer than twice the SM count, T is split
  *     across CTAs and partial sums are added with integer atomics into the
  *     output, which the call zeroes first unless XC_OPT_ACCUMULATE is set.
@@ -316,9 +317,10 @@ void xc_tri_coords(int64_t g, int64_t* bx, int64_t* by);
 int xc_channels_packed(int nstation, int npol, int nfreq);
 
 /*
- * Channels per 128-row tile of the small-array engine (XC_TILE_SMALL) for
+ * Channels per channel group of the small-array engine (XC_TILE_SMALL) for
  * these sizes: 128 / (2 * nstation * npol) when that product is 16, 32, 64
- * or 128, else 0 (the planar engine serves the sizes).  Host-side, no device
+ * or 128, 1 when it is 256 (a channel spans two 128-row tiles), else 0 (the
+ * planar engine serves the sizes).  Host-side, no device
  * work.  With XC_TILE_AUTO an 8-bit, fp16-operand handle of such sizes runs
  * on the small-array engine, and xc_channels_packed does not apply to it.
  */

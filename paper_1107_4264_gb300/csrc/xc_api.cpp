@@ -240,7 +240,7 @@ xc_handle::Timed* next_timed(xc_handle* h, int nkern) {
 }
 
 // The small-array engine serves XC_ENGINE_TENSOR handles with 8-bit input,
-// fp16 operands and 2 N P in {16, 32, 64, 128} (XC_TILE_AUTO or
+// fp16 operands and 2 N P in {16, 32, 64, 128, 256} (XC_TILE_AUTO or
 // XC_TILE_SMALL); the planar engine's test hook keeps a handle on that engine.
 bool use_small_engine(const xc_handle* h, const void* in) {
   return h->dtype == XC_CI8 && h->precision == XC_PREC_FP16 && !h->test_no_publish &&
@@ -289,7 +289,7 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
   }
   if (h->engine == XC_ENGINE_TENSOR && h->tile == XC_TILE_SMALL)
     return fail(XC_ERR_UNSUPPORTED,
-                "XC_TILE_SMALL needs 8-bit input, fp16 operands and 2*nstation*npol in {16, 32, 64, 128}");
+                "XC_TILE_SMALL needs 8-bit input, fp16 operands and 2*nstation*npol in {16, 32, 64, 128, 256}");
   if (h->engine == XC_ENGINE_TENSOR) {
     xc::XeLaunch X;
     X.g = h->pg;
@@ -531,7 +531,7 @@ xc_status xc_fp32_peak_probe(long long iterations, void* sink, void* stream, lon
 int64_t xc_tri_index(int64_t bx, int64_t by) { return xc::tri_index(bx, by); }
 
 int xc_small_engine_channels(int nstation, int npol) {
-  if (nstation <= 0 || (npol != 1 && npol != 2) || nstation > 64) return 0;
+  if (nstation <= 0 || (npol != 1 && npol != 2) || nstation > 128) return 0;
   xc::Geometry g{};
   g.N = nstation;
   g.P = npol;

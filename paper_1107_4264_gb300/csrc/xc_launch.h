@@ -143,10 +143,10 @@ bool input_map_possible(xc_dtype dtype, const Geometry& g);
 xc_status encode_input_map(CUtensorMap* map, const void* in, const Geometry& g, xc_dtype dtype);
 
 // Small-array engine (xc_small.cu): 8-bit input whose channels have
-// W = 2 N P in {16, 32, 64, 128} real rows.  small_tile_channels() is the
-// number of channels per 128-row operand tile (128 / W), or 0 when the
-// geometry does not qualify.  The input map is {W, F, T} bytes in boxes of
-// W x (128 / W) x 64.  launch_small() may queue a memset of the output
+// W = 2 N P in {16, 32, 64, 128, 256} real rows.  small_tile_channels() is
+// the number of channels per channel group (128 / W, or 1 for W = 256,
+// whose channel spans two 128-row tiles), or 0 when the geometry does not
+// qualify.  The input map is {W, F, T} bytes in boxes of W x group x 64.  launch_small() may queue a memset of the output
 // before the kernel (when it splits T across CTAs and does not accumulate).
 int small_tile_channels(const Geometry& g);
 xc_status encode_small_map(CUtensorMap* map, const void* in, const Geometry& g);

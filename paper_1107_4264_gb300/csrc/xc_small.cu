@@ -1,5 +1,5 @@
 // xc_small.cu -- tensor-core X-engine for small arrays: 8-bit input with
-// 2 N P in {16, 32, 64, 128} real rows per channel.
+// W = 2 N P in {16, 32, 64, 128, 256} real rows per channel.
 //
 // The operation is Eq. (outer) of Sec. 2.1, V_f = sum_t x_f(t) x_f(t)^H per
 // channel, lower station triangle only (Sec. 4.2).  Sec. 4.4 computes whole
@@ -17,7 +17,9 @@
 // The cross-channel blocks are computed and not read.  (One 128 x W MMA
 // per channel would skip them, but a tcgen05.mma costs about as long to
 // issue at N = 16 .. 64 as a 128 x 128 one takes to run, so m of them are
-// slower than the one full MMA.)
+// slower than the one full MMA.)  With W = 256 a channel is two tiles
+// (inputs 0-63 and 64-127) and three 128 x 128 MMAs per step form the
+// lower tile blocks G00, G10 = X1 X0^T and G11.
 //
 // No operand ring: a channel's operands are used by one CTA only, so each
 // CTA converts its 8-bit input straight into shared-memory operand tiles.
@@ -29,8 +31,8 @@
 // magnitude <= 128^2 stays <= 2^24, so each 1024-sample chunk is exact in
 // fp32 and chunks add in int32.
 //
-// Roles of a persistent CTA (one per SM, 6 + kConvWarps warps):
-//   warp 0     TMA producer: [64 samples][m channels][2n bytes] int8 boxes;
+// Roles of a persistent CTA (one per SM, 6 + Cfg<W>::kConvWarps warps):
+//   warp 0     TMA producer: [64 samples][m channels][W bytes] int8 boxes;
 //   warp 1     TMEM owner and MMA issuer (one thread);
 //   warps 2-5  epilogue: TMEM -> V (int32) in the output layout;
 //   warps 6 .. converters: int8 box -> fp16 tile in the no-swizzle K-major
@@ -55,36 +57,61 @@
 namespace xc {
 namespace {
 
-constexpr int kRows = 128;                  // real rows per operand tile
-constexpr int kBK = 64;                     // samples per stage
-constexpr int kChunk = 1024;                // samples per exact fp32 chunk
-constexpr int kInStages = 12;               // int8 boxes (8 KiB) in flight
-constexpr int kOpStages = 6;                // fp16 operand tiles (16 KiB)
-constexpr int kInBytes = kRows * kBK;       // 8 KiB
-constexpr int kOpBytes = kRows * kBK * 2;   // 16 KiB
-constexpr uint32_t kCore = 128;             // one core matrix: 8 rows x 16 B
+constexpr int kRows = 128;                    // real rows per operand tile
+constexpr int kBK = 64;                       // samples per stage
+constexpr int kChunk = 1024;                  // samples per exact fp32 chunk
+constexpr int kTileBytes = kRows * kBK * 2;   // one fp16 operand tile: 16 KiB
+constexpr uint32_t kCore = 128;               // one core matrix: 8 rows x 16 B
 constexpr uint32_t kSbo = (kBK / 8) * kCore;  // 1 KiB between 8-row groups
-constexpr int kConvWarp0 = 6;                // warps 0 .. 5: producer, MMA, epilogue
-constexpr int kConvWarps = 6;
-constexpr int kThreads = 32 * (kConvWarp0 + kConvWarps);
+constexpr int kConvWarp0 = 6;                 // warps 0 .. 5: producer, MMA, epilogue
+
+// Shapes per channel width W.  W <= 128: kM = 128 / W channels per tile,
+// two 128-column accumulator buffers.  W = 256: one channel of two tiles,
+// whose three lower 128 x 128 blocks fill 384 TMEM columns (one buffer).
 // Converter warp cw takes stages cw, cw + kConvWarps, ...; with slot counts
 // that are multiples of kConvWarps every input and operand slot belongs to
 // one warp, which waits on its barriers phase by phase.  (A slot shared by
 // two warps lets one of them wait on a parity two phases old, which passes
 // too early: mbarrier waits test parity, not a phase count.)
-static_assert(kInStages % kConvWarps == 0 && kOpStages % kConvWarps == 0,
-              "each converter warp owns its input and operand slots");
-constexpr uint32_t kTmemCols = 256;         // two accumulator buffers x 128 columns
+template <int W>
+struct Cfg {
+  static constexpr int kTiles = W > kRows ? W / kRows : 1;
+  static constexpr int kM = W > kRows ? 1 : kRows / W;        // channels per group
+  static constexpr int kWt = W > kRows ? kRows : W;           // a channel's rows in one tile
+  static constexpr int kBlocks = kTiles * (kTiles + 1) / 2;   // lower tile blocks
+  static constexpr int kConvWarps = kTiles == 1 ? 6 : 4;
+  static constexpr int kInStages = kTiles == 1 ? 12 : 4;      // int8 boxes in flight
+  static constexpr int kOpStages = kTiles == 1 ? 6 : 4;       // fp16 operand slots
+  static constexpr int kInBytes = kTiles * kRows * kBK;       // 8 or 16 KiB
+  static constexpr int kOpBytes = kTiles * kTileBytes;        // 16 or 32 KiB
+  static constexpr int kBufs = kTiles == 1 ? 2 : 1;           // accumulator buffers
+  static constexpr int kAccCols = kBlocks * kRows;            // TMEM columns per buffer
+  static constexpr uint32_t kTmemCols = kTiles == 1 ? 256 : 512;
+  static constexpr int kThreads = 32 * (kConvWarp0 + kConvWarps);
+  static constexpr int kOpOff = 0;
+  static constexpr int kInOff = kOpOff + kOpStages * kOpBytes;
+  static constexpr int kBarOff = kInOff + kInStages * kInBytes;
+  // in_full, in_empty per input stage; op_full, op_empty per operand stage;
+  // accf, acce per accumulator buffer (two reserved); one drain barrier.
+  static constexpr int kNumBars = 2 * kInStages + 2 * kOpStages + 5;
+  static constexpr int kMiscOff = kBarOff + kNumBars * 8;  // TMEM address, abort flag
+  static constexpr int kSmemBytes = kMiscOff + 16 + 1024;   // + slack to align the base to 1 KiB
+  static_assert(W == 16 || W == 32 || W == 64 || W == 128 || W == 256, "channel widths served");
+  static_assert(kInStages % kConvWarps == 0 && kOpStages % kConvWarps == 0,
+                "each converter warp owns its input and operand slots");
+  static_assert(kSmemBytes <= 232448, "shared memory budget");
+  static_assert(kBufs * kAccCols <= static_cast<int>(kTmemCols), "TMEM budget");
 
-constexpr int kOpOff = 0;
-constexpr int kInOff = kOpOff + kOpStages * kOpBytes;
-constexpr int kBarOff = kInOff + kInStages * kInBytes;
-// in_full, in_empty per input stage; op_full, op_empty per operand stage;
-// accf, acce per accumulator buffer; one drain barrier.
-constexpr int kNumBars = 2 * kInStages + 2 * kOpStages + 5;
-constexpr int kMiscOff = kBarOff + kNumBars * 8;  // TMEM address, abort flag
-constexpr int kSmemBytes = kMiscOff + 16 + 1024;   // + slack to align the base to 1 KiB
-static_assert(kSmemBytes <= 232448, "shared memory budget");
+  __device__ static uint32_t in_full(uint32_t b, int s) { return b + 8u * s; }
+  __device__ static uint32_t in_empty(uint32_t b, int s) { return b + 8u * (kInStages + s); }
+  __device__ static uint32_t op_full(uint32_t b, int s) { return b + 8u * (2 * kInStages + s); }
+  __device__ static uint32_t op_empty(uint32_t b, int s) { return b + 8u * (2 * kInStages + kOpStages + s); }
+  __device__ static uint32_t accf(uint32_t b, int ab) { return b + 8u * (2 * kInStages + 2 * kOpStages + ab); }
+  __device__ static uint32_t acce(uint32_t b, int ab) {
+    return b + 8u * (2 * kInStages + 2 * kOpStages + 2 + ab);
+  }
+  __device__ static uint32_t drain(uint32_t b) { return b + 8u * (2 * kInStages + 2 * kOpStages + 4); }
+};
 
 struct SmallParams {
   int N, P, F, T;
@@ -98,22 +125,6 @@ struct SmallParams {
   unsigned long long timeout_ns;
   int* status;
 };
-
-__device__ __forceinline__ uint32_t bar_in_full(uint32_t b, int s) { return b + 8u * s; }
-__device__ __forceinline__ uint32_t bar_in_empty(uint32_t b, int s) { return b + 8u * (kInStages + s); }
-__device__ __forceinline__ uint32_t bar_op_full(uint32_t b, int s) { return b + 8u * (2 * kInStages + s); }
-__device__ __forceinline__ uint32_t bar_op_empty(uint32_t b, int s) {
-  return b + 8u * (2 * kInStages + kOpStages + s);
-}
-__device__ __forceinline__ uint32_t bar_accf(uint32_t b, int ab) {
-  return b + 8u * (2 * kInStages + 2 * kOpStages + ab);
-}
-__device__ __forceinline__ uint32_t bar_acce(uint32_t b, int ab) {
-  return b + 8u * (2 * kInStages + 2 * kOpStages + 2 + ab);
-}
-__device__ __forceinline__ uint32_t bar_drain(uint32_t b) {
-  return b + 8u * (2 * kInStages + 2 * kOpStages + 4);
-}
 
 // Samples [t0, t1) of work item `it` (channel group it / nseg).
 struct Item {
@@ -174,42 +185,43 @@ __device__ __forceinline__ void put_vis(int32_t* dst, int re, int im, int mode) 
   }
 }
 
-// W = 2 N P real rows per channel; the tile holds kRows / W channels.
+// W = 2 N P real rows per channel (Cfg<W> holds the shapes).
 template <int W>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
     small_kernel(const __grid_constant__ CUtensorMap in_map, const SmallParams p) {
-  static_assert(W == 16 || W == 32 || W == 64 || W == 128, "a channel's rows divide the tile");
-  constexpr int kM = kRows / W;
-  constexpr int kPieces = W >= 32 ? W / 32 : 1;  // 32-column TMEM loads per channel block
+  using C = Cfg<W>;
+  constexpr int kM = C::kM;
+  constexpr int kWt = C::kWt;
+  constexpr int kPieces = kWt >= 32 ? kWt / 32 : 1;  // 32-column TMEM loads per block row
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
   unsigned char* sgen = smem_raw + (sbase - raw);
-  const uint32_t bars = sbase + kBarOff;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sgen + kMiscOff);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(sgen + kMiscOff + 4);
+  const uint32_t bars = sbase + C::kBarOff;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sgen + C::kMiscOff);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sgen + C::kMiscOff + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int items = p.ngroups * p.nseg;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kInStages; ++s) {
-      ptx::mbar_init(bar_in_full(bars, s), 1);
-      ptx::mbar_init(bar_in_empty(bars, s), 1);
+    for (int s = 0; s < C::kInStages; ++s) {
+      ptx::mbar_init(C::in_full(bars, s), 1);
+      ptx::mbar_init(C::in_empty(bars, s), 1);
     }
-    for (int s = 0; s < kOpStages; ++s) {
-      ptx::mbar_init(bar_op_full(bars, s), 1);
-      ptx::mbar_init(bar_op_empty(bars, s), 1);
+    for (int s = 0; s < C::kOpStages; ++s) {
+      ptx::mbar_init(C::op_full(bars, s), 1);
+      ptx::mbar_init(C::op_empty(bars, s), 1);
     }
     for (int ab = 0; ab < 2; ++ab) {
-      ptx::mbar_init(bar_accf(bars, ab), 1);
-      ptx::mbar_init(bar_acce(bars, ab), 4);
+      ptx::mbar_init(C::accf(bars, ab), 1);
+      ptx::mbar_init(C::acce(bars, ab), 4);
     }
-    ptx::mbar_init(bar_drain(bars), 1);
+    ptx::mbar_init(C::drain(bars), 1);
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), kTmemCols);
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), C::kTmemCols);
     ptx::tmem_relinquish();
   }
   if (warp == 0 && lane == 0) ptx::prefetch_tmap(&in_map);
@@ -230,16 +242,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int it = blockIdx.x; ok && it < items; it += gridDim.x) {
         const Item x = item_of(p, it);
         for (int t = x.t0; t < x.t1; t += kBK) {
-          if (!ptx::wait_bounded(bar_in_empty(bars, si), ph ^ 1u, wc)) {
+          if (!ptx::wait_bounded(C::in_empty(bars, si), ph ^ 1u, wc)) {
             ok = false;
             break;
           }
           // Past F or T the box is zero-filled; the transaction count is the whole box.
-          ptx::mbar_arrive_expect_tx(bar_in_full(bars, si), kInBytes);
-          ptx::tma_load_3d_hint(sbase + kInOff + si * kInBytes, &in_map, bar_in_full(bars, si), 0,
+          ptx::mbar_arrive_expect_tx(C::in_full(bars, si), C::kInBytes);
+          ptx::tma_load_3d_hint(sbase + C::kInOff + si * C::kInBytes, &in_map, C::in_full(bars, si), 0,
                                 x.g * kM, t, pol);
           ++issued;
-          if (++si == kInStages) {
+          if (++si == C::kInStages) {
             si = 0;
             ph ^= 1u;
           }
@@ -248,11 +260,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       // No box may still be landing when the CTA exits (converters that gave
       // up no longer wait for them): wait, bounded, for the last box of every
       // stage.  Issue k used phase k / kInStages of stage k % kInStages.
-      for (long long k = max(0LL, issued - kInStages); k < issued; ++k) {
-        const int s = static_cast<int>(k % kInStages);
-        const uint32_t par = static_cast<uint32_t>((k / kInStages) & 1);
+      for (long long k = max(0LL, issued - C::kInStages); k < issued; ++k) {
+        const int s = static_cast<int>(k % C::kInStages);
+        const uint32_t par = static_cast<uint32_t>((k / C::kInStages) & 1);
         const uint64_t t0 = ptx::globaltimer();
-        while (!ptx::mbar_try_wait(bar_in_full(bars, s), par) && ptx::globaltimer() - t0 < p.timeout_ns) {
+        while (!ptx::mbar_try_wait(C::in_full(bars, s), par) && ptx::globaltimer() - t0 < p.timeout_ns) {
         }
       }
     }
@@ -269,54 +281,65 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c0 = x.t0; ok && c0 < x.t1; c0 += kChunk) {
           const int c1 = min(x.t1, c0 + kChunk);
           // The epilogue has read this buffer's previous chunk.
-          if (!ptx::wait_bounded(bar_acce(bars, ab), ((usep >> ab) & 1u) ^ 1u, wc)) {
+          if (!ptx::wait_bounded(C::acce(bars, ab), ((usep >> ab) & 1u) ^ 1u, wc)) {
             ok = false;
             break;
           }
           ptx::tc_fence_after();
           for (int t = c0; t < c1; t += kBK) {
-            if (!ptx::wait_bounded(bar_op_full(bars, so), oph, wc)) {
+            if (!ptx::wait_bounded(C::op_full(bars, so), oph, wc)) {
               ok = false;
               break;
             }
             ptx::tc_fence_after();
-            const uint32_t tile = sbase + kOpOff + so * kOpBytes;
+            const uint32_t stage = sbase + C::kOpOff + so * C::kOpBytes;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk) {
-              // A and B: all 128 rows (K step kk = chunks 2kk, 2kk + 1).  D
-              // holds every channel's block on its diagonal; the epilogue
-              // reads only those.
-              const uint64_t d = ptx::interleave_kmajor_desc(tile + kk * 2 * kCore, kCore, kSbo);
-              ptx::mma_f16_ss(tmem + static_cast<uint32_t>(ab * 128), d, d, idesc,
-                              (t > c0 || kk > 0) ? 1u : 0u);
+              // K step kk = chunks 2kk, 2kk + 1 of every tile.  Block (ta, tb)
+              // of the lower tile triangle: A = tile ta, B = tile tb.  With
+              // one tile, A = B = the tile: D holds every channel's block on
+              // its diagonal and the epilogue reads only those.
+#pragma unroll
+              for (int ta = 0; ta < C::kTiles; ++ta) {
+#pragma unroll
+                for (int tb = 0; tb <= ta; ++tb) {
+                  const uint64_t da =
+                      ptx::interleave_kmajor_desc(stage + ta * kTileBytes + kk * 2 * kCore, kCore, kSbo);
+                  const uint64_t db =
+                      ptx::interleave_kmajor_desc(stage + tb * kTileBytes + kk * 2 * kCore, kCore, kSbo);
+                  const int blk = ta * (ta + 1) / 2 + tb;
+                  ptx::mma_f16_ss(tmem + static_cast<uint32_t>(ab * C::kAccCols + blk * kRows), da, db, idesc,
+                                  (t > c0 || kk > 0) ? 1u : 0u);
+                }
+              }
             }
-            ptx::mma_commit(bar_op_empty(bars, so));  // the tile may be refilled once read
-            if (++so == kOpStages) {
+            ptx::mma_commit(C::op_empty(bars, so));  // the tile may be refilled once read
+            if (++so == C::kOpStages) {
               so = 0;
               oph ^= 1u;
             }
           }
           if (!ok) break;
-          ptx::mma_commit(bar_accf(bars, ab));
+          ptx::mma_commit(C::accf(bars, ab));
           usep ^= 1u << ab;
-          ab ^= 1;
+          ab = (ab + 1) % C::kBufs;
         }
       }
       // Every MMA issued completes before TMEM is freed and the CTA exits.
-      ptx::mma_commit(bar_drain(bars));
+      ptx::mma_commit(C::drain(bars));
       const uint64_t t0 = ptx::globaltimer();
-      while (!ptx::mbar_try_wait(bar_drain(bars), 0u) && ptx::globaltimer() - t0 < p.timeout_ns) {
+      while (!ptx::mbar_try_wait(C::drain(bars), 0u) && ptx::globaltimer() - t0 < p.timeout_ns) {
       }
     }
   } else if (warp < kConvWarp0) {  // warps 2 .. 5
     // --------------------------------------------------------- epilogue
-    // Warp w reads TMEM lanes 32 (w % 4) ..: tile row r is TMEM lane r.
+    // Warp w reads TMEM lanes 32 (w % 4) ..: tile row r is TMEM lane r (in
+    // every block: block (ta, tb) has the rows of tile ta).
     const int q = warp & 3;
     const int r = 32 * q + lane;
-    const int k = r / W;           // channel of row r within the tile
-    const int a = (r % W) >> 1;    // input of the row (station a / P, polarisation a % P)
-    const int c = r & 1;           // 0: the row holds re(x_a), 1: im(x_a)
-    const int s1 = a / p.P, p1 = a % p.P;
+    const int k = r / kWt;          // channel of row r within the tile (W <= 128)
+    const int al = (r % kWt) >> 1;  // input of the row within its tile
+    const int c = r & 1;            // 0: the row holds re(x_a), 1: im(x_a)
     const int PP = p.P * p.P;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
     int ab = 0;
@@ -328,54 +351,63 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool chan_ok = ch < p.F;
       int32_t* obase = p.out + static_cast<int64_t>(ch) * p.NB * PP * 2;
       for (int c0 = x.t0; c0 < x.t1; c0 += kChunk) {
-        if (!warp_wait(bar_accf(bars, ab), (usep >> ab) & 1u, wc)) {
+        if (!warp_wait(C::accf(bars, ab), (usep >> ab) & 1u, wc)) {
           ok = false;
           break;
         }
         ptx::tc_fence_after();
         const int mode = p.use_red ? 2 : ((c0 == x.t0 && !p.accumulate) ? 0 : 1);
 #pragma unroll 1
-        for (int pc = 0; pc < kPieces; ++pc) {
-          uint32_t v[32];
-          // Channel k's G columns; with W = 16 the piece holds the warp's two channels.
-          const uint32_t col = static_cast<uint32_t>(ab * 128 + (W >= 32 ? k * W + 32 * pc : 32 * q));
-          ptx::tmem_ld_32x32b_x32(lane_base + col, v);
-          ptx::tmem_wait_ld();
-          if (pc == kPieces - 1) {  // the buffer is free for the next chunk's MMAs
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(bar_acce(bars, ab));
-          }
-          constexpr int kJ = W >= 32 ? 8 : 4;  // input pairs (2j, 2j + 1) in the piece
-          const bool hi = W == 16 && lane >= 16;
+        for (int blk = 0; blk < C::kBlocks; ++blk) {
+          // Block (ta, tb) of the lower tile triangle (ta >= tb): inputs of
+          // tile ta against those of tile tb (64 inputs per tile).
+          const int ta = blk == 0 ? 0 : 1, tb = blk == 2 ? 1 : 0;
+          const int a = ta * (kRows / 2) + al;  // station a / P, polarisation a % P
+          const int s1 = a / p.P, p1 = a % p.P;
+#pragma unroll 1
+          for (int pc = 0; pc < kPieces; ++pc) {
+            uint32_t v[32];
+            // Channel k's G columns; with W = 16 the piece holds the warp's two channels.
+            const uint32_t col = static_cast<uint32_t>(ab * C::kAccCols + blk * kRows +
+                                                       (kWt >= 32 ? k * kWt + 32 * pc : 32 * q));
+            ptx::tmem_ld_32x32b_x32(lane_base + col, v);
+            ptx::tmem_wait_ld();
+            if (blk == C::kBlocks - 1 && pc == kPieces - 1) {  // the buffer is free for the next chunk
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(C::acce(bars, ab));
+            }
+            constexpr int kJ = kWt >= 32 ? 8 : 4;  // input pairs (2j, 2j + 1) in the piece
+            const bool hi = kWt == 16 && lane >= 16;
 #pragma unroll
-          for (int jj = 0; jj < kJ; ++jj) {
-            // Columns 4j .. 4j+3 of the channel block: G[row][2b], G[row][2b+1]
-            // for b = 2j (d0, d1) and b = 2j + 1 (d2, d3).
-            const float d0 = __uint_as_float(hi ? v[16 + 4 * jj] : v[4 * jj]);
-            const float d1 = __uint_as_float(hi ? v[16 + 4 * jj + 1] : v[4 * jj + 1]);
-            const float d2 = __uint_as_float(hi ? v[16 + 4 * jj + 2] : v[4 * jj + 2]);
-            const float d3 = __uint_as_float(hi ? v[16 + 4 * jj + 3] : v[4 * jj + 3]);
-            // This lane produces V(a, b) for b = 2j + c; the partner row (lane ^ 1,
-            // same input, other component) sends its two columns for that b.
-            const float keep0 = c ? d2 : d0, keep1 = c ? d3 : d1;
-            const float send0 = c ? d0 : d2, send1 = c ? d1 : d3;
-            const float got0 = __shfl_xor_sync(0xffffffffu, send0, 1);
-            const float got1 = __shfl_xor_sync(0xffffffffu, send1, 1);
-            const int o0 = __float2int_rn(keep0), o1 = __float2int_rn(keep1);
-            const int g0 = __float2int_rn(got0), g1 = __float2int_rn(got1);
-            // c = 0: own (rr, ri), partner (ir, ii); c = 1: own (ir, ii), partner (rr, ri).
-            const int re = c ? g0 + o1 : o0 + g1;
-            const int im = c ? o0 - g1 : g0 - o1;
-            const int b = 2 * ((W >= 32 ? 8 * pc : 0) + jj) + c;
-            const int s2 = b / p.P, p2 = b % p.P;
-            if (chan_ok && s2 <= s1)
-              put_vis(obase + ((static_cast<int64_t>(s1) * (s1 + 1) / 2 + s2) * PP + p1 * p.P + p2) * 2,
-                      re, im, mode);
+            for (int jj = 0; jj < kJ; ++jj) {
+              // Columns 4j .. 4j+3 of the channel block: G[row][2b], G[row][2b+1]
+              // for b = 2j (d0, d1) and b = 2j + 1 (d2, d3).
+              const float d0 = __uint_as_float(hi ? v[16 + 4 * jj] : v[4 * jj]);
+              const float d1 = __uint_as_float(hi ? v[16 + 4 * jj + 1] : v[4 * jj + 1]);
+              const float d2 = __uint_as_float(hi ? v[16 + 4 * jj + 2] : v[4 * jj + 2]);
+              const float d3 = __uint_as_float(hi ? v[16 + 4 * jj + 3] : v[4 * jj + 3]);
+              // This lane produces V(a, b) for b = 2j + c; the partner row (lane ^ 1,
+              // same input, other component) sends its two columns for that b.
+              const float keep0 = c ? d2 : d0, keep1 = c ? d3 : d1;
+              const float send0 = c ? d0 : d2, send1 = c ? d1 : d3;
+              const float got0 = __shfl_xor_sync(0xffffffffu, send0, 1);
+              const float got1 = __shfl_xor_sync(0xffffffffu, send1, 1);
+              const int o0 = __float2int_rn(keep0), o1 = __float2int_rn(keep1);
+              const int g0 = __float2int_rn(got0), g1 = __float2int_rn(got1);
+              // c = 0: own (rr, ri), partner (ir, ii); c = 1: own (ir, ii), partner (rr, ri).
+              const int re = c ? g0 + o1 : o0 + g1;
+              const int im = c ? o0 - g1 : g0 - o1;
+              const int b = tb * (kRows / 2) + 2 * ((kWt >= 32 ? 8 * pc : 0) + jj) + c;
+              const int s2 = b / p.P, p2 = b % p.P;
+              if (chan_ok && s2 <= s1)
+                put_vis(obase + ((static_cast<int64_t>(s1) * (s1 + 1) / 2 + s2) * PP + p1 * p.P + p2) * 2,
+                        re, im, mode);
+            }
           }
         }
         usep ^= 1u << ab;
-        ab ^= 1;
+        ab = (ab + 1) % C::kBufs;
       }
     }
   } else {
@@ -383,14 +415,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     // The CTA's stages (its items in turn, 64 samples each) are numbered
     // k = 0, 1, ...; converter warp cw takes k = cw, cw + kConvWarps, ...
     // whole, so kConvWarps stages are converted at once and each warp's
-    // latency overlaps the others'.  Stage k uses input slot k % kInStages and operand slot
-    // k % kOpStages, in phase k / (slot count).  The box ([64 samples][128
-    // bytes]: byte r of a sample is tile row r) becomes the fp16 tile: lane
-    // l reads byte word l (rows 4l .. 4l+3) of each sample and writes one
-    // 16-byte core-matrix row per tile row and 8-sample chunk.  Step s
-    // writes row 4l + ((s + l / 2) mod 4), so the 8 lanes of each
-    // quarter-warp cover the 8 rows of a core matrix, one shared-memory bank
-    // group each: the 16-byte stores do not conflict.
+    // latency overlaps the others'.  Stage k uses input slot k % kInStages
+    // and operand slot k % kOpStages, in phase k / (slot count).  The box
+    // ([64 samples][kTiles x 128 bytes]: byte r of a sample's 128-byte
+    // piece t is row r of tile t) becomes the fp16 tiles: lane l reads byte
+    // word l (rows 4l .. 4l+3) of each sample and writes one 16-byte
+    // core-matrix row per tile row and 8-sample chunk.  Step s writes row
+    // 4l + ((s + l / 2) mod 4), so the 8 lanes of each quarter-warp cover
+    // the 8 rows of a core matrix, one shared-memory bank group each: the
+    // 16-byte stores do not conflict.
     const int cw = warp - kConvWarp0;
     uint32_t jsel[4];
 #pragma unroll
@@ -410,51 +443,56 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
     for (int s = 0; s < cw && it < items; ++s) advance();
-    for (long long k = cw; it < items; k += kConvWarps) {
-      const int si = static_cast<int>(k % kInStages), so = static_cast<int>(k % kOpStages);
-      const uint32_t iph = static_cast<uint32_t>((k / kInStages) & 1);
-      const uint32_t oph = static_cast<uint32_t>((k / kOpStages) & 1);
-      if (!warp_wait(bar_in_full(bars, si), iph, wc) || !warp_wait(bar_op_empty(bars, so), oph ^ 1u, wc))
+    for (long long k = cw; it < items; k += C::kConvWarps) {
+      const int si = static_cast<int>(k % C::kInStages), so = static_cast<int>(k % C::kOpStages);
+      const uint32_t iph = static_cast<uint32_t>((k / C::kInStages) & 1);
+      const uint32_t oph = static_cast<uint32_t>((k / C::kOpStages) & 1);
+      if (!warp_wait(C::in_full(bars, si), iph, wc) || !warp_wait(C::op_empty(bars, so), oph ^ 1u, wc))
         break;
-      const uint32_t src = sbase + kInOff + si * kInBytes + 4u * lane;
-      const uint32_t dst = sbase + kOpOff + so * kOpBytes;
+#pragma unroll
+      for (int tl = 0; tl < C::kTiles; ++tl) {
+        const uint32_t src = sbase + C::kInOff + si * C::kInBytes + tl * kRows + 4u * lane;
+        const uint32_t dst = sbase + C::kOpOff + so * C::kOpBytes + tl * kTileBytes;
 #pragma unroll 2
-      for (int cc = 0; cc < kBK / 8; ++cc) {
-        uint32_t w[8];
+        for (int cc = 0; cc < kBK / 8; ++cc) {
+          uint32_t w[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) w[u] = lds32(src + static_cast<uint32_t>((8 * cc + u) * kRows));
+          for (int u = 0; u < 8; ++u)
+            w[u] = lds32(src + static_cast<uint32_t>((8 * cc + u) * C::kTiles * kRows));
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t j = jsel[q];
-          const uint32_t row = 4u * lane + j;
-          sts128(dst + (row >> 3) * kSbo + cc * kCore + (row & 7u) * 16u, i8pair_to_h2(w[0], w[1], j),
-                 i8pair_to_h2(w[2], w[3], j), i8pair_to_h2(w[4], w[5], j), i8pair_to_h2(w[6], w[7], j));
+          for (int qq = 0; qq < 4; ++qq) {
+            const uint32_t j = jsel[qq];
+            const uint32_t row = 4u * lane + j;
+            sts128(dst + (row >> 3) * kSbo + cc * kCore + (row & 7u) * 16u, i8pair_to_h2(w[0], w[1], j),
+                   i8pair_to_h2(w[2], w[3], j), i8pair_to_h2(w[4], w[5], j), i8pair_to_h2(w[6], w[7], j));
+          }
         }
       }
-      // The tile's generic stores before the tensor core's reads; the box's
+      // The tiles' generic stores before the tensor core's reads; the box's
       // reads are complete (their values were stored).
       ptx::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        ptx::mbar_arrive(bar_in_empty(bars, si));
-        ptx::mbar_arrive(bar_op_full(bars, so));
+        ptx::mbar_arrive(C::in_empty(bars, si));
+        ptx::mbar_arrive(C::op_full(bars, so));
       }
-      for (int s = 0; s < kConvWarps && it < items; ++s) advance();
+      for (int s = 0; s < C::kConvWarps && it < items; ++s) advance();
     }
   }
   ptx::tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, kTmemCols);
+    ptx::tmem_dealloc(tmem, C::kTmemCols);
   }
 }
 
 template <int W>
 cudaError_t launch_w(const CUtensorMap* map, const SmallParams& p, int grid, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(small_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  using C = Cfg<W>;
+  cudaError_t e = cudaFuncSetAttribute(small_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
-  small_kernel<W><<<grid, kThreads, kSmemBytes, s>>>(*map, p);
+  small_kernel<W><<<grid, C::kThreads, C::kSmemBytes, s>>>(*map, p);
   return cudaGetLastError();
 }
 
@@ -462,6 +500,7 @@ cudaError_t launch_w(const CUtensorMap* map, const SmallParams& p, int grid, cud
 
 int small_tile_channels(const Geometry& g) {
   const int W = 2 * g.N * g.P;
+  if (W == 256) return 1;
   return (W == 16 || W == 32 || W == 64 || W == 128) ? kRows / W : 0;
 }
 
@@ -498,7 +537,8 @@ cudaError_t launch_small(const CUtensorMap* in_map, const XeLaunch& X, cudaStrea
     case 16: return launch_w<16>(in_map, p, grid, s);
     case 32: return launch_w<32>(in_map, p, grid, s);
     case 64: return launch_w<64>(in_map, p, grid, s);
-    default: return launch_w<128>(in_map, p, grid, s);
+    case 128: return launch_w<128>(in_map, p, grid, s);
+    default: return launch_w<256>(in_map, p, grid, s);
   }
 }
 

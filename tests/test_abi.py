@@ -133,13 +133,15 @@ def test_channels_packed_rule(lib):
 
 def test_small_engine_channels_rule(lib):
     """The small-array engine's reach: 128 / W channels per tile for
-    W = 2 N P in {16, 32, 64, 128}, else 0 (restated from its documentation)."""
-    for N in range(0, 80):
+    W = 2 N P in {16, 32, 64, 128}, one channel of two tiles for W = 256,
+    else 0 (restated from its documentation)."""
+    for N in range(0, 160):
         for P in (-1, 0, 1, 2, 3):
             W = 2 * N * P
-            want = 128 // W if P in (1, 2) and W in (16, 32, 64, 128) else 0
+            want = (128 // W if W <= 128 else 1) if P in (1, 2) and W in (16, 32, 64, 128, 256) else 0
             assert lib.xc_small_engine_channels(N, P) == want, (N, P)
     assert lib.xc_small_engine_channels(16, 2) == 2
+    assert lib.xc_small_engine_channels(64, 2) == 1 and lib.xc_small_engine_channels(128, 1) == 1
     assert lib.xc_small_engine_channels(2 ** 31 - 1, 2) == 0
 
 

@@ -1,11 +1,12 @@
 """The small-array engine (XC_TILE_SMALL): 8-bit input with W = 2 N P in
-{16, 32, 64, 128} real rows per channel.
+{16, 32, 64, 128, 256} real rows per channel.
 
-Each input is two real rows of a 128-row tile holding 128 / W channels; one
-MMA per channel and 16-sample step forms the real Gram matrix of the tile's
-rows against the channel's rows, and the epilogue combines its 2 x 2
-sub-blocks into V.  Every case is compared with the oracle bit for bit (the
-8-bit path is exact): all four tile widths with both polarisation counts,
+Each input is two real rows of a 128-row tile holding 128 / W channels (or,
+at W = 256, of two tiles holding one channel); 128 x 128 MMAs per 16-sample
+step form the real Gram matrix of the tile rows (three lower tile blocks at
+W = 256), and the epilogue combines its 2 x 2 sub-blocks into V.  Every case
+is compared with the oracle bit for bit (the 8-bit path is exact): all five
+widths with both polarisation counts,
 channel counts that leave the last tile part-empty, integrations shorter than
 one 64-sample stage, ragged against it, exactly one exact-fp32 chunk, one
 sample past it, and several chunks; full-scale -128 input at the chunk
@@ -47,24 +48,27 @@ def run(x, dev, tile=xc.XC_TILE_SMALL, accumulate=False, out=None, reps=1):
         eng.close()
 
 
-# (N, P, F, T): W = 16, 32, 64, 128 with P = 2 and P = 1; F not a multiple of
-# the channels per tile; T short, ragged, one chunk, chunk + 1, several chunks.
+# (N, P, F, T): W = 16, 32, 64, 128, 256 with P = 2 and P = 1; F not a
+# multiple of the channels per tile; T short, ragged, one chunk, chunk + 1,
+# several chunks.
 CASES = [(4, 2, 17, 300), (8, 2, 9, 1000), (16, 2, 5, 1024), (32, 2, 3, 1025),
          (8, 1, 13, 70), (16, 1, 7, 2500), (32, 1, 3, 33), (64, 1, 2, 3000),
-         (16, 2, 1, 1), (4, 2, 8, 64)]
+         (16, 2, 1, 1), (4, 2, 8, 64), (64, 2, 7, 1000), (64, 2, 3, 2500), (128, 1, 5, 300),
+         (64, 2, 1, 33)]
 
 
 @pytest.mark.parametrize("N,P,F,T", CASES, ids=["N%d_P%d_F%d_T%d" % c for c in CASES])
 def test_small_engine_bit_exact(N, P, F, T, dev):
-    assert xc.load().xc_small_engine_channels(N, P) == 128 // (2 * N * P)
+    assert xc.load().xc_small_engine_channels(N, P) == max(1, 128 // (2 * N * P))
     x = synth.uniform_int8((T, F, N, P, 2), -128, 127, 7100 + 3 * N + F + T)
     np.testing.assert_array_equal(run(x, dev), oracle.correlate_i8(x.numpy()))
 
 
-def test_small_engine_full_scale_chunk(dev):
+@pytest.mark.parametrize("N", [32, 64])
+def test_small_engine_full_scale_chunk(N, dev):
     """All samples -128 over exactly 1024 samples: every fp32 sum of the
     Gram matrix reaches 128^2 * 1024 = 2^24, the largest exact chunk."""
-    N, P, F, T = 32, 2, 2, 1024
+    P, F, T = 2, 2, 1024
     x = torch.full((T, F, N, P, 2), -128, dtype=torch.int8)
     got = run(x, dev)
     np.testing.assert_array_equal(got, oracle.correlate_i8(x.numpy()))
@@ -72,10 +76,11 @@ def test_small_engine_full_scale_chunk(dev):
 
 
 @pytest.mark.parametrize("accumulate", [False, True], ids=["store", "accumulate"])
-def test_small_engine_split_t(accumulate, dev):
-    """Two channel groups and 20 chunks: T is split across CTAs and the
-    partial sums meet in the output by integer atomics."""
-    N, P, F, T = 16, 2, 4, 20000
+@pytest.mark.parametrize("N", [16, 64])
+def test_small_engine_split_t(accumulate, N, dev):
+    """Two (N=16) or four (N=64) channel groups and 20 chunks: T is split
+    across CTAs and the partial sums meet in the output by integer atomics."""
+    P, F, T = 2, 4, 20000
     x = synth.uniform_int8((T, F, N, P, 2), -128, 127, 7201)
     want = oracle.correlate_i8(x.numpy())
     if accumulate:
@@ -101,7 +106,7 @@ def test_small_engine_accumulate_single_segment(dev):
     np.testing.assert_array_equal(got, oracle.correlate_i8(xa.numpy()) + oracle.correlate_i8(xb.numpy()))
 
 
-@pytest.mark.parametrize("N,P", [(16, 2), (32, 2), (8, 2), (64, 1)])
+@pytest.mark.parametrize("N,P", [(16, 2), (32, 2), (8, 2), (64, 1), (64, 2)])
 def test_auto_picks_small_engine_and_matches_planar(N, P, dev):
     F, T = 37, 500
     x = synth.uniform_int8((T, F, N, P, 2), -128, 127, 7300 + N)
@@ -111,7 +116,7 @@ def test_auto_picks_small_engine_and_matches_planar(N, P, dev):
     np.testing.assert_array_equal(auto, oracle.correlate_i8(x.numpy()))
 
 
-@pytest.mark.parametrize("N,F", [(16, 65528), (32, 65104)])
+@pytest.mark.parametrize("N,F", [(16, 65528), (32, 65104), (64, 16520)])
 def test_small_engine_sweep_size_sampled(N, F, dev):
     """The N sweep's sizes (T = 1000): the whole launch, checked on channels
     spread over it (first, last, and across the persistent CTAs' turns)."""
@@ -134,13 +139,14 @@ def test_tile_small_rejected_where_it_does_not_apply(dev):
     finally:
         eng.close()
     assert xc.load().xc_small_engine_channels(24, 2) == 0
-    assert xc.load().xc_small_engine_channels(64, 2) == 0
+    assert xc.load().xc_small_engine_channels(96, 2) == 0
 
 
-def test_noalloc_small_engine(dev):
+@pytest.mark.parametrize("N", [16, 64])
+def test_noalloc_small_engine(N, dev):
     """xc_correlate_noalloc runs the small-array engine for these sizes, with
     results identical to xc_correlate's."""
-    N, P, F, T = 16, 2, 300, 1100
+    P, F, T = 2, 300, 1100
     x = synth.uniform_int8((T, F, N, P, 2), -128, 127, 7500, device=dev)
     want = run(x, dev, tile=xc.XC_TILE_AUTO)
     out = torch.full(want.shape, -7, dtype=torch.int32, device=dev)
