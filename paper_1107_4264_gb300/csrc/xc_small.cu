@@ -185,10 +185,13 @@ __device__ __forceinline__ void put_vis(int32_t* dst, int re, int im, int mode) 
   }
 }
 
-// W = 2 N P real rows per channel (Cfg<W> holds the shapes).
-template <int W>
+// W = 2 N P real rows per channel (Cfg<W> holds the shapes); P
+// polarisations (a compile-time constant, so the epilogue's station and
+// polarisation indices are shifts).
+template <int W, int P>
 __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
     small_kernel(const __grid_constant__ CUtensorMap in_map, const SmallParams p) {
+  static_assert(P == 1 || P == 2, "one or two polarisations");
   using C = Cfg<W>;
   constexpr int kM = C::kM;
   constexpr int kWt = C::kWt;
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
     const int k = r / kWt;          // channel of row r within the tile (W <= 128)
     const int al = (r % kWt) >> 1;  // input of the row within its tile
     const int c = r & 1;            // 0: the row holds re(x_a), 1: im(x_a)
-    const int PP = p.P * p.P;
+    constexpr int PP = P * P;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
     int ab = 0;
     uint32_t usep = 0;  // bit ab: parity of buffer ab's use count
@@ -363,7 +366,11 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
           // tile ta against those of tile tb (64 inputs per tile).
           const int ta = blk == 0 ? 0 : 1, tb = blk == 2 ? 1 : 0;
           const int a = ta * (kRows / 2) + al;  // station a / P, polarisation a % P
-          const int s1 = a / p.P, p1 = a % p.P;
+          const int s1 = a / P, p1 = a % P;
+          // Row s1's records of this channel: baseline s1 (s1 + 1) / 2 + s2,
+          // product p1 P + p2, two int32 each.
+          int32_t* orow = obase + ((static_cast<int64_t>(s1) * (s1 + 1) / 2) * PP + p1 * P) * 2;
+          const bool lower_only = ta == tb;  // diagonal tile blocks keep s2 <= s1
 #pragma unroll 1
           for (int pc = 0; pc < kPieces; ++pc) {
             uint32_t v[32];
@@ -399,10 +406,8 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
               const int re = c ? g0 + o1 : o0 + g1;
               const int im = c ? o0 - g1 : g0 - o1;
               const int b = tb * (kRows / 2) + 2 * ((kWt >= 32 ? 8 * pc : 0) + jj) + c;
-              const int s2 = b / p.P, p2 = b % p.P;
-              if (chan_ok && s2 <= s1)
-                put_vis(obase + ((static_cast<int64_t>(s1) * (s1 + 1) / 2 + s2) * PP + p1 * p.P + p2) * 2,
-                        re, im, mode);
+              const int s2 = b / P, p2 = b % P;
+              if (chan_ok && (!lower_only || s2 <= s1)) put_vis(orow + (s2 * PP + p2) * 2, re, im, mode);
             }
           }
         }
@@ -487,13 +492,19 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
   }
 }
 
+template <int W, int P>
+cudaError_t launch_wp(const CUtensorMap* map, const SmallParams& p, int grid, cudaStream_t s) {
+  using C = Cfg<W>;
+  cudaError_t e =
+      cudaFuncSetAttribute(small_kernel<W, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  small_kernel<W, P><<<grid, C::kThreads, C::kSmemBytes, s>>>(*map, p);
+  return cudaGetLastError();
+}
+
 template <int W>
 cudaError_t launch_w(const CUtensorMap* map, const SmallParams& p, int grid, cudaStream_t s) {
-  using C = Cfg<W>;
-  cudaError_t e = cudaFuncSetAttribute(small_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
-  if (e != cudaSuccess) return e;
-  small_kernel<W><<<grid, C::kThreads, C::kSmemBytes, s>>>(*map, p);
-  return cudaGetLastError();
+  return p.P == 2 ? launch_wp<W, 2>(map, p, grid, s) : launch_wp<W, 1>(map, p, grid, s);
 }
 
 }  // namespace
