@@ -34,7 +34,8 @@
 // Roles of a persistent CTA (one per SM, 6 + Cfg<W>::kConvWarps warps):
 //   warp 0     TMA producer: [64 samples][m channels][W bytes] int8 boxes;
 //   warp 1     TMEM owner and MMA issuer (one thread);
-//   warps 2-5  epilogue: TMEM -> V (int32) in the output layout;
+//   warps 2-5  epilogue: TMEM -> V (int32) in the output layout (at
+//              W = 256 a second group of four after the converters);
 //   warps 6 .. converters: int8 box -> fp16 tile in the no-swizzle K-major
 //              canonical layout, whole stages in turn.
 // Work items are (channel group, segment of T); a CTA takes items in turn.
@@ -80,6 +81,9 @@ struct Cfg {
   static constexpr int kWt = W > kRows ? kRows : W;           // a channel's rows in one tile
   static constexpr int kBlocks = kTiles * (kTiles + 1) / 2;   // lower tile blocks
   static constexpr int kConvWarps = kTiles == 1 ? 6 : 4;
+  // Epilogue warp groups (four warps each, one per TMEM lane quarter): two at
+  // W = 256, where the single accumulator's drain holds up the next MMAs.
+  static constexpr int kEpiGroups = kTiles == 1 ? 1 : 2;
   static constexpr int kInStages = kTiles == 1 ? 12 : 4;      // int8 boxes in flight
   static constexpr int kOpStages = kTiles == 1 ? 6 : 4;       // fp16 operand slots
   static constexpr int kInBytes = kTiles * kRows * kBK;       // 8 or 16 KiB
@@ -87,7 +91,7 @@ struct Cfg {
   static constexpr int kBufs = kTiles == 1 ? 2 : 1;           // accumulator buffers
   static constexpr int kAccCols = kBlocks * kRows;            // TMEM columns per buffer
   static constexpr uint32_t kTmemCols = kTiles == 1 ? 256 : 512;
-  static constexpr int kThreads = 32 * (kConvWarp0 + kConvWarps);
+  static constexpr int kThreads = 32 * (kConvWarp0 + kConvWarps + 4 * (kEpiGroups - 1));
   static constexpr int kOpOff = 0;
   static constexpr int kInOff = kOpOff + kOpStages * kOpBytes;
   static constexpr int kBarOff = kInOff + kInStages * kInBytes;
@@ -101,6 +105,9 @@ struct Cfg {
                 "each converter warp owns its input and operand slots");
   static_assert(kSmemBytes <= 232448, "shared memory budget");
   static_assert(kBufs * kAccCols <= static_cast<int>(kTmemCols), "TMEM budget");
+  // Every epilogue group must load (and then release the accumulator after)
+  // at least one 32-column piece of each block.
+  static_assert(kEpiGroups <= (kWt >= 32 ? kWt / 32 : 1), "an epilogue group per piece at most");
 
   __device__ static uint32_t in_full(uint32_t b, int s) { return b + 8u * s; }
   __device__ static uint32_t in_empty(uint32_t b, int s) { return b + 8u * (kInStages + s); }
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
     }
     for (int ab = 0; ab < 2; ++ab) {
       ptx::mbar_init(C::accf(bars, ab), 1);
-      ptx::mbar_init(C::acce(bars, ab), 4);
+      ptx::mbar_init(C::acce(bars, ab), 4 * C::kEpiGroups);
     }
     ptx::mbar_init(C::drain(bars), 1);
     *abort_flag = 0;
@@ -334,10 +341,14 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
       while (!ptx::mbar_try_wait(C::drain(bars), 0u) && ptx::globaltimer() - t0 < p.timeout_ns) {
       }
     }
-  } else if (warp < kConvWarp0) {  // warps 2 .. 5
+  } else if (warp < kConvWarp0 || warp >= kConvWarp0 + C::kConvWarps) {
     // --------------------------------------------------------- epilogue
-    // Warp w reads TMEM lanes 32 (w % 4) ..: tile row r is TMEM lane r (in
-    // every block: block (ta, tb) has the rows of tile ta).
+    // Warps 2 .. 5 (group 0) and, at W = 256, the warps after the
+    // converters (group 1); group eg takes the 32-column pieces pc with
+    // pc % kEpiGroups == eg.  Warp w reads TMEM lanes 32 (w % 4) ..: tile
+    // row r is TMEM lane r (in every block: block (ta, tb) has the rows of
+    // tile ta).
+    const int eg = warp < kConvWarp0 ? 0 : 1;
     const int q = warp & 3;
     const int r = 32 * q + lane;
     const int k = r / kWt;          // channel of row r within the tile (W <= 128)
@@ -372,14 +383,14 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
           int32_t* orow = obase + ((static_cast<int64_t>(s1) * (s1 + 1) / 2) * PP + p1 * P) * 2;
           const bool lower_only = ta == tb;  // diagonal tile blocks keep s2 <= s1
 #pragma unroll 1
-          for (int pc = 0; pc < kPieces; ++pc) {
+          for (int pc = eg; pc < kPieces; pc += C::kEpiGroups) {
             uint32_t v[32];
             // Channel k's G columns; with W = 16 the piece holds the warp's two channels.
             const uint32_t col = static_cast<uint32_t>(ab * C::kAccCols + blk * kRows +
                                                        (kWt >= 32 ? k * kWt + 32 * pc : 32 * q));
             ptx::tmem_ld_32x32b_x32(lane_base + col, v);
             ptx::tmem_wait_ld();
-            if (blk == C::kBlocks - 1 && pc == kPieces - 1) {  // the buffer is free for the next chunk
+            if (blk == C::kBlocks - 1 && pc + C::kEpiGroups >= kPieces) {  // the buffer is free for the next chunk
               ptx::tc_fence_before();
               __syncwarp();
               if (lane == 0) ptx::mbar_arrive(C::acce(bars, ab));
