@@ -225,7 +225,7 @@ enum { XC_PREC_FP16 = 0, XC_PREC_HILO = 1, XC_PREC_FP8 = 2 };
  *     operand forms, and for batch handles.
  *   XC_TILE_AUTO: XC_TILE_SMALL where it applies (see
  *     xc_small_engine_channels; an input pointer that is not 16-byte aligned
- *     and the XC_OPT_TEST_NO_PUBLISH hook keep the planar engine), else
+ *     keeps the planar engine), else
  *     XC_TILE_128, the fastest planar shape measured on the Large-N
  *     workload.  A batch handle takes the shape xc_batch_tune chose
  *     (XC_TILE_AUTO restores the default). */

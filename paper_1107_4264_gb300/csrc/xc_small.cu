@@ -129,6 +129,7 @@ struct SmallParams {
   int32_t* out;
   int accumulate;  // add into out instead of overwriting it
   int use_red;     // nseg > 1: every chunk is added with atomics (out pre-zeroed)
+  int test_no_publish;  // test hook: converted tiles are never marked full
   unsigned long long timeout_ns;
   int* status;
 };
@@ -490,7 +491,8 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
       __syncwarp();
       if (lane == 0) {
         ptx::mbar_arrive(C::in_empty(bars, si));
-        ptx::mbar_arrive(C::op_full(bars, so));
+        // (Failure-detection test: without this arrival every MMA wait runs out.)
+        if (!p.test_no_publish) ptx::mbar_arrive(C::op_full(bars, so));
       }
       for (int s = 0; s < C::kConvWarps && it < items; ++s) advance();
     }
@@ -546,6 +548,7 @@ cudaError_t launch_small(const CUtensorMap* in_map, const XeLaunch& X, cudaStrea
   p.out = static_cast<int32_t*>(X.out);
   p.accumulate = X.accumulate;
   p.use_red = p.nseg > 1 ? 1 : 0;
+  p.test_no_publish = X.test_no_publish;
   p.timeout_ns = X.timeout_ns;
   p.status = X.status;
   if (p.use_red && !X.accumulate) {

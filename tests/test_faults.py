@@ -1,8 +1,9 @@
 """Failure detection without a GPU fault.
 
 Device side: the converters of the planar engine are told (test hook
-XC_OPT_TEST_NO_PUBLISH) never to publish a converted unit, so every wait of
-the kernel's consumers runs out after XC_OPT_TIMEOUT_MS.  The kernel must then
+XC_OPT_TEST_NO_PUBLISH) never to publish a converted unit, and those of the
+small-array engine never to mark a converted tile full, so every wait of the
+kernel's consumers runs out after XC_OPT_TIMEOUT_MS.  The kernel must then
 finish its in-flight copies and MMAs, free its tensor memory and return; the
 host reads XC_ERR_TIMEOUT from xc_synchronize, and the same handle must give
 exact results on its next call.  Host side: allocation failure and bad
@@ -28,12 +29,15 @@ def dev():
 
 # 8-bit (TMA converter) and fp16 with n % 4 == 0 (TMA float converter) at
 # N = 256 x 2 pols, where 40 channels exceed the ring's 29 slots, so the
-# converters' slot claims run out too; fp32 with n odd (direct-load converter).
-CASES = [("int8", 256, 2, 40, 128), ("float16", 256, 2, 40, 128), ("float32", 33, 1, 40, 130)]
+# converters' slot claims run out too; fp32 with n odd (direct-load converter);
+# 8-bit at N = 16 and N = 64 x 2 pols (the small-array engine, one tile and
+# two tiles per channel).
+CASES = [("int8", 256, 2, 40, 128), ("float16", 256, 2, 40, 128), ("float32", 33, 1, 40, 130),
+         ("int8", 16, 2, 40, 128), ("int8", 64, 2, 8, 300)]
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("dtype,N,P,F,T", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("dtype,N,P,F,T", CASES, ids=["%s_N%d" % (c[0], c[1]) for c in CASES])
 def test_waits_run_out_and_handle_recovers(dtype, N, P, F, T, dev):
     if dtype == "int8":
         x = synth.uniform_int8((T, F, N, P, 2), -20, 20, 811)
