@@ -18,8 +18,9 @@
 // per channel would skip them, but a tcgen05.mma costs about as long to
 // issue at N = 16 .. 64 as a 128 x 128 one takes to run, so m of them are
 // slower than the one full MMA.)  With W = 256 a channel is two tiles
-// (inputs 0-63 and 64-127) and three 128 x 128 MMAs per step form the
-// lower tile blocks G00, G10 = X1 X0^T and G11.
+// (inputs 0-63 and 64-127) and two MMAs per step form the lower tile
+// blocks: 128 x 128 for G00, 128 x 256 (A = tile 1, B = both tiles) for
+// G10 = X1 X0^T and G11 side by side.
 //
 // No operand ring: a channel's operands are used by one CTA only, so each
 // CTA converts its 8-bit input straight into shared-memory operand tiles.
@@ -31,13 +32,14 @@
 // magnitude <= 128^2 stays <= 2^24, so each 1024-sample chunk is exact in
 // fp32 and chunks add in int32.
 //
-// Roles of a persistent CTA (one per SM, 6 + Cfg<W>::kConvWarps warps):
+// Roles of a persistent CTA (one per SM, 12 warps; 18 at W = 256):
 //   warp 0     TMA producer: [64 samples][m channels][W bytes] int8 boxes;
 //   warp 1     TMEM owner and MMA issuer (one thread);
 //   warps 2-5  epilogue: TMEM -> V (int32) in the output layout (at
 //              W = 256 a second group of four after the converters);
 //   warps 6 .. converters: int8 box -> fp16 tile in the no-swizzle K-major
-//              canonical layout, whole stages in turn.
+//              canonical layout, whole stages in turn (a warp pair per
+//              stage, one warp per tile, at W = 256).
 // Work items are (channel group, segment of T); a CTA takes items in turn.
 // When there are too few channel groups to fill the GPU, T is split into
 // segments whose results are added to the (pre-zeroed) output with integer
@@ -69,18 +71,24 @@ constexpr int kConvWarp0 = 6;                 // warps 0 .. 5: producer, MMA, ep
 // Shapes per channel width W.  W <= 128: kM = 128 / W channels per tile,
 // two 128-column accumulator buffers.  W = 256: one channel of two tiles,
 // whose three lower 128 x 128 blocks fill 384 TMEM columns (one buffer).
-// Converter warp cw takes stages cw, cw + kConvWarps, ...; with slot counts
-// that are multiples of kConvWarps every input and operand slot belongs to
-// one warp, which waits on its barriers phase by phase.  (A slot shared by
-// two warps lets one of them wait on a parity two phases old, which passes
-// too early: mbarrier waits test parity, not a phase count.)
+// Converter group gi takes stages gi, gi + kConvGroups, ...; with slot
+// counts that are multiples of kConvGroups every input and operand slot
+// belongs to one group, which waits on its barriers phase by phase (the two
+// warps of a group cannot get a phase apart: a slot's next fill needs both
+// of their arrivals).  (A slot shared by two groups lets one of them wait on
+// a parity two phases old, which passes too early: mbarrier waits test
+// parity, not a phase count.)
 template <int W>
 struct Cfg {
   static constexpr int kTiles = W > kRows ? W / kRows : 1;
   static constexpr int kM = W > kRows ? 1 : kRows / W;        // channels per group
   static constexpr int kWt = W > kRows ? kRows : W;           // a channel's rows in one tile
   static constexpr int kBlocks = kTiles * (kTiles + 1) / 2;   // lower tile blocks
-  static constexpr int kConvWarps = kTiles == 1 ? 6 : 4;
+  // Converter warps, in groups of kConvPerStage (one warp per tile of a
+  // stage); group gi takes stages gi, gi + kConvGroups, ...
+  static constexpr int kConvPerStage = kTiles;
+  static constexpr int kConvWarps = kTiles == 1 ? 6 : 8;
+  static constexpr int kConvGroups = kConvWarps / kConvPerStage;
   // Epilogue warp groups (four warps each, one per TMEM lane quarter): two at
   // W = 256, where the single accumulator's drain holds up the next MMAs.
   static constexpr int kEpiGroups = kTiles == 1 ? 1 : 2;
@@ -95,14 +103,19 @@ struct Cfg {
   static constexpr int kOpOff = 0;
   static constexpr int kInOff = kOpOff + kOpStages * kOpBytes;
   static constexpr int kBarOff = kInOff + kInStages * kInBytes;
+  // "Drained" barriers: one per accumulator buffer (W <= 128), or one per
+  // tile block of the single accumulator (W = 256), so that the next
+  // chunk's MMAs into a block wait only for that block's drain.
+  static constexpr int kAcce = kTiles == 1 ? kBufs : kBlocks;
   // in_full, in_empty per input stage; op_full, op_empty per operand stage;
-  // accf, acce per accumulator buffer (two reserved); one drain barrier.
-  static constexpr int kNumBars = 2 * kInStages + 2 * kOpStages + 5;
+  // accf per accumulator buffer (two reserved); kAcce drained barriers; one
+  // drain barrier for the exit.
+  static constexpr int kNumBars = 2 * kInStages + 2 * kOpStages + 2 + kAcce + 1;
   static constexpr int kMiscOff = kBarOff + kNumBars * 8;  // TMEM address, abort flag
   static constexpr int kSmemBytes = kMiscOff + 16 + 1024;   // + slack to align the base to 1 KiB
   static_assert(W == 16 || W == 32 || W == 64 || W == 128 || W == 256, "channel widths served");
-  static_assert(kInStages % kConvWarps == 0 && kOpStages % kConvWarps == 0,
-                "each converter warp owns its input and operand slots");
+  static_assert(kInStages % kConvGroups == 0 && kOpStages % kConvGroups == 0,
+                "each converter group owns its input and operand slots");
   static_assert(kSmemBytes <= 232448, "shared memory budget");
   static_assert(kBufs * kAccCols <= static_cast<int>(kTmemCols), "TMEM budget");
   // Every epilogue group must load (and then release the accumulator after)
@@ -114,10 +127,12 @@ struct Cfg {
   __device__ static uint32_t op_full(uint32_t b, int s) { return b + 8u * (2 * kInStages + s); }
   __device__ static uint32_t op_empty(uint32_t b, int s) { return b + 8u * (2 * kInStages + kOpStages + s); }
   __device__ static uint32_t accf(uint32_t b, int ab) { return b + 8u * (2 * kInStages + 2 * kOpStages + ab); }
-  __device__ static uint32_t acce(uint32_t b, int ab) {
-    return b + 8u * (2 * kInStages + 2 * kOpStages + 2 + ab);
+  __device__ static uint32_t acce(uint32_t b, int i) {
+    return b + 8u * (2 * kInStages + 2 * kOpStages + 2 + i);
   }
-  __device__ static uint32_t drain(uint32_t b) { return b + 8u * (2 * kInStages + 2 * kOpStages + 4); }
+  __device__ static uint32_t drain(uint32_t b) {
+    return b + 8u * (2 * kInStages + 2 * kOpStages + 2 + kAcce);
+  }
 };
 
 struct SmallParams {
@@ -217,16 +232,14 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kInStages; ++s) {
       ptx::mbar_init(C::in_full(bars, s), 1);
-      ptx::mbar_init(C::in_empty(bars, s), 1);
+      ptx::mbar_init(C::in_empty(bars, s), C::kConvPerStage);
     }
     for (int s = 0; s < C::kOpStages; ++s) {
-      ptx::mbar_init(C::op_full(bars, s), 1);
+      ptx::mbar_init(C::op_full(bars, s), C::kConvPerStage);
       ptx::mbar_init(C::op_empty(bars, s), 1);
     }
-    for (int ab = 0; ab < 2; ++ab) {
-      ptx::mbar_init(C::accf(bars, ab), 1);
-      ptx::mbar_init(C::acce(bars, ab), 4 * C::kEpiGroups);
-    }
+    for (int ab = 0; ab < 2; ++ab) ptx::mbar_init(C::accf(bars, ab), 1);
+    for (int i = 0; i < C::kAcce; ++i) ptx::mbar_init(C::acce(bars, i), 4 * C::kEpiGroups);
     ptx::mbar_init(C::drain(bars), 1);
     *abort_flag = 0;
     ptx::fence_mbar_init();
@@ -291,8 +304,11 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
         const Item x = item_of(p, it);
         for (int c0 = x.t0; ok && c0 < x.t1; c0 += kChunk) {
           const int c1 = min(x.t1, c0 + kChunk);
-          // The epilogue has read this buffer's previous chunk.
-          if (!ptx::wait_bounded(C::acce(bars, ab), ((usep >> ab) & 1u) ^ 1u, wc)) {
+          // The epilogue has read this buffer's previous chunk.  (W = 256:
+          // each block's drain is awaited just before the chunk's first
+          // MMAs into that block, below.)
+          const uint32_t drained = ((usep >> ab) & 1u) ^ 1u;
+          if (C::kTiles == 1 && !ptx::wait_bounded(C::acce(bars, ab), drained, wc)) {
             ok = false;
             break;
           }
@@ -304,26 +320,36 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
             }
             ptx::tc_fence_after();
             const uint32_t stage = sbase + C::kOpOff + so * C::kOpBytes;
+            // Row ta of the lower tile triangle: A = tile ta, B = tiles
+            // 0 .. ta (contiguous, so one descriptor covers them: N = 128 (ta
+            // + 1)), D = blocks (ta, 0) .. (ta, ta), which sit side by side in
+            // TMEM; the row's four K steps (chunks 2kk, 2kk + 1) in a row.
+            // With one tile, A = B = the tile: D holds every channel's block
+            // on its diagonal and the epilogue reads only those.
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk) {
-              // K step kk = chunks 2kk, 2kk + 1 of every tile.  Block (ta, tb)
-              // of the lower tile triangle: A = tile ta, B = tile tb.  With
-              // one tile, A = B = the tile: D holds every channel's block on
-              // its diagonal and the epilogue reads only those.
-#pragma unroll
-              for (int ta = 0; ta < C::kTiles; ++ta) {
-#pragma unroll
-                for (int tb = 0; tb <= ta; ++tb) {
-                  const uint64_t da =
-                      ptx::interleave_kmajor_desc(stage + ta * kTileBytes + kk * 2 * kCore, kCore, kSbo);
-                  const uint64_t db =
-                      ptx::interleave_kmajor_desc(stage + tb * kTileBytes + kk * 2 * kCore, kCore, kSbo);
-                  const int blk = ta * (ta + 1) / 2 + tb;
-                  ptx::mma_f16_ss(tmem + static_cast<uint32_t>(ab * C::kAccCols + blk * kRows), da, db, idesc,
-                                  (t > c0 || kk > 0) ? 1u : 0u);
+            for (int ta = 0; ta < C::kTiles; ++ta) {
+              const int blk0 = ta * (ta + 1) / 2;
+              if (C::kTiles > 1 && t == c0) {
+                for (int b = blk0; b <= blk0 + ta; ++b) {
+                  if (!ptx::wait_bounded(C::acce(bars, b), drained, wc)) {
+                    ok = false;
+                    break;
+                  }
                 }
+                if (!ok) break;
+                ptx::tc_fence_after();
+              }
+              const uint32_t idesc_row = ta == 0 ? idesc : ptx::idesc_f16_f32(kRows, kRows * (ta + 1));
+#pragma unroll
+              for (int kk = 0; kk < kBK / 16; ++kk) {
+                const uint64_t da =
+                    ptx::interleave_kmajor_desc(stage + ta * kTileBytes + kk * 2 * kCore, kCore, kSbo);
+                const uint64_t db = ptx::interleave_kmajor_desc(stage + kk * 2 * kCore, kCore, kSbo);
+                ptx::mma_f16_ss(tmem + static_cast<uint32_t>(ab * C::kAccCols + blk0 * kRows), da, db, idesc_row,
+                                (t > c0 || kk > 0) ? 1u : 0u);
               }
             }
+            if (!ok) break;
             ptx::mma_commit(C::op_empty(bars, so));  // the tile may be refilled once read
             if (++so == C::kOpStages) {
               so = 0;
@@ -391,10 +417,12 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
                                                        (kWt >= 32 ? k * kWt + 32 * pc : 32 * q));
             ptx::tmem_ld_32x32b_x32(lane_base + col, v);
             ptx::tmem_wait_ld();
-            if (blk == C::kBlocks - 1 && pc + C::kEpiGroups >= kPieces) {  // the buffer is free for the next chunk
+            if (pc + C::kEpiGroups >= kPieces && (C::kTiles > 1 || blk == C::kBlocks - 1)) {
+              // This warp's last load of the block (W = 256) or of the buffer:
+              // the next chunk's MMAs may overwrite it.
               ptx::tc_fence_before();
               __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(C::acce(bars, ab));
+              if (lane == 0) ptx::mbar_arrive(C::acce(bars, C::kTiles > 1 ? blk : ab));
             }
             constexpr int kJ = kWt >= 32 ? 8 : 4;  // input pairs (2j, 2j + 1) in the piece
             const bool hi = kWt == 16 && lane >= 16;
@@ -430,10 +458,11 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
   } else {
     // ------------------------------------------------------- converters
     // The CTA's stages (its items in turn, 64 samples each) are numbered
-    // k = 0, 1, ...; converter warp cw takes k = cw, cw + kConvWarps, ...
-    // whole, so kConvWarps stages are converted at once and each warp's
-    // latency overlaps the others'.  Stage k uses input slot k % kInStages
-    // and operand slot k % kOpStages, in phase k / (slot count).  The box
+    // k = 0, 1, ...; converter group gi takes k = gi, gi + kConvGroups, ...
+    // (its warps one tile each), so kConvGroups stages are converted at once
+    // and each group's latency overlaps the others'.  Stage k uses input slot
+    // k % kInStages and operand slot k % kOpStages, in phase k / (slot
+    // count).  The box
     // ([64 samples][kTiles x 128 bytes]: byte r of a sample's 128-byte
     // piece t is row r of tile t) becomes the fp16 tiles: lane l reads byte
     // word l (rows 4l .. 4l+3) of each sample and writes one 16-byte
@@ -442,6 +471,8 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
     // the 8 rows of a core matrix, one shared-memory bank group each: the
     // 16-byte stores do not conflict.
     const int cw = warp - kConvWarp0;
+    const int cg = cw / C::kConvPerStage;        // converter group: its stages
+    const int ctile = cw % C::kConvPerStage;     // this warp's first tile of each stage
     uint32_t jsel[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) jsel[s] = static_cast<uint32_t>((s + (lane >> 1)) & 3);
@@ -459,15 +490,14 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
         }
       }
     };
-    for (int s = 0; s < cw && it < items; ++s) advance();
-    for (long long k = cw; it < items; k += C::kConvWarps) {
+    for (int s = 0; s < cg && it < items; ++s) advance();
+    for (long long k = cg; it < items; k += C::kConvGroups) {
       const int si = static_cast<int>(k % C::kInStages), so = static_cast<int>(k % C::kOpStages);
       const uint32_t iph = static_cast<uint32_t>((k / C::kInStages) & 1);
       const uint32_t oph = static_cast<uint32_t>((k / C::kOpStages) & 1);
       if (!warp_wait(C::in_full(bars, si), iph, wc) || !warp_wait(C::op_empty(bars, so), oph ^ 1u, wc))
         break;
-#pragma unroll
-      for (int tl = 0; tl < C::kTiles; ++tl) {
+      for (int tl = ctile; tl < C::kTiles; tl += C::kConvPerStage) {
         const uint32_t src = sbase + C::kInOff + si * C::kInBytes + tl * kRows + 4u * lane;
         const uint32_t dst = sbase + C::kOpOff + so * C::kOpBytes + tl * kTileBytes;
 #pragma unroll 2
@@ -494,7 +524,7 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
         // (Failure-detection test: without this arrival every MMA wait runs out.)
         if (!p.test_no_publish) ptx::mbar_arrive(C::op_full(bars, so));
       }
-      for (int s = 0; s < C::kConvWarps && it < items; ++s) advance();
+      for (int s = 0; s < C::kConvGroups && it < items; ++s) advance();
     }
   }
   ptx::tc_fence_before();
