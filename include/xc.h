@@ -336,19 +336,22 @@ int xc_small_engine_channels(int nstation, int npol);
  * an application whose device memory is entirely held by another allocator,
  * or a plug-in whose host forbids allocation inside its processing callback.
  * xc_create allocates the operand workspace, so those callers use this call
- * instead: it runs the same tensor-core kernel as xc_correlate (default tile
+ * instead: it runs the same tensor-core kernel as xc_correlate with default
+ * options (the small-array engine for 8-bit input of the sizes
+ * xc_small_engine_channels accepts, else the planar engine's default tile
  * shape, FP16 operands with the same per-input power-of-two scaling for float
- * input, the same exact chunks for 8-bit input), so its visibilities are
+ * input and the same exact chunks for 8-bit input), so its visibilities are
  * identical to xc_correlate's, and it allocates nothing, neither device nor
  * host memory.
  *
  * Its scratch is a static device array of XC_NOALLOC_SCRATCH_BYTES that
- * every GPU loading the library holds until the process exits.  It holds the
- * kernel's counters, the scale pre-pass maxima (nfreq*npol*nstation words for
- * float input) and as many operand-ring channel slots as fit; one slot is
- * 2*P*N rows (rounded up to 128) x ntime (rounded up to 64) x 2 bytes.  A
- * size where not even one slot fits is rejected with XC_ERR_UNSUPPORTED
- * (message in xc_last_error_message()).
+ * every GPU loading the library holds until the process exits.  The planar
+ * engine keeps in it the kernel's counters, the scale pre-pass maxima
+ * (nfreq*npol*nstation words for float input) and as many operand-ring
+ * channel slots as fit; one slot is 2*P*N rows (rounded up to 128) x ntime
+ * (rounded up to 64) x 2 bytes.  A size where not even one slot fits is
+ * rejected with XC_ERR_UNSUPPORTED (message in xc_last_error_message()).
+ * The small-array engine uses only the status word.
  *
  *   sizes, in_dtype, in, out: as for xc_create / xc_correlate.
  *   status: optional caller-owned device int; a kernel whose bounded wait

@@ -50,7 +50,6 @@
 
 #include <algorithm>
 #include <cstdint>
-#include <mutex>
 
 #include "xc.h"
 #include "xc_internal.h"
@@ -136,7 +135,7 @@ struct Cfg {
 };
 
 struct SmallParams {
-  int N, P, F, T;
+  int P, F, T;
   int ngroups;     // ceil(F / m)
   int nseg;        // segments of T per channel group
   int seg_len;     // samples per segment (a multiple of kChunk)
@@ -563,7 +562,6 @@ cudaError_t launch_small(const CUtensorMap* in_map, const XeLaunch& X, cudaStrea
   const int m = small_tile_channels(g);
   if (m == 0 || X.in_dtype != 0 || !in_map) return cudaErrorInvalidValue;
   SmallParams p;
-  p.N = g.N;
   p.P = g.P;
   p.F = g.F;
   p.T = g.T;
