@@ -209,8 +209,9 @@ enum { XC_PREC_FP16 = 0, XC_PREC_HILO = 1, XC_PREC_FP8 = 2 };
  *     128 x 256 MMA per step (N = 256; one TMEM accumulator set): a quarter
  *     fewer shared-memory and L2 operand bytes per MAC than XC_TILE_128.  Not
  *     with XC_PREC_HILO (XC_ERR_UNSUPPORTED at the call).
- *   XC_TILE_SMALL: the small-array engine (8-bit input, fp16 operands,
- *     W = 2 * nstation * npol in {16, 32, 64, 128, 256}).  Each input is two
+ *   XC_TILE_SMALL: the small-array engine (8-bit input, fp16 operands or,
+ *     with XC_PREC_FP8, e4m3 operands for |x| <= 16 with the same range
+ *     report; W = 2 * nstation * npol in {16, 32, 64, 128, 256}).  Each input is two
  *     real rows (re, im) of 128-row tiles; a tile holds 128 / W channels
  *     (W <= 128) or a channel spans two tiles (W = 256).  Per 16-sample step
  *     128 x 128 MMAs form the real Gram matrix of the tile rows (one MMA, or

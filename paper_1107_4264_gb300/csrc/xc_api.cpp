@@ -240,10 +240,10 @@ xc_handle::Timed* next_timed(xc_handle* h, int nkern) {
 }
 
 // The small-array engine serves XC_ENGINE_TENSOR handles with 8-bit input,
-// fp16 operands and 2 N P in {16, 32, 64, 128, 256} (XC_TILE_AUTO or
+// fp16 or e4m3 operands and 2 N P in {16, 32, 64, 128, 256} (XC_TILE_AUTO or
 // XC_TILE_SMALL).
 bool use_small_engine(const xc_handle* h, const void* in) {
-  return h->dtype == XC_CI8 && h->precision == XC_PREC_FP16 &&
+  return h->dtype == XC_CI8 && (h->precision == XC_PREC_FP16 || h->precision == XC_PREC_FP8) &&
          (h->tile == XC_TILE_AUTO || h->tile == XC_TILE_SMALL) && xc::small_tile_channels(h->g) > 0 &&
          aligned16(in);
 }
@@ -276,6 +276,7 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
     X.in_dtype = 0;
     X.out = out;
     X.accumulate = h->accumulate;
+    X.fmt = h->precision;  // fp16 or e4m3 operands
     X.test_no_publish = h->test_no_publish;
     X.grid = h->num_sms;
     X.timeout_ns = h->timeout_ns;
@@ -290,7 +291,7 @@ xc_status launch_one(xc_handle* h, const void* in, void* out, cudaStream_t s) {
   }
   if (h->engine == XC_ENGINE_TENSOR && h->tile == XC_TILE_SMALL)
     return fail(XC_ERR_UNSUPPORTED,
-                "XC_TILE_SMALL needs 8-bit input, fp16 operands and 2*nstation*npol in {16, 32, 64, 128, 256}");
+                "XC_TILE_SMALL needs 8-bit input, fp16 or e4m3 operands and 2*nstation*npol in {16, 32, 64, 128, 256}");
   if (h->engine == XC_ENGINE_TENSOR) {
     xc::XeLaunch X;
     X.g = h->pg;

@@ -143,7 +143,8 @@ bool input_map_possible(xc_dtype dtype, const Geometry& g);
 xc_status encode_input_map(CUtensorMap* map, const void* in, const Geometry& g, xc_dtype dtype);
 
 // Small-array engine (xc_small.cu): 8-bit input whose channels have
-// W = 2 N P in {16, 32, 64, 128, 256} real rows.  small_tile_channels() is
+// W = 2 N P in {16, 32, 64, 128, 256} real rows; fp16 operands, or e4m3
+// when XeLaunch::fmt is 2.  small_tile_channels() is
 // the number of channels per channel group (128 / W, or 1 for W = 256,
 // whose channel spans two 128-row tiles), or 0 when the geometry does not
 // qualify.  The input map is {W, F, T} bytes in boxes of W x group x 64.  launch_small() may queue a memset of the output

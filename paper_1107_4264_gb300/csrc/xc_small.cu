@@ -46,6 +46,7 @@
 // atomics; integer addition is exact in any order.
 #include <cuda.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,9 +63,7 @@ namespace {
 constexpr int kRows = 128;                    // real rows per operand tile
 constexpr int kBK = 64;                       // samples per stage
 constexpr int kChunk = 1024;                  // samples per exact fp32 chunk
-constexpr int kTileBytes = kRows * kBK * 2;   // one fp16 operand tile: 16 KiB
 constexpr uint32_t kCore = 128;               // one core matrix: 8 rows x 16 B
-constexpr uint32_t kSbo = (kBK / 8) * kCore;  // 1 KiB between 8-row groups
 constexpr int kConvWarp0 = 6;                 // warps 0 .. 5: producer, MMA, epilogue
 
 // Shapes per channel width W.  W <= 128: kM = 128 / W channels per tile,
@@ -77,8 +76,13 @@ constexpr int kConvWarp0 = 6;                 // warps 0 .. 5: producer, MMA, ep
 // of their arrivals).  (A slot shared by two groups lets one of them wait on
 // a parity two phases old, which passes too early: mbarrier waits test
 // parity, not a phase count.)
-template <int W>
+template <int W, bool F8>
 struct Cfg {
+  // Operand tiles: fp16 (8-sample, 16-byte chunks) or, for 4-bit-class
+  // 8-bit input, e4m3 (16-sample chunks): [chunk][128 rows][16 B] per stage.
+  static constexpr int kTileBytes = kRows * kBK * (F8 ? 1 : 2);   // 16 or 8 KiB
+  static constexpr uint32_t kSbo = (kTileBytes / kRows / 16) * kCore;  // between 8-row groups
+  static constexpr int kKStep = F8 ? 32 : 16;                     // samples per MMA
   static constexpr int kTiles = W > kRows ? W / kRows : 1;
   static constexpr int kM = W > kRows ? 1 : kRows / W;        // channels per group
   static constexpr int kWt = W > kRows ? kRows : W;           // a channel's rows in one tile
@@ -94,7 +98,7 @@ struct Cfg {
   static constexpr int kInStages = kTiles == 1 ? 12 : 4;      // int8 boxes in flight
   static constexpr int kOpStages = kTiles == 1 ? 6 : 4;       // fp16 operand slots
   static constexpr int kInBytes = kTiles * kRows * kBK;       // 8 or 16 KiB
-  static constexpr int kOpBytes = kTiles * kTileBytes;        // 16 or 32 KiB
+  static constexpr int kOpBytes = kTiles * kTileBytes;        // one stage's tiles
   static constexpr int kBufs = kTiles == 1 ? 2 : 1;           // accumulator buffers
   static constexpr int kAccCols = kBlocks * kRows;            // TMEM columns per buffer
   static constexpr uint32_t kTmemCols = kTiles == 1 ? 256 : 512;
@@ -173,6 +177,21 @@ __device__ __forceinline__ uint32_t i8pair_to_h2(uint32_t a, uint32_t b, uint32_
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// e4m3 bytes of byte j of four consecutive words w[u0 .. u0+3] (four
+// samples of one row): the exact fp16 pair conversion above, then one
+// fp16x2 -> e4m3x2 conversion per pair (exact for |x| <= 16, saturating).
+__device__ __forceinline__ uint32_t i8quad_to_e4m3(const uint32_t (&w)[16], int u0, uint32_t j) {
+  const uint32_t h01 = i8pair_to_h2(w[u0], w[u0 + 1], j), h23 = i8pair_to_h2(w[u0 + 2], w[u0 + 3], j);
+  __half2_raw r01, r23;
+  r01.x = static_cast<unsigned short>(h01 & 0xffffu);
+  r01.y = static_cast<unsigned short>(h01 >> 16);
+  r23.x = static_cast<unsigned short>(h23 & 0xffffu);
+  r23.y = static_cast<unsigned short>(h23 >> 16);
+  const uint32_t e01 = __nv_cvt_halfraw2_to_fp8x2(r01, __NV_SATFINITE, __NV_E4M3);
+  const uint32_t e23 = __nv_cvt_halfraw2_to_fp8x2(r23, __NV_SATFINITE, __NV_E4M3);
+  return (e01 & 0xffffu) | (e23 << 16);
+}
+
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
                : "memory");
@@ -207,15 +226,18 @@ __device__ __forceinline__ void put_vis(int32_t* dst, int re, int im, int mode) 
   }
 }
 
-// W = 2 N P real rows per channel (Cfg<W> holds the shapes); P
-// polarisations (a compile-time constant, so the epilogue's station and
-// polarisation indices are shifts).
-template <int W, int P>
-__global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
+// W = 2 N P real rows per channel (Cfg holds the shapes); P polarisations
+// (a compile-time constant, so the epilogue's station and polarisation
+// indices are shifts); F8: e4m3 operands (exact for |x| <= 16; a larger
+// value sets the range bit of the status word).
+template <int W, int P, bool F8>
+__global__ void __launch_bounds__(Cfg<W, F8>::kThreads, 1)
     small_kernel(const __grid_constant__ CUtensorMap in_map, const SmallParams p) {
   static_assert(P == 1 || P == 2, "one or two polarisations");
-  using C = Cfg<W>;
+  using C = Cfg<W, F8>;
   constexpr int kM = C::kM;
+  constexpr int kTileBytes = C::kTileBytes;
+  constexpr uint32_t kSbo = C::kSbo;
   constexpr int kWt = C::kWt;
   constexpr int kPieces = kWt >= 32 ? kWt / 32 : 1;  // 32-column TMEM loads per block row
   extern __shared__ unsigned char smem_raw[];
@@ -322,7 +344,7 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
             // Row ta of the lower tile triangle: A = tile ta, B = tiles
             // 0 .. ta (contiguous, so one descriptor covers them: N = 128 (ta
             // + 1)), D = blocks (ta, 0) .. (ta, ta), which sit side by side in
-            // TMEM; the row's four K steps (chunks 2kk, 2kk + 1) in a row.
+            // TMEM; the row's K steps (chunks 2kk, 2kk + 1) in a row.
             // With one tile, A = B = the tile: D holds every channel's block
             // on its diagonal and the epilogue reads only those.
 #pragma unroll
@@ -340,12 +362,17 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
               }
               const uint32_t idesc_row = ta == 0 ? idesc : ptx::idesc_f16_f32(kRows, kRows * (ta + 1));
 #pragma unroll
-              for (int kk = 0; kk < kBK / 16; ++kk) {
+              for (int kk = 0; kk < kBK / C::kKStep; ++kk) {
+                // K step kk: two 16-byte chunks of every row.
                 const uint64_t da =
                     ptx::interleave_kmajor_desc(stage + ta * kTileBytes + kk * 2 * kCore, kCore, kSbo);
                 const uint64_t db = ptx::interleave_kmajor_desc(stage + kk * 2 * kCore, kCore, kSbo);
-                ptx::mma_f16_ss(tmem + static_cast<uint32_t>(ab * C::kAccCols + blk0 * kRows), da, db, idesc_row,
-                                (t > c0 || kk > 0) ? 1u : 0u);
+                const uint32_t dcol = tmem + static_cast<uint32_t>(ab * C::kAccCols + blk0 * kRows);
+                // (kind::f8f6f4 with e4m3 A and B takes the same descriptor type fields as f16.)
+                if constexpr (F8)
+                  ptx::mma_f8_ss(dcol, da, db, idesc_row, (t > c0 || kk > 0) ? 1u : 0u);
+                else
+                  ptx::mma_f16_ss(dcol, da, db, idesc_row, (t > c0 || kk > 0) ? 1u : 0u);
               }
             }
             if (!ok) break;
@@ -499,18 +526,41 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
       for (int tl = ctile; tl < C::kTiles; tl += C::kConvPerStage) {
         const uint32_t src = sbase + C::kInOff + si * C::kInBytes + tl * kRows + 4u * lane;
         const uint32_t dst = sbase + C::kOpOff + so * C::kOpBytes + tl * kTileBytes;
+        if constexpr (F8) {
+          // 16-sample chunks: row j's 16 e4m3 bytes from 16 words.  Bytes
+          // with |x| > 16 (not exact in e4m3) set the range bit.
+          uint32_t mb = 0;
 #pragma unroll 2
-        for (int cc = 0; cc < kBK / 8; ++cc) {
-          uint32_t w[8];
+          for (int cc = 0; cc < kBK / 16; ++cc) {
+            uint32_t w[16];
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
-            w[u] = lds32(src + static_cast<uint32_t>((8 * cc + u) * C::kTiles * kRows));
+            for (int u = 0; u < 16; ++u) {
+              w[u] = lds32(src + static_cast<uint32_t>((16 * cc + u) * C::kTiles * kRows));
+              mb = __vmaxu4(mb, __vabs4(w[u]));
+            }
 #pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            const uint32_t j = jsel[qq];
-            const uint32_t row = 4u * lane + j;
-            sts128(dst + (row >> 3) * kSbo + cc * kCore + (row & 7u) * 16u, i8pair_to_h2(w[0], w[1], j),
-                   i8pair_to_h2(w[2], w[3], j), i8pair_to_h2(w[4], w[5], j), i8pair_to_h2(w[6], w[7], j));
+            for (int qq = 0; qq < 4; ++qq) {
+              const uint32_t j = jsel[qq];
+              const uint32_t row = 4u * lane + j;
+              sts128(dst + (row >> 3) * kSbo + cc * kCore + (row & 7u) * 16u, i8quad_to_e4m3(w, 0, j),
+                     i8quad_to_e4m3(w, 4, j), i8quad_to_e4m3(w, 8, j), i8quad_to_e4m3(w, 12, j));
+            }
+          }
+          if (__vcmpgtu4(mb, 0x10101010u)) atomicOr(p.status, kStatusRange);
+        } else {
+#pragma unroll 2
+          for (int cc = 0; cc < kBK / 8; ++cc) {
+            uint32_t w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              w[u] = lds32(src + static_cast<uint32_t>((8 * cc + u) * C::kTiles * kRows));
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              const uint32_t j = jsel[qq];
+              const uint32_t row = 4u * lane + j;
+              sts128(dst + (row >> 3) * kSbo + cc * kCore + (row & 7u) * 16u, i8pair_to_h2(w[0], w[1], j),
+                     i8pair_to_h2(w[2], w[3], j), i8pair_to_h2(w[4], w[5], j), i8pair_to_h2(w[6], w[7], j));
+            }
           }
         }
       }
@@ -534,19 +584,20 @@ __global__ void __launch_bounds__(Cfg<W>::kThreads, 1)
   }
 }
 
-template <int W, int P>
-cudaError_t launch_wp(const CUtensorMap* map, const SmallParams& p, int grid, cudaStream_t s) {
-  using C = Cfg<W>;
+template <int W, int P, bool F8>
+cudaError_t launch_wpf(const CUtensorMap* map, const SmallParams& p, int grid, cudaStream_t s) {
+  using C = Cfg<W, F8>;
   cudaError_t e =
-      cudaFuncSetAttribute(small_kernel<W, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+      cudaFuncSetAttribute(small_kernel<W, P, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
-  small_kernel<W, P><<<grid, C::kThreads, C::kSmemBytes, s>>>(*map, p);
+  small_kernel<W, P, F8><<<grid, C::kThreads, C::kSmemBytes, s>>>(*map, p);
   return cudaGetLastError();
 }
 
 template <int W>
-cudaError_t launch_w(const CUtensorMap* map, const SmallParams& p, int grid, cudaStream_t s) {
-  return p.P == 2 ? launch_wp<W, 2>(map, p, grid, s) : launch_wp<W, 1>(map, p, grid, s);
+cudaError_t launch_w(const CUtensorMap* map, const SmallParams& p, bool f8, int grid, cudaStream_t s) {
+  if (f8) return p.P == 2 ? launch_wpf<W, 2, true>(map, p, grid, s) : launch_wpf<W, 1, true>(map, p, grid, s);
+  return p.P == 2 ? launch_wpf<W, 2, false>(map, p, grid, s) : launch_wpf<W, 1, false>(map, p, grid, s);
 }
 
 }  // namespace
@@ -586,12 +637,13 @@ cudaError_t launch_small(const CUtensorMap* in_map, const XeLaunch& X, cudaStrea
   }
   const int items = p.ngroups * p.nseg;
   const int grid = std::max(1, std::min(X.grid, items));
+  const bool f8 = X.fmt == 2;  // e4m3 operands (XC_PREC_FP8)
   switch (2 * g.N * g.P) {
-    case 16: return launch_w<16>(in_map, p, grid, s);
-    case 32: return launch_w<32>(in_map, p, grid, s);
-    case 64: return launch_w<64>(in_map, p, grid, s);
-    case 128: return launch_w<128>(in_map, p, grid, s);
-    default: return launch_w<256>(in_map, p, grid, s);
+    case 16: return launch_w<16>(in_map, p, f8, grid, s);
+    case 32: return launch_w<32>(in_map, p, f8, grid, s);
+    case 64: return launch_w<64>(in_map, p, f8, grid, s);
+    case 128: return launch_w<128>(in_map, p, f8, grid, s);
+    default: return launch_w<256>(in_map, p, f8, grid, s);
   }
 }
 

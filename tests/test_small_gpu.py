@@ -13,7 +13,9 @@ sample past it, and several chunks; full-scale -128 input at the chunk
 length where the fp32 sums reach 2^24; T split across CTAs (few channels,
 long T) with and without accumulation; and, at the sweep's channel count, a
 sample of channels spread over the whole launch.  XC_TILE_AUTO must pick the
-engine for these sizes and agree with the planar engine (XC_TILE_128)."""
+engine for these sizes and agree with the planar engine (XC_TILE_128).  With
+e4m3 operands (XC_PREC_FP8) 4-bit-class data (|x| <= 16) is bit-exact too,
+and a larger value is reported."""
 import numpy as np
 import pytest
 import torch
@@ -157,3 +159,37 @@ def test_noalloc_small_engine(N, dev):
     torch.cuda.synchronize(dev)
     assert int(status.item()) == 0
     np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+FP8_CASES = [(4, 2, 9, 300), (8, 2, 5, 1000), (16, 2, 7, 1025), (32, 2, 3, 70), (16, 1, 4, 2500),
+             (64, 2, 3, 1000), (128, 1, 2, 300)]
+
+
+@pytest.mark.parametrize("N,P,F,T", FP8_CASES, ids=["N%d_P%d_F%d_T%d" % c for c in FP8_CASES])
+def test_small_engine_fp8_4bit_exact(N, P, F, T, dev):
+    """e4m3 operands (XC_PREC_FP8) on the small-array engine: 4-bit-class
+    data (|x| <= 16, full range of it) stays bit-exact against the oracle."""
+    x = synth.uniform_int8((T, F, N, P, 2), -16, 16, 7600 + N + F + T)
+    eng = xc.Correlator(N, P, F, T, "int8", tile=xc.XC_TILE_SMALL, precision=xc.XC_PREC_FP8)
+    try:
+        out = eng.correlate(x.to(dev))
+        st = xc.xc_synchronize(eng.h, torch.cuda.current_stream().cuda_stream)
+        got = out.cpu().numpy()
+    finally:
+        eng.close()
+    assert st == xc.XC_OK, xc.status_string(st)
+    np.testing.assert_array_equal(got, oracle.correlate_i8(x.numpy()))
+
+
+@pytest.mark.parametrize("N", [16, 64])
+def test_small_engine_fp8_reports_out_of_range(N, dev):
+    P, F, T = 2, 3, 200
+    x = synth.uniform_int8((T, F, N, P, 2), -7, 7, 7700 + N)
+    x[150, 2, N - 1, 1, 0] = -17
+    eng = xc.Correlator(N, P, F, T, "int8", tile=xc.XC_TILE_SMALL, precision=xc.XC_PREC_FP8)
+    try:
+        eng.correlate(x.to(dev))
+        st = xc.xc_synchronize(eng.h, torch.cuda.current_stream().cuda_stream)
+    finally:
+        eng.close()
+    assert st == xc.XC_ERR_OVERFLOW_RISK, xc.status_string(st)
