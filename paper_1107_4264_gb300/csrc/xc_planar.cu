@@ -195,9 +195,12 @@ cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps,
     default: k->func = nullptr;
   }
   if (!k->func) return cudaErrorInvalidValue;
-  k->block = kThreads;
-  k->smem = shape == kShapePair ? Cfg<kShapePair>::kSmemBytes
-                                : (shape == kShapeWide ? Cfg<kShapeWide>::kSmemBytes : Cfg<kShape128>::kSmemBytes);
+  const bool f8 = fmt == kFmtF8;
+  k->block = f8 ? threads_of<kFmtF8>() : threads_of<kFmtF16>();
+  k->smem = shape == kShapePair
+                ? (f8 ? Cfg<kShapePair, kFmtF8>::kSmemBytes : Cfg<kShapePair, kFmtF16>::kSmemBytes)
+                : (shape == kShapeWide ? (f8 ? Cfg<kShapeWide, kFmtF8>::kSmemBytes : Cfg<kShapeWide, kFmtF16>::kSmemBytes)
+                                       : (f8 ? Cfg<kShape128, kFmtF8>::kSmemBytes : Cfg<kShape128, kFmtF16>::kSmemBytes));
   k->shape = shape;
   cudaError_t e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, k->smem);
   if (e != cudaSuccess) return e;
@@ -206,7 +209,7 @@ cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps,
   if (pair) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(std::max(2, subs[0].grid & ~1)));
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(static_cast<unsigned>(k->block));
     cfg.dynamicSmemBytes = static_cast<size_t>(k->smem);
     int clusters = 0;
     e = cudaOccupancyMaxActiveClusters(&clusters, k->func, &cfg);
@@ -216,7 +219,7 @@ cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps,
     k->grid = static_cast<int>(2 * ncl);
   } else {
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, kThreads, static_cast<size_t>(k->smem));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, k->block, static_cast<size_t>(k->smem));
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long resident = static_cast<long long>(per_sm) * subs[0].grid;
