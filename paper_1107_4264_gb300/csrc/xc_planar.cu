@@ -195,12 +195,13 @@ cudaError_t planar_prepare(const XeLaunch* subs, const CUtensorMap* const* maps,
     default: k->func = nullptr;
   }
   if (!k->func) return cudaErrorInvalidValue;
-  const bool f8 = fmt == kFmtF8;
-  k->block = f8 ? threads_of<kFmtF8>() : threads_of<kFmtF16>();
+  const bool f8 = fmt == kFmtF8 && dt == 0;  // the e4m3 plan of 8-bit input
+  k->block = f8 ? threads_of<kFmtF8, 0>() : threads_of<kFmtF16, 0>();
   k->smem = shape == kShapePair
-                ? (f8 ? Cfg<kShapePair, kFmtF8>::kSmemBytes : Cfg<kShapePair, kFmtF16>::kSmemBytes)
-                : (shape == kShapeWide ? (f8 ? Cfg<kShapeWide, kFmtF8>::kSmemBytes : Cfg<kShapeWide, kFmtF16>::kSmemBytes)
-                                       : (f8 ? Cfg<kShape128, kFmtF8>::kSmemBytes : Cfg<kShape128, kFmtF16>::kSmemBytes));
+                ? (f8 ? Cfg<kShapePair, kFmtF8, 0>::kSmemBytes : Cfg<kShapePair, kFmtF16, 0>::kSmemBytes)
+                : (shape == kShapeWide
+                       ? (f8 ? Cfg<kShapeWide, kFmtF8, 0>::kSmemBytes : Cfg<kShapeWide, kFmtF16, 0>::kSmemBytes)
+                       : (f8 ? Cfg<kShape128, kFmtF8, 0>::kSmemBytes : Cfg<kShape128, kFmtF16, 0>::kSmemBytes));
   k->shape = shape;
   cudaError_t e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, k->smem);
   if (e != cudaSuccess) return e;

@@ -126,33 +126,39 @@ enum : int { kShape128 = 0, kShapePair = 1, kShapeWide = 2 };
 
 enum : int { kFmtF16 = 0, kFmtHiLo = 1, kFmtF8 = 2 };
 
-// Converter warps per CTA: six for e4m3 operands, whose conversion costs the
-// most per byte while its MMAs take half the time; four otherwise.
-template <int FMT>
-constexpr int conv_warps() {
-  return FMT == kFmtF8 ? 6 : kNumConvWarps;
+// The stage plan of 8-bit input on e4m3 operands, whose conversion costs the
+// most per byte while its MMAs take half the time: half-size stages, and six
+// converter warps instead of four (float input keeps the fp16 plan: its
+// converters gain nothing from more warps and spill more registers).
+template <int FMT, int DT>
+constexpr bool f8_int8_plan() {
+  return FMT == kFmtF8 && DT == 0;
 }
-template <int FMT>
+template <int FMT, int DT>
+constexpr int conv_warps() {
+  return f8_int8_plan<FMT, DT>() ? 6 : kNumConvWarps;
+}
+template <int FMT, int DT>
 constexpr int threads_of() {
-  return 32 * (2 + kNumEpiWarps + conv_warps<FMT>());
+  return 32 * (2 + kNumEpiWarps + conv_warps<FMT, DT>());
 }
 
 // Shared-memory plan per shape and operand format: stages of (Ar, Ai, Br,
 // Bi) tiles; (Ar, Ai, half Br, half Bi) on pairs; (Ar, Ai, Br Br', Bi Bi')
 // for 128 x 256; then the converters' staging buffers and the barriers.
-// e4m3 tiles are half the size of fp16 ones: more stages and two more
-// converter warps fit in the same bytes.
-template <int SHAPE, int FMT>
+// e4m3 tiles are half the size of fp16 ones: for 8-bit input, more stages
+// and two more converter warps fit in the same bytes.
+template <int SHAPE, int FMT, int DT>
 struct Cfg {
-  static constexpr bool kF8 = FMT == kFmtF8;
+  static constexpr bool kF8 = f8_int8_plan<FMT, DT>();
   static constexpr int kStages = kF8 ? (SHAPE == kShapePair ? 7 : (SHAPE == kShapeWide ? 3 : 5))
                                      : (SHAPE == kShapePair ? 4 : (SHAPE == kShapeWide ? 2 : 3));
   static constexpr int kStageBytes =
       (SHAPE == kShapePair ? 3 : (SHAPE == kShapeWide ? 6 : 4)) * (kF8 ? kTileBytes / 2 : kTileBytes);
   static constexpr int kConvOff = kStages * kStageBytes;
-  static constexpr int kBarOff = kConvOff + conv_warps<FMT>() * kConvBufBytes;
+  static constexpr int kBarOff = kConvOff + conv_warps<FMT, DT>() * kConvBufBytes;
   // full, empty (and pfull) per stage; accf, acce x 2; drain; one per converter
-  static constexpr int kNumBars = (SHAPE == kShapePair ? 3 : 2) * kStages + 5 + conv_warps<FMT>();
+  static constexpr int kNumBars = (SHAPE == kShapePair ? 3 : 2) * kStages + 5 + conv_warps<FMT, DT>();
   // then the TMEM address, the abort flag and one word per stage (the chunk
   // length of the item whose first step the stage holds)
   static constexpr int kSmemBytes = kBarOff + kNumBars * 8 + 8 + 4 * kStages + 1024;
@@ -496,9 +502,9 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
 template <int DT, int FMT, bool MULTI>
 __device__ void converter_direct(const Batch& bt, int cw, int lane, volatile int* abort_flag) {
   const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
-  const long long stride = static_cast<long long>(gridDim.x) * conv_warps<FMT>();
+  const long long stride = static_cast<long long>(gridDim.x) * conv_warps<FMT, DT>();
   int sb = 0, claimed = -1, claimed_sb = -1;
-  for (long long u = static_cast<long long>(blockIdx.x) * conv_warps<FMT>() + cw; u < total; u += stride) {
+  for (long long u = static_cast<long long>(blockIdx.x) * conv_warps<FMT, DT>() + cw; u < total; u += stride) {
     sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
     const Params& p = bt.sub[sb];
     const Unit x = unit_of(p, u - bt.unit_base[sb]);
@@ -644,7 +650,7 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
                               volatile int* abort_flag) {
   static_assert(FMT == kFmtF16 || FMT == kFmtF8, "8-bit input: fp16 or e4m3 operands");
   const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
-  const long long nw = static_cast<long long>(gridDim.x) * conv_warps<FMT>();
+  const long long nw = static_cast<long long>(gridDim.x) * conv_warps<FMT, 0>();
   const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
   int sb_issue = 0;
   bool tma_pending = false;  // a box issued and not yet waited for
@@ -671,7 +677,7 @@ __device__ void converter_tma(const Batch& bt, uint32_t buf, uint32_t bar, int c
   const Params* pend = nullptr;
   int pend_slot = 0, pend_c = -1, pend_sb = -1;
   unsigned pend_n = 0;
-  long long u = first_unit(static_cast<long long>(blockIdx.x) * conv_warps<FMT>() + cw);
+  long long u = first_unit(static_cast<long long>(blockIdx.x) * conv_warps<FMT, 0>() + cw);
   if (u < total) issue(u);
   for (; u < total; u = next_unit(u, nw)) {
     sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
@@ -886,7 +892,7 @@ __device__ void converter_tma_float(const Batch& bt, uint32_t buf, uint32_t bar,
   constexpr int kBoxes = kUnitT / kFBox;
   static_assert(kFBox % 16 == 0 && kUnitT % kFBox == 0, "boxes hold whole 16-sample groups");
   const long long total = table_end<MULTI>(bt.unit_base, bt.nsub);
-  const long long nw = static_cast<long long>(gridDim.x) * conv_warps<FMT>();
+  const long long nw = static_cast<long long>(gridDim.x) * conv_warps<FMT, DT>();
   const ptx::WaitCtl wc{bt.sub[0].timeout_ns, bt.sub[0].status, abort_flag};
   int sb_issue = 0;
   bool tma_pending = false;  // a box issued and not yet waited for
@@ -909,7 +915,7 @@ __device__ void converter_tma_float(const Batch& bt, uint32_t buf, uint32_t bar,
   const Params* pend = nullptr;
   int pend_slot = 0, pend_c = -1, pend_sb = -1;
   unsigned pend_n = 0;
-  long long u = first_unit(static_cast<long long>(blockIdx.x) * conv_warps<FMT>() + cw);
+  long long u = first_unit(static_cast<long long>(blockIdx.x) * conv_warps<FMT, DT>() + cw);
   if (u < total) issue(u, 0);
   for (; u < total; u = next_unit(u, nw)) {
     sb = advance_sub<MULTI>(bt.unit_base, bt.nsub, u, sb);
@@ -1410,7 +1416,7 @@ template <bool IS_INT, int DT, int FMT, bool MULTI, int SHAPE>
 __device__ __forceinline__ void planar_body(const Batch& bt) {
   constexpr bool PAIR = SHAPE == kShapePair;
   constexpr bool WIDE = SHAPE == kShapeWide;
-  using C = Cfg<SHAPE, FMT>;
+  using C = Cfg<SHAPE, FMT, DT>;
   constexpr int kStages = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -1449,7 +1455,7 @@ __device__ __forceinline__ void planar_body(const Batch& bt) {
       ptx::mbar_init(acce_bar(b), (PAIR ? 2 : 1) * kNumEpiWarps);
     }
     ptx::mbar_init(drain_bar, 1);
-    for (int w = 0; w < conv_warps<FMT>(); ++w) ptx::mbar_init(conv_bar(w), 1);
+    for (int w = 0; w < conv_warps<FMT, DT>(); ++w) ptx::mbar_init(conv_bar(w), 1);
     *abort_flag = 0;
     ptx::fence_mbar_init();
     ptx::fence_proxy_async_smem();
@@ -1992,20 +1998,20 @@ __device__ __forceinline__ void planar_body(const Batch& bt) {
 }
 
 template <bool IS_INT, int DT, int FMT, bool MULTI>
-__global__ void __launch_bounds__(threads_of<FMT>(), 1) planar_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(threads_of<FMT, DT>(), 1) planar_kernel(const __grid_constant__ Batch bt) {
   planar_body<IS_INT, DT, FMT, MULTI, kShape128>(bt);
 }
 
 // 128 x 256 items: one CTA, N = 256 MMAs.
 template <bool IS_INT, int DT, int FMT, bool MULTI>
-__global__ void __launch_bounds__(threads_of<FMT>(), 1) planar_wide_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(threads_of<FMT, DT>(), 1) planar_wide_kernel(const __grid_constant__ Batch bt) {
   if constexpr (FMT != kFmtHiLo) planar_body<IS_INT, DT, FMT, MULTI, kShapeWide>(bt);
 }
 
 // CTA pairs: the cluster shape is part of the kernel, so no launch can run it
 // without its peer.
 template <bool IS_INT, int DT, int FMT, bool MULTI>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(threads_of<FMT>(), 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(threads_of<FMT, DT>(), 1)
     planar_pair_kernel(const __grid_constant__ Batch bt) {
   planar_body<IS_INT, DT, FMT, MULTI, kShapePair>(bt);
 }
