@@ -9,10 +9,11 @@
 // n / 128 of each MMA pairs inputs of one channel.  This kernel instead
 // takes every input as two real rows (re, im: the interleaved order the
 // input already has) so that a 128-row operand tile holds m = 128 / (2 n)
-// channels at twice that density.  One 128 x 128 MMA per 16-sample step
-// (A = B = the tile) gives the real Gram matrix G = X X^T of the tile's
-// rows, with channel k's W x W block on the diagonal at rows and columns
-// k W .. k W + W - 1.  For inputs a, b with real rows (2a, 2a+1), (2b, 2b+1):
+// channels at twice that density.  One 128 x 128 MMA per K step (16
+// samples; 32 with e4m3 operands), A = B = the tile, gives the real Gram
+// matrix G = X X^T of the tile's rows, with channel k's W x W block on the
+// diagonal at rows and columns k W .. k W + W - 1.  For inputs a, b with
+// real rows (2a, 2a+1), (2b, 2b+1):
 //   Re V_ab = G[2a][2b] + G[2a+1][2b+1],  Im V_ab = G[2a+1][2b] - G[2a][2b+1].
 // The cross-channel blocks are computed and not read.  (One 128 x W MMA
 // per channel would skip them, but a tcgen05.mma costs about as long to
@@ -23,23 +24,26 @@
 // G10 = X1 X0^T and G11 side by side.
 //
 // No operand ring: a channel's operands are used by one CTA only, so each
-// CTA converts its 8-bit input straight into shared-memory operand tiles.
-// The kernel is then bound by the input stream from HBM (one read of
-// 2 n bytes per channel-sample) for every n it serves.
+// CTA converts its 8-bit input straight into shared-memory operand tiles
+// and reads the input once (2 n bytes per channel-sample).  What bounds it
+// is that input stream and the shared-memory traffic it shares with the
+// conversion and the MMAs' operand reads.
 //
 // Exactness (Sec. 5's 8-bit input): int8 samples are exact in fp16, their
 // products exact in fp32, and a fp32 sum of at most 1024 products of
 // magnitude <= 128^2 stays <= 2^24, so each 1024-sample chunk is exact in
-// fp32 and chunks add in int32.
+// fp32 and chunks add in int32.  With e4m3 operands (opt-in, 4-bit-class
+// data) the same holds for |x| <= 16; a larger value sets the range bit of
+// the status word.
 //
 // Roles of a persistent CTA (one per SM, 12 warps; 18 at W = 256):
 //   warp 0     TMA producer: [64 samples][m channels][W bytes] int8 boxes;
 //   warp 1     TMEM owner and MMA issuer (one thread);
 //   warps 2-5  epilogue: TMEM -> V (int32) in the output layout (at
 //              W = 256 a second group of four after the converters);
-//   warps 6 .. converters: int8 box -> fp16 tile in the no-swizzle K-major
-//              canonical layout, whole stages in turn (a warp pair per
-//              stage, one warp per tile, at W = 256).
+//   warps 6 .. converters: int8 box -> fp16 (or e4m3) tile in the
+//              no-swizzle K-major canonical layout, whole stages in turn (a
+//              warp pair per stage, one warp per tile, at W = 256).
 // Work items are (channel group, segment of T); a CTA takes items in turn.
 // When there are too few channel groups to fill the GPU, T is split into
 // segments whose results are added to the (pre-zeroed) output with integer
@@ -96,7 +100,7 @@ struct Cfg {
   // W = 256, where the single accumulator's drain holds up the next MMAs.
   static constexpr int kEpiGroups = kTiles == 1 ? 1 : 2;
   static constexpr int kInStages = kTiles == 1 ? 12 : 4;      // int8 boxes in flight
-  static constexpr int kOpStages = kTiles == 1 ? 6 : 4;       // fp16 operand slots
+  static constexpr int kOpStages = kTiles == 1 ? 6 : 4;       // operand (tile) slots
   static constexpr int kInBytes = kTiles * kRows * kBK;       // 8 or 16 KiB
   static constexpr int kOpBytes = kTiles * kTileBytes;        // one stage's tiles
   static constexpr int kBufs = kTiles == 1 ? 2 : 1;           // accumulator buffers
